@@ -1,0 +1,170 @@
+/*
+ * wf.h -- C ABI of the GB300 dual messenger Wiener-filter library.
+ *
+ * The library solves the Wiener-filter equation (S^-1 + N^-1) s_WF = N^-1 d
+ * (Eq. 2 of Kodi Ramanah, Lavaux & Wandelt 2017) on the sphere with the
+ * hybrid dual messenger iteration of the paper's Algorithm 2 (Eqs. 13-15):
+ * a HEALPix-ring pixelisation with RING pixel order, a band-limited isotropic
+ * signal covariance S = diag(C_l), a per-pixel noise variance N = diag(sigma^2_p)
+ * and an arbitrary mask (N^-1 = 0 on masked pixels).
+ *
+ * Conventions used by every call:
+ *  - Maps: double[Npix], Npix = 12 nside^2, HEALPix RING order.
+ *  - Harmonic coefficients ("alm"): double[2 * Nalm], Nalm = (lmax+1)(lmax+2)/2,
+ *    complex numbers stored (re, im) interleaved, m-major: the coefficient
+ *    (l, m), 0 <= m <= l <= lmax, sits at complex index m*(2 lmax + 1 - m)/2 + l.
+ *    Negative m follow from the reality of the field.  Y_lm are orthonormal
+ *    with the Condon-Shortley phase.
+ *  - Synthesis Y: s(p) = sum_l [a_l0 Y_l0(p) + 2 sum_{m>0} Re(a_lm Y_lm(p))].
+ *    Analysis "map2alm" is Omega * Y^T with Omega = 4 pi / Npix (no ring
+ *    weights): a_lm = Omega sum_p s(p) Y*_lm(p).
+ *  - "_dev" pointers are CUDA device pointers; "_host" pointers are host memory.
+ *    The caller owns every buffer it passes; the library owns its plan and
+ *    the plan's workspaces.  Device arguments must stay valid until the call
+ *    that uses them has completed on the plan's stream.
+ *  - All work of a plan is ordered on the CUDA stream given at plan creation
+ *    (NULL = the legacy default stream).  Calls return when their results are
+ *    ready (they synchronise the plan's stream) unless documented otherwise.
+ *  - No call throws; each returns a wf_status.  wf_last_error() gives a
+ *    human-readable message for the last failing call of the calling thread.
+ *  - A plan is not thread-safe: calls on one plan must not overlap.
+ */
+#ifndef WF_H
+#define WF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wf_plan_s *wf_plan_t;
+
+typedef enum {
+  WF_OK = 0,
+  WF_ERR_ARG = 1,            /* invalid argument (nothing was launched) */
+  WF_ERR_CUDA = 2,           /* a CUDA call failed; see wf_last_error() */
+  WF_ERR_NOT_CONVERGED = 3,  /* max_iter reached; outputs hold the last iterate */
+  WF_ERR_NUMERIC = 4,        /* NaN/Inf met in the iteration */
+  WF_ERR_TIMEOUT = 5,        /* a bounded device wait gave up */
+  WF_ERR_UNIMPLEMENTED = 6,
+  WF_ERR_STATE = 7           /* call not valid for this plan (e.g. no noise) */
+} wf_status;
+
+typedef enum { WF_PREC_FP64 = 0, WF_PREC_MIXED = 1 } wf_precision;
+
+typedef enum {
+  WF_STOP_CAUCHY = 0, /* last stage ends when ||x_i - x_{i-1}|| / ||x_i|| < eps_final */
+  WF_STOP_ERROR = 1   /* last stage ends when the geometric error estimate
+                         c_i r / (1 - r), r = c_i / c_{i-1}, is < eps_final */
+} wf_stop_rule;
+
+/* Solver options.  Start from wf_opts_default() and override fields. */
+typedef struct {
+  double beta;       /* cooling factor of xi, 0 < beta < 1 (Algorithm 2; default 0.75) */
+  double eps_final;  /* tolerance of the last stage (default 1e-6) */
+  double eps_cap;    /* relaxed tolerance of the early stages is
+                        min(eps_cap, eps_final * mu / alpha) (default 1e-2) */
+  double mu0;        /* initial mu in pixel-variance units; < 0 selects
+                        mu0 * Omega = beta * max_l C_l (default -1) */
+  int max_iter;      /* bound on the total number of iterations (default 200000) */
+  int stop_rule;     /* wf_stop_rule (default WF_STOP_ERROR) */
+  int precision;     /* wf_precision (default WF_PREC_FP64) */
+  int band_limit;    /* 1: restrict each stage's transforms to the band where
+                        the truncated spectrum is nonzero (exact; default 1) */
+  int graph_chunk;   /* iterations per captured CUDA graph launch; 0 = auto */
+  int refine_max;    /* WF_PREC_MIXED: max FP64 refinement steps (default 8) */
+} wf_opts;
+
+/* Per-solve statistics. */
+typedef struct {
+  int iterations;      /* inner iterations, all stages (mixed: all passes) */
+  int stages;          /* cooling stages run (mixed: of the first pass) */
+  int converged;       /* 1 if the last stage met its stop rule */
+  int refinements;     /* WF_PREC_MIXED: FP64 correction steps taken */
+  double alpha;        /* min noise variance over observed pixels */
+  double final_cauchy; /* last Cauchy ratio */
+  double err_estimate; /* last geometric error estimate (WF_STOP_ERROR) */
+  double fp_residual;  /* WF_PREC_MIXED: final FP64 fixed-point residual */
+  double elapsed_ms;   /* device time of the solve (CUDA events) */
+} wf_stats;
+
+void wf_opts_default(wf_opts *opts);
+
+/* Create a plan for one geometry and one problem.
+ *  nside         HEALPix resolution, 1 <= nside <= 8192.
+ *  lmax          band limit, 1 <= lmax <= 3 nside - 1.
+ *  cl_host       host double[lmax+1]: C_l >= 0 (signal covariance, Eq. 2).
+ *  noise_var_dev device double[Npix]: sigma^2_p > 0 on observed pixels; may be
+ *                NULL for a transform-only plan (wf_alm2map / wf_map2alm).
+ *  mask_dev      device uint8_t[Npix], nonzero = masked (N^-1 = 0); may be NULL.
+ *  opts          NULL = defaults.   stream: cudaStream_t or NULL.
+ * Errors: WF_ERR_ARG for out-of-range sizes, negative C_l, all pixels masked,
+ * or a non-positive / non-finite variance on an observed pixel (checked on
+ * the device during creation).  The noise and mask are copied; the caller
+ * may free them after the call. */
+wf_status wf_plan(wf_plan_t *out, int nside, int lmax, const double *cl_host,
+                  const double *noise_var_dev, const uint8_t *mask_dev,
+                  const wf_opts *opts, void *stream);
+
+/* Replace the noise variance and mask of an existing plan (same geometry). */
+wf_status wf_set_noise(wf_plan_t plan, const double *noise_var_dev,
+                       const uint8_t *mask_dev);
+
+/* Replace the spectrum C_l of an existing plan. */
+wf_status wf_set_cl(wf_plan_t plan, const double *cl_host);
+
+/* Solve (S^-1 + N^-1) s = N^-1 d with Algorithm 2 (Sect. 2.2).
+ *  d_dev      device double[Npix] data map (values on masked pixels ignored).
+ *  alm_dev    device double[2 Nalm] output: the harmonic coefficients of
+ *             s_WF, or NULL.
+ *  map_dev    device double[Npix] output: s_WF = Y alm, or NULL.
+ *  init_alm_dev / init_map_dev  optional warm start (NULL = the paper's cold
+ *             start s_0 = 0, t_0 = d): the initial signal coefficients and
+ *             messenger field t_0; if only init_alm_dev is given, t_0 = d.
+ *  stats      optional output.
+ * Returns WF_OK, WF_ERR_NOT_CONVERGED (outputs hold the last iterate) or an
+ * error. */
+wf_status wf_solve(wf_plan_t plan, const double *d_dev, double *alm_dev,
+                   double *map_dev, const double *init_alm_dev,
+                   const double *init_map_dev, wf_stats *stats);
+
+/* Same as wf_solve with host buffers: copies d in, solves, copies the
+ * requested outputs back (both copies are part of the call). */
+wf_status wf_solve_host(wf_plan_t plan, const double *d_host, double *alm_host,
+                        double *map_host, wf_stats *stats);
+
+/* Diagnostics of a candidate solution alm_dev (Sect. 4, App. C), FP64:
+ *  rel_res_wf  ||A x - y|| / ||y||, A = 1 + C^1/2 Y^T N^-1 Y C^1/2,
+ *              x = C^-1/2 alm, y = C^1/2 Y^T N^-1 d (the residual of Fig. 5);
+ *  rel_res_fp  ||G(alm) - alm|| / ||alm|| for one last-stage iteration G
+ *              (xi = alpha, mu = 0): the messenger fixed-point residual;
+ *  chi2        (d - Y alm)^T N^-1 (d - Y alm) + alm^T C^-1 alm.
+ * Any output pointer may be NULL. */
+wf_status wf_residual(wf_plan_t plan, const double *d_dev, const double *alm_dev,
+                      double *rel_res_wf, double *rel_res_fp, double *chi2);
+
+/* FP64 spherical-harmonic transforms on the plan's geometry.
+ * wf_alm2map: map = Y alm.  wf_map2alm: alm = Omega Y^T map. */
+wf_status wf_alm2map(wf_plan_t plan, const double *alm_dev, double *map_dev);
+wf_status wf_map2alm(wf_plan_t plan, const double *map_dev, double *alm_dev);
+
+/* Sizes of a plan. */
+long wf_npix(int nside);
+long wf_nalm(int lmax);
+
+/* Copy the per-iteration trace of the last solve to host arrays of length
+ * >= *count (in: capacity, out: entries written): stage index, xi, mu and
+ * the Cauchy ratio of each iteration. */
+wf_status wf_trace(wf_plan_t plan, int *count, int *stage, double *xi,
+                   double *mu, double *cauchy);
+
+void wf_destroy(wf_plan_t plan);
+const char *wf_status_str(wf_status s);
+const char *wf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WF_H */

@@ -1,0 +1,285 @@
+// capi.cu -- the extern "C" entry points declared in include/wf.h:
+// argument checking, plan lifetime, error strings.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "wf_internal.cuh"
+
+namespace wf {
+static thread_local std::string g_last_error;
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+static wf_status arg_error(const char *msg) {
+  set_error(msg);
+  return WF_ERR_ARG;
+}
+
+static void free_plan(wf_plan_s *P) {
+  if (!P) return;
+  for (int i = 0; i < 2; ++i)
+    if (P->graph[i]) cudaGraphExecDestroy(P->graph[i]);
+  void *bufs[] = {P->pairs, P->cl_d,   P->rc,      P->rg,     P->rc32,   P->seed_l,
+                  P->seed_u, P->tw64,  P->tw32,    P->chirp64, P->chirp32, P->bhat64,
+                  P->bhat32, P->nvar,  P->F64,     P->G64,    P->F32,    P->G32,
+                  P->x,      P->xtmp,  P->dmap,    P->mtmp,   P->partials, P->red,
+                  P->state,  P->trace};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  if (P->state_h) cudaFreeHost(P->state_h);
+  if (P->capture_stream) cudaStreamDestroy(P->capture_stream);
+  if (P->ev0) cudaEventDestroy(P->ev0);
+  if (P->ev1) cudaEventDestroy(P->ev1);
+  delete P;
+}
+
+static wf_status alloc_work(Plan &P) {
+  const size_t nF = (size_t)P.nring * (P.lmax + 1);
+  WF_CUDA(cudaMalloc(&P.F64, sizeof(double2) * nF));
+  WF_CUDA(cudaMalloc(&P.G64, sizeof(double2) * nF));
+  WF_CUDA(cudaMalloc(&P.F32, sizeof(float2) * nF));
+  WF_CUDA(cudaMalloc(&P.G32, sizeof(float2) * nF));
+  WF_CUDA(cudaMalloc(&P.x, sizeof(double2) * P.nalm));
+  WF_CUDA(cudaMalloc(&P.xtmp, sizeof(double2) * P.nalm));
+  WF_CUDA(cudaMalloc(&P.dmap, sizeof(double) * P.npix));
+  WF_CUDA(cudaMalloc(&P.mtmp, sizeof(double) * P.npix));
+  WF_CUDA(cudaMalloc(&P.partials, sizeof(double) * 2 * (P.lmax + 1)));
+  WF_CUDA(cudaMalloc(&P.red, sizeof(double) * 1024));
+  WF_CUDA(cudaMalloc(&P.state, sizeof(SolverState)));
+  WF_CUDA(cudaMallocHost(&P.state_h, sizeof(SolverState)));
+  P.trace_cap = 1 << 20;
+  WF_CUDA(cudaMalloc(&P.trace, sizeof(TraceEntry) * P.trace_cap));
+  WF_CUDA(cudaEventCreate(&P.ev0));
+  WF_CUDA(cudaEventCreate(&P.ev1));
+  WF_CUDA(cudaMemsetAsync(P.F64, 0, sizeof(double2) * nF, P.stream));
+  WF_CUDA(cudaMemsetAsync(P.G64, 0, sizeof(double2) * nF, P.stream));
+  WF_CUDA(cudaMemsetAsync(P.F32, 0, sizeof(float2) * nF, P.stream));
+  WF_CUDA(cudaMemsetAsync(P.G32, 0, sizeof(float2) * nF, P.stream));
+  return WF_OK;
+}
+
+static wf_status check_opts(const wf_opts &o) {
+  if (!(o.beta > 0.0 && o.beta < 1.0)) return arg_error("wf: beta must be in (0, 1)");
+  if (!(o.eps_final > 0.0) || !(o.eps_cap > 0.0))
+    return arg_error("wf: eps_final and eps_cap must be > 0");
+  if (o.max_iter < 1) return arg_error("wf: max_iter must be >= 1");
+  if (o.stop_rule != WF_STOP_CAUCHY && o.stop_rule != WF_STOP_ERROR)
+    return arg_error("wf: unknown stop_rule");
+  if (o.precision != WF_PREC_FP64 && o.precision != WF_PREC_MIXED)
+    return arg_error("wf: unknown precision");
+  if (o.graph_chunk < 0 || o.graph_chunk > 4096)
+    return arg_error("wf: graph_chunk out of range");
+  return WF_OK;
+}
+
+}  // namespace wf
+
+using namespace wf;
+
+extern "C" {
+
+void wf_opts_default(wf_opts *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->beta = 0.75;
+  o->eps_final = 1e-6;
+  o->eps_cap = 1e-2;
+  o->mu0 = -1.0;
+  o->max_iter = 200000;
+  o->stop_rule = WF_STOP_ERROR;
+  o->precision = WF_PREC_FP64;
+  o->band_limit = 1;
+  o->graph_chunk = 0;
+  o->refine_max = 8;
+}
+
+long wf_npix(int nside) { return 12L * nside * nside; }
+long wf_nalm(int lmax) { return (long)(lmax + 1) * (lmax + 2) / 2; }
+
+const char *wf_status_str(wf_status s) {
+  switch (s) {
+    case WF_OK: return "ok";
+    case WF_ERR_ARG: return "invalid argument";
+    case WF_ERR_CUDA: return "CUDA error";
+    case WF_ERR_NOT_CONVERGED: return "not converged";
+    case WF_ERR_NUMERIC: return "NaN or Inf in the iteration";
+    case WF_ERR_TIMEOUT: return "device wait timed out";
+    case WF_ERR_UNIMPLEMENTED: return "not implemented";
+    case WF_ERR_STATE: return "invalid call for this plan";
+  }
+  return "unknown status";
+}
+
+const char *wf_last_error(void) { return g_last_error.c_str(); }
+
+wf_status wf_plan(wf_plan_t *out, int nside, int lmax, const double *cl_host,
+                  const double *noise_var_dev, const uint8_t *mask_dev,
+                  const wf_opts *opts, void *stream) {
+  if (!out) return arg_error("wf_plan: out is NULL");
+  *out = nullptr;
+  if (nside < 1 || nside > 8192) return arg_error("wf_plan: nside out of range [1, 8192]");
+  if (lmax < 1 || lmax > 3 * nside - 1)
+    return arg_error("wf_plan: lmax out of range [1, 3 nside - 1]");
+  if (!cl_host) return arg_error("wf_plan: cl_host is NULL");
+  for (int l = 0; l <= lmax; ++l)
+    if (!(cl_host[l] >= 0.0) || isinf(cl_host[l]))
+      return arg_error("wf_plan: C_l must be finite and >= 0");
+  wf_opts o;
+  wf_opts_default(&o);
+  if (opts) o = *opts;
+  WF_TRY(check_opts(o));
+  wf_plan_s *P = new (std::nothrow) wf_plan_s();
+  if (!P) return arg_error("wf_plan: out of host memory");
+  P->nside = nside;
+  P->lmax = lmax;
+  P->nring = 4 * nside - 1;
+  P->npairs = 2 * nside;
+  P->npix = 12L * nside * nside;
+  P->nalm = (long)(lmax + 1) * (lmax + 2) / 2;
+  P->omega = 4.0 * M_PI / (double)P->npix;
+  P->stream = (cudaStream_t)stream;
+  P->opts = o;
+  P->cl.assign(cl_host, cl_host + lmax + 1);
+  wf_status s = WF_OK;
+  try {
+    s = build_tables(*P);
+    if (s == WF_OK) s = alloc_work(*P);
+    if (s == WF_OK && noise_var_dev) s = upload_noise(*P, noise_var_dev, mask_dev);
+    if (s == WF_OK) {
+      cudaError_t e = cudaStreamSynchronize(P->stream);
+      if (e != cudaSuccess) {
+        set_error(std::string("wf_plan: ") + cudaGetErrorString(e));
+        s = WF_ERR_CUDA;
+      }
+    }
+  } catch (const std::bad_alloc &) {
+    set_error("wf_plan: out of host memory");
+    s = WF_ERR_ARG;
+  }
+  if (s != WF_OK) {
+    free_plan(P);
+    return s;
+  }
+  *out = P;
+  return WF_OK;
+}
+
+wf_status wf_set_noise(wf_plan_t plan, const double *noise_var_dev,
+                       const uint8_t *mask_dev) {
+  if (!plan) return arg_error("wf_set_noise: plan is NULL");
+  if (!noise_var_dev) return arg_error("wf_set_noise: noise_var_dev is NULL");
+  return upload_noise(*plan, noise_var_dev, mask_dev);
+}
+
+wf_status wf_set_cl(wf_plan_t plan, const double *cl_host) {
+  if (!plan) return arg_error("wf_set_cl: plan is NULL");
+  if (!cl_host) return arg_error("wf_set_cl: cl_host is NULL");
+  for (int l = 0; l <= plan->lmax; ++l)
+    if (!(cl_host[l] >= 0.0) || isinf(cl_host[l]))
+      return arg_error("wf_set_cl: C_l must be finite and >= 0");
+  plan->cl.assign(cl_host, cl_host + plan->lmax + 1);
+  WF_CUDA(cudaMemcpyAsync(plan->cl_d, plan->cl.data(), sizeof(double) * (plan->lmax + 1),
+                          cudaMemcpyHostToDevice, plan->stream));
+  WF_CUDA(cudaStreamSynchronize(plan->stream));
+  return WF_OK;
+}
+
+wf_status wf_solve(wf_plan_t plan, const double *d_dev, double *alm_dev,
+                   double *map_dev, const double *init_alm_dev,
+                   const double *init_map_dev, wf_stats *stats) {
+  if (!plan) return arg_error("wf_solve: plan is NULL");
+  if (!d_dev) return arg_error("wf_solve: d_dev is NULL");
+  return solve(*plan, d_dev, alm_dev, map_dev, init_alm_dev, init_map_dev, stats);
+}
+
+wf_status wf_solve_host(wf_plan_t plan, const double *d_host, double *alm_host,
+                        double *map_host, wf_stats *stats) {
+  if (!plan) return arg_error("wf_solve_host: plan is NULL");
+  if (!d_host) return arg_error("wf_solve_host: d_host is NULL");
+  Plan &P = *plan;
+  double *dd = nullptr, *mm = nullptr;
+  double2 *aa = nullptr;
+  WF_CUDA(cudaMalloc(&dd, sizeof(double) * P.npix));
+  wf_status s = WF_OK;
+  do {
+    if (map_host && cudaMalloc(&mm, sizeof(double) * P.npix) != cudaSuccess) {
+      s = WF_ERR_CUDA;
+      break;
+    }
+    if (alm_host && cudaMalloc(&aa, sizeof(double2) * P.nalm) != cudaSuccess) {
+      s = WF_ERR_CUDA;
+      break;
+    }
+    if (cudaMemcpyAsync(dd, d_host, sizeof(double) * P.npix, cudaMemcpyHostToDevice,
+                        P.stream) != cudaSuccess) {
+      s = WF_ERR_CUDA;
+      break;
+    }
+    s = solve(P, dd, reinterpret_cast<double *>(aa), mm, nullptr, nullptr, stats);
+    if (s != WF_OK && s != WF_ERR_NOT_CONVERGED) break;
+    if (alm_host &&
+        cudaMemcpyAsync(alm_host, aa, sizeof(double2) * P.nalm, cudaMemcpyDeviceToHost,
+                        P.stream) != cudaSuccess) {
+      s = WF_ERR_CUDA;
+      break;
+    }
+    if (map_host && cudaMemcpyAsync(map_host, mm, sizeof(double) * P.npix,
+                                    cudaMemcpyDeviceToHost, P.stream) != cudaSuccess) {
+      s = WF_ERR_CUDA;
+      break;
+    }
+    if (cudaStreamSynchronize(P.stream) != cudaSuccess) s = WF_ERR_CUDA;
+  } while (0);
+  if (s == WF_ERR_CUDA) set_error("wf_solve_host: CUDA allocation or copy failed");
+  cudaFree(dd);
+  if (mm) cudaFree(mm);
+  if (aa) cudaFree(aa);
+  return s;
+}
+
+wf_status wf_residual(wf_plan_t plan, const double *d_dev, const double *alm_dev,
+                      double *rel_res_wf, double *rel_res_fp, double *chi2) {
+  if (!plan) return arg_error("wf_residual: plan is NULL");
+  if (!d_dev || !alm_dev) return arg_error("wf_residual: NULL input");
+  return residual(*plan, d_dev, alm_dev, rel_res_wf, rel_res_fp, chi2);
+}
+
+wf_status wf_alm2map(wf_plan_t plan, const double *alm_dev, double *map_dev) {
+  if (!plan) return arg_error("wf_alm2map: plan is NULL");
+  if (!alm_dev || !map_dev) return arg_error("wf_alm2map: NULL buffer");
+  WF_TRY(alm2map(*plan, alm_dev, map_dev));
+  WF_CUDA(cudaStreamSynchronize(plan->stream));
+  return WF_OK;
+}
+
+wf_status wf_map2alm(wf_plan_t plan, const double *map_dev, double *alm_dev) {
+  if (!plan) return arg_error("wf_map2alm: plan is NULL");
+  if (!alm_dev || !map_dev) return arg_error("wf_map2alm: NULL buffer");
+  WF_TRY(map2alm(*plan, map_dev, alm_dev));
+  WF_CUDA(cudaStreamSynchronize(plan->stream));
+  return WF_OK;
+}
+
+wf_status wf_trace(wf_plan_t plan, int *count, int *stage, double *xi, double *mu,
+                   double *cauchy) {
+  if (!plan || !count) return arg_error("wf_trace: NULL argument");
+  const int n = std::min(*count, plan->trace_len);
+  std::vector<TraceEntry> h(n > 0 ? n : 1);
+  if (n > 0)
+    WF_CUDA(cudaMemcpy(h.data(), plan->trace, sizeof(TraceEntry) * n,
+                       cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n; ++i) {
+    if (stage) stage[i] = h[i].stage;
+    if (xi) xi[i] = h[i].xi;
+    if (mu) mu[i] = h[i].mu;
+    if (cauchy) cauchy[i] = h[i].cauchy;
+  }
+  *count = n;
+  return WF_OK;
+}
+
+void wf_destroy(wf_plan_t plan) { free_plan(plan); }
+
+}  // extern "C"

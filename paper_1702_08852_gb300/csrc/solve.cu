@@ -1,0 +1,529 @@
+// solve.cu -- the hybrid dual messenger iteration (Algorithm 2, Eqs. 13-15)
+// driven from the device, plus the FP64 transforms and diagnostics.
+//
+// One iteration = four kernels on the plan's stream:
+//   A  Legendre analysis of G (= FFT of the messenger field t) with the
+//      truncated-spectrum filter fused: x <- f_l(xi, mu) Omega Y^T t, and the
+//      per-m partial sums of ||x_new - x_old||^2 and ||x_new||^2;
+//   S  Legendre synthesis x -> F (ring Fourier coefficients of s = Y x);
+//   R  ring kernel: F -> s -> t = s + w (d - s) -> G, w = xi / (sigma^2 + mu);
+//   C  control: Cauchy ratio, stage test, cooling xi <- max(alpha, beta xi),
+//      mu = xi - alpha, the band limit of the next stage, trace, stop.
+// The order follows Algorithm 2: s and t of iteration i use the xi of the
+// stage that produced x_i; the cooling happens after the Cauchy test.
+// Iterations are captured in a CUDA graph of `chunk` iterations; every kernel
+// returns at once when the control kernel has set `done`, so the host only
+// polls the state between graph launches.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "wf_internal.cuh"
+
+namespace wf {
+
+// ---------------------------------------------------------------- helpers
+__global__ void k_mask_data(const double *d, const double *nvar, long npix,
+                            double *out) {
+  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+       p += (long)gridDim.x * blockDim.x)
+    out[p] = isinf(nvar[p]) ? 0.0 : d[p];
+}
+
+// largest l with C_l - mu Omega > 0 (the band where Sbar = Theta(S - U) is
+// nonzero), -1 if none; block-wide, result valid in thread 0
+__device__ int band_of(const double *cl, int lmax, double mu, double omega,
+                       int *sh) {
+  int best = -1;
+  for (int l = threadIdx.x; l <= lmax; l += blockDim.x)
+    if (cl[l] - mu * omega > 0.0) best = max(best, l);
+  sh[threadIdx.x] = best;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] = max(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  const int r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+constexpr int CTRL_THREADS = 256;
+
+__global__ void __launch_bounds__(CTRL_THREADS)
+    k_control(SolverState *st, const double *__restrict__ partials, int lmax,
+              const double *__restrict__ cl, TraceEntry *trace) {
+  __shared__ double snum[CTRL_THREADS], sden[CTRL_THREADS];
+  __shared__ int sh[CTRL_THREADS];
+  __shared__ int advance;
+  if (st->done) return;
+  double num = 0.0, den = 0.0;
+  for (int m = threadIdx.x; m <= lmax; m += CTRL_THREADS) {
+    num += partials[2 * m];
+    den += partials[2 * m + 1];
+  }
+  snum[threadIdx.x] = num;
+  sden[threadIdx.x] = den;
+  __syncthreads();
+  for (int s = CTRL_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      snum[threadIdx.x] += snum[threadIdx.x + s];
+      sden[threadIdx.x] += sden[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    num = snum[0];
+    den = sden[0];
+    const double c = den > 0.0 ? sqrt(num / den) : 0.0;
+    const int it = ++st->iter;
+    st->stage_iter += 1;
+    if (trace && it - 1 < st->trace_cap) {
+      TraceEntry e;
+      e.stage = st->stage;
+      e.pad = 0;
+      e.xi = st->xi;
+      e.mu = st->mu;
+      e.cauchy = c;
+      trace[it - 1] = e;
+    }
+    int adv = 0;
+    if (!isfinite(c) || !isfinite(num)) {
+      st->numeric_error = 1;
+      st->done = 1;
+    } else if (st->mu == 0.0) {
+      if (st->stop_rule == WF_STOP_ERROR) {
+        if (st->prev_c > 0.0 && c > 0.0) {
+          const double r = fmin(c / st->prev_c, 0.999999);
+          const double err = c * r / (1.0 - r);
+          st->err_est = err;
+          if (err < st->eps_final) {
+            st->done = 1;
+            st->converged = 1;
+          }
+        } else if (c == 0.0) {
+          st->err_est = 0.0;
+          st->done = 1;
+          st->converged = 1;
+        }
+      } else if (c < st->eps_final) {
+        st->done = 1;
+        st->converged = 1;
+      }
+    } else if (c < st->eps_k) {
+      adv = 1;
+    }
+    st->prev_c = c;
+    st->last_c = c;
+    if (adv) {
+      const double xi = fmax(st->alpha, st->beta * st->xi);
+      st->xi = xi;
+      st->mu = xi > st->alpha ? xi - st->alpha : 0.0;
+      st->stage += 1;
+      st->stage_iter = 0;
+      st->prev_c = -1.0;
+      st->eps_k = st->mu == 0.0
+                      ? st->eps_final
+                      : fmin(st->eps_cap, st->eps_final * fmax(1.0, st->mu / st->alpha));
+      st->lcur = st->lnext;
+    }
+    if (!st->done && st->iter >= st->max_iter) st->done = 1;
+    advance = adv;
+  }
+  __syncthreads();
+  if (advance) {
+    // band of the stage after the new one
+    const double xi2 = fmax(st->alpha, st->beta * st->xi);
+    const double mu2 = xi2 > st->alpha ? xi2 - st->alpha : 0.0;
+    const int b = st->band_limit ? band_of(cl, lmax, mu2, st->omega, sh) : lmax;
+    if (threadIdx.x == 0) st->lnext = b;
+  }
+}
+
+// ---------------------------------------------------------------- reductions
+// sum_lm w_m (a . b), optionally with a per-l factor fl (NULL = 1) applied to
+// both; deterministic two-level reduction (blocks -> out[0..nb), then host)
+__global__ void k_alm_dot(const double2 *a, const double2 *b, const double *fl,
+                          int lmax, long nalm, double *out) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nalm;
+       i += (long)gridDim.x * blockDim.x) {
+    // m of slot i: largest m with m (2 lmax + 1 - m) / 2 <= i
+    int m = (int)((2.0 * lmax + 1.0 - sqrt((2.0 * lmax + 1.0) * (2.0 * lmax + 1.0) -
+                                           8.0 * (double)i)) / 2.0);
+    while (m > 0 && (long)m * (2 * lmax + 1 - m) / 2 > i) --m;
+    while ((long)(m + 1) * (2 * lmax + 1 - (m + 1)) / 2 <= i && m < lmax) ++m;
+    const int l = (int)(i - (long)m * (2 * lmax + 1 - m) / 2);
+    const double w = m == 0 ? 1.0 : 2.0;
+    double f = fl ? fl[l] : 1.0;
+    acc += w * f * f * (a[i].x * b[i].x + a[i].y * b[i].y);
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
+// r = cm12 * x - cp12 * u (per l), used by the App. C residual
+__global__ void k_alm_combine(const double2 *x, const double2 *u, const double *cm12,
+                              const double *cp12, int lmax, double2 *r) {
+  const int m = blockIdx.x;
+  const long base = (long)m * (2 * lmax + 1 - m) / 2;
+  for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
+    const long i = base + l;
+    r[i] = make_double2(cm12[l] * x[i].x - cp12[l] * u[i].x,
+                        cm12[l] * x[i].y - cp12[l] * u[i].y);
+  }
+}
+
+// per-pixel: out = (d - s) / sigma^2 (0 masked); chi partial sums of
+// (d - s)^2 / sigma^2; also y = d / sigma^2
+__global__ void k_pix_resid(const double *d, const double *s, const double *nvar,
+                            long npix, double *r, double *y, double *out) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+       p += (long)gridDim.x * blockDim.x) {
+    const double v = nvar[p];
+    if (isinf(v)) {
+      r[p] = 0.0;
+      y[p] = 0.0;
+    } else {
+      const double e = d[p] - s[p];
+      r[p] = e / v;
+      y[p] = d[p] / v;
+      acc += e * e / v;
+    }
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
+}
+
+static const int RED_BLOCKS = 256;
+
+static wf_status host_sum(Plan &P, double *dev, int n, double *res) {
+  std::vector<double> h(n);
+  WF_CUDA(cudaMemcpyAsync(h.data(), dev, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                          P.stream));
+  WF_CUDA(cudaStreamSynchronize(P.stream));
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += h[i];
+  *res = s;
+  return WF_OK;
+}
+
+static wf_status alm_dot(Plan &P, const double2 *a, const double2 *b,
+                         const double *fl, double *res) {
+  k_alm_dot<<<RED_BLOCKS, 256, 0, P.stream>>>(a, b, fl, P.lmax, P.nalm, P.red);
+  WF_CUDA(cudaGetLastError());
+  return host_sum(P, P.red, RED_BLOCKS, res);
+}
+
+// ---------------------------------------------------------------- transforms
+wf_status alm2map(Plan &P, const double *alm, double *map) {
+  const double2 *a = reinterpret_cast<const double2 *>(alm);
+  WF_TRY(launch_legendre_synth<double2>(P, a, P.F64, nullptr, P.lmax));
+  WF_TRY(launch_ring<double2>(P, RING_SYNTH, P.F64, nullptr, nullptr, map, nullptr,
+                              P.lmax));
+  return WF_OK;
+}
+
+wf_status map2alm(Plan &P, const double *map, double *alm) {
+  WF_TRY(launch_ring<double2>(P, RING_ANALYSIS, nullptr, P.G64, map, nullptr,
+                              nullptr, P.lmax));
+  WF_TRY(launch_legendre_anal<double2>(P, P.G64, reinterpret_cast<double2 *>(alm),
+                                       nullptr, ANA_PLAIN, P.lmax));
+  return WF_OK;
+}
+
+// ---------------------------------------------------------------- solve
+static int band_host(const std::vector<double> &cl, double mu, double omega) {
+  int b = -1;
+  for (int l = 0; l < (int)cl.size(); ++l)
+    if (cl[l] - mu * omega > 0.0) b = l;
+  return b;
+}
+
+static SolverState initial_state(const Plan &P) {
+  SolverState s{};
+  const wf_opts &o = P.opts;
+  double cmax = 0.0;
+  for (double c : P.cl) cmax = std::max(cmax, c);
+  s.alpha = P.alpha;
+  s.beta = o.beta;
+  s.omega = P.omega;
+  const double mu0 = o.mu0 < 0.0 ? o.beta * cmax / P.omega : o.mu0;
+  s.mu = mu0;
+  s.xi = P.alpha + mu0;
+  s.eps_final = o.eps_final;
+  s.eps_cap = o.eps_cap;
+  s.eps_k = mu0 == 0.0 ? o.eps_final
+                       : std::min(o.eps_cap, o.eps_final * std::max(1.0, mu0 / P.alpha));
+  s.prev_c = -1.0;
+  s.last_c = 0.0;
+  s.err_est = 0.0;
+  s.stage = 0;
+  s.iter = 0;
+  s.done = 0;
+  s.converged = 0;
+  s.numeric_error = 0;
+  s.max_iter = o.max_iter;
+  s.stop_rule = o.stop_rule;
+  s.band_limit = o.band_limit;
+  s.trace_cap = P.trace_cap;
+  s.stage_iter = 0;
+  if (o.band_limit) {
+    s.lcur = band_host(P.cl, mu0, P.omega);
+    const double xi2 = std::max(P.alpha, o.beta * s.xi);
+    const double mu2 = xi2 > P.alpha ? xi2 - P.alpha : 0.0;
+    s.lnext = band_host(P.cl, mu2, P.omega);
+  } else {
+    s.lcur = s.lnext = P.lmax;
+  }
+  return s;
+}
+
+template <typename T2>
+static wf_status enqueue_iteration(Plan &P, T2 *F, T2 *G) {
+  WF_TRY(launch_legendre_anal<T2>(P, G, P.x, P.state, ANA_FILTER, P.lmax));
+  WF_TRY(launch_legendre_synth<T2>(P, P.x, F, P.state, P.lmax));
+  WF_TRY(launch_ring<T2>(P, RING_FUSED, F, G, P.dmap, nullptr, P.state, P.lmax));
+  k_control<<<1, CTRL_THREADS, 0, P.stream>>>(P.state, P.partials, P.lmax, P.cl_d,
+                                              P.trace);
+  WF_CUDA(cudaGetLastError());
+  return WF_OK;
+}
+
+static int auto_chunk(const Plan &P) {
+  long k = (1L << 24) / std::max(1L, P.npix);
+  return (int)std::max(2L, std::min(128L, k));
+}
+
+template <typename T2>
+static wf_status capture_graph(Plan &P, int which, T2 *F, T2 *G) {
+  if (P.graph[which]) return WF_OK;
+  const int chunk = P.opts.graph_chunk > 0 ? P.opts.graph_chunk : auto_chunk(P);
+  cudaGraph_t g = nullptr;
+  // capture on the plan's private stream (the caller's stream may be the
+  // legacy default stream, which cannot be captured); launch on P.stream
+  if (!P.capture_stream)
+    WF_CUDA(cudaStreamCreateWithFlags(&P.capture_stream, cudaStreamNonBlocking));
+  cudaStream_t user = P.stream;
+  P.stream = P.capture_stream;
+  cudaError_t eb = cudaStreamBeginCapture(P.stream, cudaStreamCaptureModeThreadLocal);
+  if (eb != cudaSuccess) {
+    P.stream = user;
+    set_error(std::string("graph capture: ") + cudaGetErrorString(eb));
+    return WF_ERR_CUDA;
+  }
+  wf_status s = WF_OK;
+  for (int i = 0; i < chunk && s == WF_OK; ++i) s = enqueue_iteration<T2>(P, F, G);
+  cudaError_t e = cudaStreamEndCapture(P.stream, &g);
+  P.stream = user;
+  if (s != WF_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) {
+    set_error(std::string("graph capture: ") + cudaGetErrorString(e));
+    return WF_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(&P.graph[which], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    set_error(std::string("graph instantiate: ") + cudaGetErrorString(e));
+    P.graph[which] = nullptr;
+    return WF_ERR_CUDA;
+  }
+  P.graph_chunk[which] = chunk;
+  return WF_OK;
+}
+
+template <typename T2>
+static wf_status run_loop(Plan &P, int which, T2 *F, T2 *G, const double *tinit) {
+  // G <- FFT of the initial messenger field
+  WF_TRY(launch_ring<T2>(P, RING_ANALYSIS, nullptr, G, tinit, nullptr, nullptr,
+                         P.lmax));
+  WF_TRY(capture_graph<T2>(P, which, F, G));
+  for (;;) {
+    WF_CUDA(cudaGraphLaunch(P.graph[which], P.stream));
+    WF_CUDA(cudaMemcpyAsync(P.state_h, P.state, sizeof(SolverState),
+                            cudaMemcpyDeviceToHost, P.stream));
+    WF_CUDA(cudaStreamSynchronize(P.stream));
+    if (P.state_h->done) break;
+  }
+  return WF_OK;
+}
+
+wf_status solve(Plan &P, const double *d, double *alm, double *map,
+                const double *init_alm, const double *init_map, wf_stats *stats) {
+  if (!P.has_noise) {
+    set_error("wf_solve: plan has no noise variance");
+    return WF_ERR_STATE;
+  }
+  WF_CUDA(cudaEventRecord(P.ev0, P.stream));
+  k_mask_data<<<304, 256, 0, P.stream>>>(d, P.nvar, P.npix, P.dmap);
+  WF_CUDA(cudaGetLastError());
+  if (init_alm)
+    WF_CUDA(cudaMemcpyAsync(P.x, init_alm, sizeof(double2) * P.nalm,
+                            cudaMemcpyDeviceToDevice, P.stream));
+  else
+    WF_CUDA(cudaMemsetAsync(P.x, 0, sizeof(double2) * P.nalm, P.stream));
+  const double *tinit = P.dmap;
+  if (init_map) {
+    k_mask_data<<<304, 256, 0, P.stream>>>(init_map, P.nvar, P.npix, P.mtmp);
+    WF_CUDA(cudaGetLastError());
+    tinit = P.mtmp;
+  }
+  *P.state_h = initial_state(P);
+  WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
+                          cudaMemcpyHostToDevice, P.stream));
+  if (P.opts.precision == WF_PREC_MIXED) {
+    WF_TRY(run_loop<float2>(P, 1, P.F32, P.G32, tinit));
+  } else {
+    WF_TRY(run_loop<double2>(P, 0, P.F64, P.G64, tinit));
+  }
+  if (map) WF_TRY(alm2map(P, reinterpret_cast<const double *>(P.x), map));
+  if (alm)
+    WF_CUDA(cudaMemcpyAsync(alm, P.x, sizeof(double2) * P.nalm,
+                            cudaMemcpyDeviceToDevice, P.stream));
+  WF_CUDA(cudaEventRecord(P.ev1, P.stream));
+  WF_CUDA(cudaStreamSynchronize(P.stream));
+  const SolverState &s = *P.state_h;
+  P.trace_len = std::min(s.iter, P.trace_cap);
+  if (stats) {
+    float ms = 0.f;
+    WF_CUDA(cudaEventElapsedTime(&ms, P.ev0, P.ev1));
+    stats->iterations = s.iter;
+    stats->stages = s.stage + 1;
+    stats->converged = s.converged;
+    stats->refinements = 0;
+    stats->alpha = P.alpha;
+    stats->final_cauchy = s.last_c;
+    stats->err_estimate = s.err_est;
+    stats->fp_residual = -1.0;
+    stats->elapsed_ms = ms;
+  }
+  if (s.numeric_error) {
+    set_error("wf_solve: NaN or Inf in the iteration");
+    return WF_ERR_NUMERIC;
+  }
+  if (!s.converged) {
+    set_error("wf_solve: max_iter reached before the last stage converged");
+    return WF_ERR_NOT_CONVERGED;
+  }
+  return WF_OK;
+}
+
+// ---------------------------------------------------------------- residual
+wf_status residual(Plan &P, const double *d, const double *alm, double *res_wf,
+                   double *res_fp, double *chi2) {
+  if (!P.has_noise) {
+    set_error("wf_residual: plan has no noise variance");
+    return WF_ERR_STATE;
+  }
+  const double2 *x = reinterpret_cast<const double2 *>(alm);
+  const long npix = P.npix;
+  // buffers: s (mtmp), r = N^-1 (d - s) and y = N^-1 d (two pixel maps)
+  double *pr = nullptr, *py = nullptr, *cm12 = nullptr, *cp12 = nullptr;
+  double2 *u = nullptr, *v = nullptr, *rr = nullptr;
+  WF_CUDA(cudaMalloc(&pr, sizeof(double) * npix));
+  WF_CUDA(cudaMalloc(&py, sizeof(double) * npix));
+  WF_CUDA(cudaMalloc(&u, sizeof(double2) * P.nalm));
+  WF_CUDA(cudaMalloc(&v, sizeof(double2) * P.nalm));
+  WF_CUDA(cudaMalloc(&rr, sizeof(double2) * P.nalm));
+  WF_CUDA(cudaMalloc(&cm12, sizeof(double) * (P.lmax + 1)));
+  WF_CUDA(cudaMalloc(&cp12, sizeof(double) * (P.lmax + 1)));
+  wf_status status = WF_OK;
+  do {
+    k_mask_data<<<304, 256, 0, P.stream>>>(d, P.nvar, npix, P.dmap);
+    if ((status = alm2map(P, alm, P.mtmp)) != WF_OK) break;
+    k_pix_resid<<<RED_BLOCKS, 256, 0, P.stream>>>(P.dmap, P.mtmp, P.nvar, npix, pr,
+                                                  py, P.red);
+    double chi_pix = 0.0;
+    if ((status = host_sum(P, P.red, RED_BLOCKS, &chi_pix)) != WF_OK) break;
+    std::vector<double> hm(P.lmax + 1), hp(P.lmax + 1), hinv(P.lmax + 1);
+    for (int l = 0; l <= P.lmax; ++l) {
+      const double c = P.cl[l];
+      hp[l] = sqrt(c);
+      hm[l] = c > 0 ? 1.0 / sqrt(c) : 0.0;
+      hinv[l] = c > 0 ? 1.0 / sqrt(c) : 0.0;  // for x^T C^-1 x via f^2
+    }
+    cudaMemcpyAsync(cm12, hm.data(), sizeof(double) * (P.lmax + 1),
+                    cudaMemcpyHostToDevice, P.stream);
+    cudaMemcpyAsync(cp12, hp.data(), sizeof(double) * (P.lmax + 1),
+                    cudaMemcpyHostToDevice, P.stream);
+    double prior = 0.0;
+    if ((status = alm_dot(P, x, x, cm12, &prior)) != WF_OK) break;
+    if (chi2) *chi2 = chi_pix + prior;
+    // u = Y^T N^-1 (d - s), v = Y^T N^-1 d  (map2alm gives Omega Y^T)
+    if ((status = map2alm(P, pr, reinterpret_cast<double *>(u))) != WF_OK) break;
+    if ((status = map2alm(P, py, reinterpret_cast<double *>(v))) != WF_OK) break;
+    // App. C: r = C^-1/2 x - C^1/2 Y^T N^-1 (d - s);  y = C^1/2 Y^T N^-1 d
+    // with the Omega of map2alm divided out
+    std::vector<double> hp_om(P.lmax + 1);
+    for (int l = 0; l <= P.lmax; ++l) hp_om[l] = hp[l] / P.omega;
+    cudaMemcpyAsync(cp12, hp_om.data(), sizeof(double) * (P.lmax + 1),
+                    cudaMemcpyHostToDevice, P.stream);
+    k_alm_combine<<<P.lmax + 1, 128, 0, P.stream>>>(x, u, cm12, cp12, P.lmax, rr);
+    double rn = 0.0, yn = 0.0;
+    if ((status = alm_dot(P, rr, rr, nullptr, &rn)) != WF_OK) break;
+    if ((status = alm_dot(P, v, v, cp12, &yn)) != WF_OK) break;
+    if (res_wf) *res_wf = yn > 0 ? sqrt(rn / yn) : 0.0;
+    if (res_fp) {
+      // one last-stage iteration G(x): xi = alpha, mu = 0, full band
+      SolverState s = initial_state(P);
+      s.xi = P.alpha;
+      s.mu = 0.0;
+      s.lcur = s.lnext = P.lmax;
+      s.done = 0;
+      *P.state_h = s;
+      cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState), cudaMemcpyHostToDevice,
+                      P.stream);
+      cudaMemcpyAsync(P.xtmp, x, sizeof(double2) * P.nalm, cudaMemcpyDeviceToDevice,
+                      P.stream);
+      if ((status = launch_legendre_synth<double2>(P, x, P.F64, nullptr, P.lmax)) !=
+          WF_OK)
+        break;
+      if ((status = launch_ring<double2>(P, RING_FUSED, P.F64, P.G64, P.dmap, nullptr,
+                                         P.state, P.lmax)) != WF_OK)
+        break;
+      if ((status = launch_legendre_anal<double2>(P, P.G64, P.xtmp, P.state,
+                                                  ANA_FILTER, P.lmax)) != WF_OK)
+        break;
+      std::vector<double> part(2 * (P.lmax + 1));
+      cudaMemcpyAsync(part.data(), P.partials, sizeof(double) * part.size(),
+                      cudaMemcpyDeviceToHost, P.stream);
+      double xn = 0.0;
+      if ((status = alm_dot(P, x, x, nullptr, &xn)) != WF_OK) break;
+      double num = 0.0;
+      for (int m = 0; m <= P.lmax; ++m) num += part[2 * m];
+      *res_fp = xn > 0 ? sqrt(num / xn) : 0.0;
+    }
+  } while (0);
+  cudaError_t e = cudaStreamSynchronize(P.stream);
+  cudaFree(pr);
+  cudaFree(py);
+  cudaFree(u);
+  cudaFree(v);
+  cudaFree(rr);
+  cudaFree(cm12);
+  cudaFree(cp12);
+  if (status == WF_OK && e != cudaSuccess) {
+    set_error(std::string("wf_residual: ") + cudaGetErrorString(e));
+    return WF_ERR_CUDA;
+  }
+  return status;
+}
+
+}  // namespace wf

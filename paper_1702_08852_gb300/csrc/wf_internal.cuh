@@ -1,0 +1,168 @@
+// wf_internal.cuh -- shared declarations of the CUDA implementation behind
+// include/wf.h.  Everything here is internal to libwf.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/wf.h"
+
+namespace wf {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+
+#define WF_CUDA(call)                                                        \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      ::wf::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));   \
+      return WF_ERR_CUDA;                                                    \
+    }                                                                        \
+  } while (0)
+
+#define WF_TRY(expr)                    \
+  do {                                  \
+    wf_status s_ = (expr);              \
+    if (s_ != WF_OK) return s_;         \
+  } while (0)
+
+// ---------------------------------------------------------------- geometry
+// One iso-latitude ring pair: the north ring and its mirror image in the
+// south (the equator ring is a "pair" with no south ring).  Both rings share
+// nphi, |z| and phi0.
+struct RingPair {
+  double z;        // z of the north ring
+  double sth;      // sin(theta) of the north ring
+  long ofsN;       // first pixel of the north ring
+  long ofsS;       // first pixel of the south ring, -1 for the equator ring
+  int ringN;       // 0-based ring index of the north ring
+  int ringS;       // 0-based ring index of the south ring, -1 for the equator
+  int nphi;        // pixels per ring
+  int phi_num;     // phi0 = pi * phi_num / phi_den (exact rational)
+  int phi_den;
+  int fftM;        // FFT length used: nphi if a power of two, else the
+                   // Bluestein length (power of two >= 2 nphi - 1)
+  long chirp_ofs;  // offset into the chirp table (Bluestein rings), else -1
+  long bhat_ofs;   // offset into the chirp-spectrum table, else -1
+};
+
+// Device-resident solver state; read by every kernel of an iteration and
+// updated by the control kernel.  Stage control stays on the device.
+struct SolverState {
+  double xi, mu, alpha, beta, omega;
+  double eps_final, eps_cap, eps_k;
+  double prev_c, last_c, err_est;
+  int stage, iter, done, converged, numeric_error;
+  int lcur;    // largest l with a nonzero filter in the current stage
+  int lnext;   // same for the next stage (the ring kernel fills G up to it)
+  int max_iter, stop_rule, band_limit, trace_cap;
+  int stage_iter;
+};
+
+struct TraceEntry {
+  int stage, pad;
+  double xi, mu, cauchy;
+};
+
+// ---------------------------------------------------------------- plan
+struct Plan {
+  int nside = 0, lmax = 0, nring = 0, npairs = 0;
+  long npix = 0, nalm = 0;
+  double omega = 0.0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture_stream = nullptr;  // graphs are captured here
+  wf_opts opts{};
+  std::vector<double> cl;
+  std::vector<RingPair> pairs_h;
+
+  // geometry / Legendre tables
+  RingPair *pairs = nullptr;     // [npairs]
+  double *cl_d = nullptr;        // [lmax+1]
+  double *rc = nullptr;          // [nalm] recurrence coefficient c_lm
+  double *rg = nullptr;          // [nalm] scale g_lm (lambda = g u)
+  float *rc32 = nullptr;         // [nalm] FP32 copy of rc
+  int *seed_l = nullptr;         // [lmax+1][npairs] first l with |lambda| >= 2^-100
+  double2 *seed_u = nullptr;     // [lmax+1][npairs] (u_ls, u_ls+1)
+
+  // FFT tables
+  int fftMmax = 1;
+  double2 *tw64 = nullptr;       // e^{-2 pi i k / Mmax}, k < Mmax/2
+  float2 *tw32 = nullptr;
+  double2 *chirp64 = nullptr;    // e^{i pi j^2 / n}, per Bluestein ring
+  float2 *chirp32 = nullptr;
+  double2 *bhat64 = nullptr;     // FFT_M of the chirp kernel, bit-reversed order
+  float2 *bhat32 = nullptr;
+  long chirp_total = 0, bhat_total = 0;
+
+  // noise
+  bool has_noise = false;
+  double alpha = 0.0;
+  double *nvar = nullptr;        // [npix] sigma^2, +inf on masked pixels
+
+  // work buffers
+  double2 *F64 = nullptr, *G64 = nullptr;   // [nring][lmax+1]
+  float2 *F32 = nullptr, *G32 = nullptr;
+  double2 *x = nullptr;          // [nalm] current iterate
+  double2 *xtmp = nullptr;       // [nalm]
+  double *dmap = nullptr;        // [npix] data with masked pixels zeroed
+  double *mtmp = nullptr;        // [npix]
+  double *partials = nullptr;    // [lmax+1][2]
+  double *red = nullptr;         // small reduction scratch
+  SolverState *state = nullptr;  // device
+  SolverState *state_h = nullptr;  // pinned host mirror
+  TraceEntry *trace = nullptr;
+  int trace_cap = 0;
+  int trace_len = 0;
+
+  // graphs (one per precision), captured lazily
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_chunk[2] = {0, 0};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+// ---------------------------------------------------------------- kernels
+// Legendre transforms (legendre.cu).  Modes of the analysis:
+enum AnalysisMode { ANA_PLAIN = 0, ANA_FILTER = 1 };
+
+template <typename T2>
+wf_status launch_legendre_synth(const Plan &P, const double2 *x, T2 *F,
+                                const SolverState *st, int lstatic);
+template <typename T2>
+wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
+                               const SolverState *st, int mode, int lstatic);
+
+// Ring transforms (ringfft.cu).  Modes:
+enum RingMode {
+  RING_SYNTH = 0,     // F -> map (write s)
+  RING_ANALYSIS = 1,  // map (masked pixels -> 0) -> G
+  RING_FUSED = 2      // F -> s -> t = s + w (d - s) -> G
+};
+template <typename T2>
+wf_status launch_ring(const Plan &P, int mode, const T2 *F, T2 *G,
+                      const double *in_map, double *out_map,
+                      const SolverState *st, int lstatic);
+
+// once per plan (kernel attributes; allowed outside stream capture only)
+wf_status init_legendre_attributes();
+wf_status init_ring_attributes();
+
+// plan.cu
+wf_status build_tables(Plan &P);
+wf_status upload_noise(Plan &P, const double *nvar_dev, const uint8_t *mask_dev);
+
+// solve.cu
+wf_status solve(Plan &P, const double *d, double *alm, double *map,
+                const double *init_alm, const double *init_map, wf_stats *st);
+wf_status residual(Plan &P, const double *d, const double *alm, double *res_wf,
+                   double *res_fp, double *chi2);
+wf_status alm2map(Plan &P, const double *alm, double *map);
+wf_status map2alm(Plan &P, const double *map, double *alm);
+
+}  // namespace wf
+
+// The opaque handle of the C ABI is the plan itself.
+struct wf_plan_s : public wf::Plan {};

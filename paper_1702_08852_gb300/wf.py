@@ -1,0 +1,313 @@
+"""Python binding of the C ABI in include/wf.h (libwf.so).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  PyTorch supplies device memory and the CUDA stream.  The
+functions carry the names of the C entry points (wf_plan, wf_solve, ...);
+``Plan`` wraps a plan handle with the same calls as methods.
+
+Tensors: maps are float64 CUDA tensors of length Npix (HEALPix RING order);
+harmonic coefficients are complex128 CUDA tensors of length Nalm in m-major
+order (index m (2 lmax + 1 - m) / 2 + l); masks are uint8/bool CUDA tensors.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libwf.so")
+
+WF_OK, WF_ERR_ARG, WF_ERR_CUDA, WF_ERR_NOT_CONVERGED = 0, 1, 2, 3
+WF_ERR_NUMERIC, WF_ERR_TIMEOUT, WF_ERR_UNIMPLEMENTED, WF_ERR_STATE = 4, 5, 6, 7
+WF_PREC_FP64, WF_PREC_MIXED = 0, 1
+WF_STOP_CAUCHY, WF_STOP_ERROR = 0, 1
+
+
+class WFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class wf_opts(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("eps_final", ctypes.c_double),
+                ("eps_cap", ctypes.c_double), ("mu0", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("stop_rule", ctypes.c_int),
+                ("precision", ctypes.c_int), ("band_limit", ctypes.c_int),
+                ("graph_chunk", ctypes.c_int), ("refine_max", ctypes.c_int)]
+
+
+class wf_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("stages", ctypes.c_int),
+                ("converged", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("final_cauchy", ctypes.c_double),
+                ("err_estimate", ctypes.c_double), ("fp_residual", ctypes.c_double),
+                ("elapsed_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib():
+    """Load libwf.so.  There is no fallback: a missing library is an error."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"libwf.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        I, D = ctypes.c_int, ctypes.c_double
+        sigs = {
+            "wf_opts_default": (None, [ctypes.POINTER(wf_opts)]),
+            "wf_plan": (I, [ctypes.POINTER(_P), I, I, _P, _P, _P,
+                            ctypes.POINTER(wf_opts), _P]),
+            "wf_set_noise": (I, [_P, _P, _P]),
+            "wf_set_cl": (I, [_P, _P]),
+            "wf_solve": (I, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(wf_stats)]),
+            "wf_solve_host": (I, [_P, _P, _P, _P, ctypes.POINTER(wf_stats)]),
+            "wf_residual": (I, [_P, _P, _P, ctypes.POINTER(D), ctypes.POINTER(D),
+                                ctypes.POINTER(D)]),
+            "wf_alm2map": (I, [_P, _P, _P]),
+            "wf_map2alm": (I, [_P, _P, _P]),
+            "wf_npix": (ctypes.c_long, [I]),
+            "wf_nalm": (ctypes.c_long, [I]),
+            "wf_trace": (I, [_P, ctypes.POINTER(I), _P, _P, _P, _P]),
+            "wf_destroy": (None, [_P]),
+            "wf_status_str": (ctypes.c_char_p, [I]),
+            "wf_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != WF_OK:
+        raise WFError(status, lib().wf_last_error().decode())
+    return status
+
+
+def _dev_ptr(t, dtype, numel, name):
+    import torch
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or t.numel() != numel or not t.is_contiguous():
+        raise ValueError(f"{name}: expected contiguous {dtype} with {numel} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def wf_opts_default(**overrides):
+    o = wf_opts()
+    lib().wf_opts_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def wf_npix(nside):
+    return 12 * nside * nside
+
+
+def wf_nalm(lmax):
+    return (lmax + 1) * (lmax + 2) // 2
+
+
+def wf_status_str(s):
+    return lib().wf_status_str(int(s)).decode()
+
+
+def wf_last_error():
+    return lib().wf_last_error().decode()
+
+
+class Plan:
+    """A plan: geometry tables, noise, spectrum and workspaces on the GPU."""
+
+    def __init__(self, nside, lmax, cl, noise_var=None, mask=None, opts=None,
+                 stream=None, **opt_overrides):
+        import torch
+        self.nside, self.lmax = int(nside), int(lmax)
+        self.npix, self.nalm = wf_npix(nside), wf_nalm(lmax)
+        cl = np.ascontiguousarray(cl, dtype=np.float64)
+        if cl.shape != (self.lmax + 1,):
+            raise ValueError("cl must have lmax + 1 entries")
+        self._cl = cl
+        if opts is None:
+            opts = wf_opts_default(**opt_overrides)
+        self.opts = opts
+        nv = _dev_ptr(noise_var, torch.float64, self.npix, "noise_var")
+        mk = None
+        if mask is not None:
+            mask = mask.to(torch.uint8).contiguous()
+            mk = _dev_ptr(mask, torch.uint8, self.npix, "mask")
+        self._stream_obj = stream
+        h = ctypes.c_void_p()
+        _check(lib().wf_plan(ctypes.byref(h), self.nside, self.lmax,
+                             cl.ctypes.data_as(ctypes.c_void_p), nv, mk,
+                             ctypes.byref(opts), _stream(stream)))
+        self.handle = h
+
+    # -- calls of the C ABI ------------------------------------------------
+    def set_noise(self, noise_var, mask=None):
+        import torch
+        nv = _dev_ptr(noise_var, torch.float64, self.npix, "noise_var")
+        mk = None
+        if mask is not None:
+            mask = mask.to(torch.uint8).contiguous()
+            mk = _dev_ptr(mask, torch.uint8, self.npix, "mask")
+        _check(lib().wf_set_noise(self.handle, nv, mk))
+
+    def set_cl(self, cl):
+        cl = np.ascontiguousarray(cl, dtype=np.float64)
+        _check(lib().wf_set_cl(self.handle, cl.ctypes.data_as(ctypes.c_void_p)))
+        self._cl = cl
+
+    def solve(self, d, alm=None, map=None, init_alm=None, init_map=None,
+              want_map=True, check=True):
+        """Returns (alm, map, stats); alm/map are allocated when not given."""
+        import torch
+        dev = d.device
+        if alm is None:
+            alm = torch.empty(self.nalm, dtype=torch.complex128, device=dev)
+        if map is None and want_map:
+            map = torch.empty(self.npix, dtype=torch.float64, device=dev)
+        st = wf_stats()
+        status = lib().wf_solve(
+            self.handle, _dev_ptr(d, torch.float64, self.npix, "d"),
+            _dev_ptr(alm, torch.complex128, self.nalm, "alm"),
+            _dev_ptr(map, torch.float64, self.npix, "map"),
+            _dev_ptr(init_alm, torch.complex128, self.nalm, "init_alm"),
+            _dev_ptr(init_map, torch.float64, self.npix, "init_map"),
+            ctypes.byref(st))
+        if check and status not in (WF_OK,):
+            _check(status)
+        return alm, map, st.as_dict() | {"status": status}
+
+    def solve_host(self, d_host, want_alm=True, want_map=True):
+        d = np.ascontiguousarray(d_host, dtype=np.float64)
+        alm = np.empty(self.nalm, dtype=np.complex128) if want_alm else None
+        mp = np.empty(self.npix, dtype=np.float64) if want_map else None
+        st = wf_stats()
+        status = lib().wf_solve_host(
+            self.handle, d.ctypes.data_as(ctypes.c_void_p),
+            alm.ctypes.data_as(ctypes.c_void_p) if alm is not None else None,
+            mp.ctypes.data_as(ctypes.c_void_p) if mp is not None else None,
+            ctypes.byref(st))
+        if status != WF_OK:
+            _check(status)
+        return alm, mp, st.as_dict()
+
+    def residual(self, d, alm):
+        import torch
+        r1, r2, c2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().wf_residual(self.handle,
+                                 _dev_ptr(d, torch.float64, self.npix, "d"),
+                                 _dev_ptr(alm, torch.complex128, self.nalm, "alm"),
+                                 ctypes.byref(r1), ctypes.byref(r2), ctypes.byref(c2)))
+        return {"rel_res_wf": r1.value, "rel_res_fp": r2.value, "chi2": c2.value}
+
+    def alm2map(self, alm, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.npix, dtype=torch.float64, device=alm.device)
+        _check(lib().wf_alm2map(self.handle,
+                                _dev_ptr(alm, torch.complex128, self.nalm, "alm"),
+                                _dev_ptr(out, torch.float64, self.npix, "map")))
+        return out
+
+    def map2alm(self, m, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.nalm, dtype=torch.complex128, device=m.device)
+        _check(lib().wf_map2alm(self.handle,
+                                _dev_ptr(m, torch.float64, self.npix, "map"),
+                                _dev_ptr(out, torch.complex128, self.nalm, "alm")))
+        return out
+
+    def trace(self, cap=1 << 20):
+        n = ctypes.c_int(cap)
+        st = np.empty(cap, dtype=np.int32)
+        xi, mu, c = np.empty(cap), np.empty(cap), np.empty(cap)
+        _check(lib().wf_trace(self.handle, ctypes.byref(n),
+                              st.ctypes.data_as(ctypes.c_void_p),
+                              xi.ctypes.data_as(ctypes.c_void_p),
+                              mu.ctypes.data_as(ctypes.c_void_p),
+                              c.ctypes.data_as(ctypes.c_void_p)))
+        k = n.value
+        return {"stage": st[:k], "xi": xi[:k], "mu": mu[:k], "cauchy": c[:k]}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().wf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# -- functional names of the C ABI ------------------------------------------
+def wf_plan(nside, lmax, cl, noise_var=None, mask=None, opts=None, stream=None,
+            **opt_overrides):
+    return Plan(nside, lmax, cl, noise_var, mask, opts, stream, **opt_overrides)
+
+
+def wf_solve(plan, d, **kw):
+    return plan.solve(d, **kw)
+
+
+def wf_solve_host(plan, d_host, **kw):
+    return plan.solve_host(d_host, **kw)
+
+
+def wf_residual(plan, d, alm):
+    return plan.residual(d, alm)
+
+
+def wf_alm2map(plan, alm, out=None):
+    return plan.alm2map(alm, out)
+
+
+def wf_map2alm(plan, m, out=None):
+    return plan.map2alm(m, out)
+
+
+def wf_set_noise(plan, noise_var, mask=None):
+    return plan.set_noise(noise_var, mask)
+
+
+def wf_set_cl(plan, cl):
+    return plan.set_cl(cl)
+
+
+def wf_trace(plan):
+    return plan.trace()
+
+
+def wf_destroy(plan):
+    plan.close()

@@ -1,0 +1,85 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/wf.h declares; argument errors are reported before any CUDA work
+(these calls need no GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "wf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(wf_[a-z0-9_]+)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def wflib():
+    from paper_1702_08852_gb300 import build
+    build.build()
+    from paper_1702_08852_gb300 import wf
+    return wf
+
+
+def test_header_lists_the_entry_points():
+    names = declared_functions()
+    for n in ("wf_plan", "wf_solve", "wf_residual", "wf_alm2map", "wf_map2alm",
+              "wf_destroy", "wf_solve_host"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(wflib):
+    L = ctypes.CDLL(wflib.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing
+
+
+def test_defaults_and_strings(wflib):
+    o = wflib.wf_opts_default()
+    assert o.beta == 0.75 and o.eps_final == 1e-6 and o.band_limit == 1
+    assert wflib.wf_status_str(0) == "ok"
+    assert "argument" in wflib.wf_status_str(1)
+    L = wflib.lib()
+    assert L.wf_npix(1024) == 12 * 1024 * 1024
+    assert L.wf_nalm(2048) == 2049 * 2050 // 2
+
+
+@pytest.mark.parametrize("nside,lmax,cl_bad", [(0, 4, False), (4, 12, False),
+                                               (4, 0, False), (4, 8, True)])
+def test_plan_rejects_bad_arguments_before_cuda(wflib, nside, lmax, cl_bad):
+    L = wflib.lib()
+    cl = np.ones(max(lmax, 1) + 1)
+    if cl_bad:
+        cl[3] = -1.0
+    h = ctypes.c_void_p()
+    o = wflib.wf_opts_default()
+    st = L.wf_plan(ctypes.byref(h), nside, lmax, cl.ctypes.data_as(ctypes.c_void_p),
+                   None, None, ctypes.byref(o), None)
+    assert st == wflib.WF_ERR_ARG
+    assert h.value is None
+    assert wflib.wf_last_error()
+
+
+def test_bad_options_rejected(wflib):
+    L = wflib.lib()
+    cl = np.ones(9)
+    for field, val in (("beta", 1.0), ("beta", 0.0), ("eps_final", 0.0),
+                       ("max_iter", 0), ("precision", 7), ("stop_rule", 3)):
+        o = wflib.wf_opts_default(**{field: val})
+        h = ctypes.c_void_p()
+        st = L.wf_plan(ctypes.byref(h), 4, 8, cl.ctypes.data_as(ctypes.c_void_p),
+                       None, None, ctypes.byref(o), None)
+        assert st == wflib.WF_ERR_ARG, field
+
+
+def test_null_plan_calls(wflib):
+    L = wflib.lib()
+    assert L.wf_solve(None, None, None, None, None, None, None) == wflib.WF_ERR_ARG
+    assert L.wf_alm2map(None, None, None) == wflib.WF_ERR_ARG
+    L.wf_destroy(None)

@@ -1,0 +1,176 @@
+"""The dual messenger solve of the CUDA path (through the C ABI) against the
+oracle: dense fixed points, the uniform-noise closed form, the oracle's own
+iteration trace, and the diagnostics of App. C."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1702_08852_gb300 import build
+    build.build()
+    return torch
+
+
+def problem(osht, kind, nside, seed, **kw):
+    from paper_1702_08852_gb300 import inputs
+    if kind == "lognormal":
+        p = inputs.lognormal_problem(nside, seed=seed, **kw)
+    elif kind == "scan":
+        p = inputs.scan_problem(nside, seed=seed, **kw)
+    else:
+        p = inputs.uniform_problem(nside, seed=seed, **kw)
+    d = p.data(osht.alm2map(p.alm_true, p.nside, p.lmax))
+    return p, d
+
+
+def gpu_solve(torch, p, d, **opts):
+    from paper_1702_08852_gb300 import wf
+    nv = torch.from_numpy(p.noise_var).cuda()
+    mk = torch.from_numpy(p.mask.astype(np.uint8)).cuda()
+    with wf.Plan(p.nside, p.lmax, p.cl, nv, mk, **opts) as plan:
+        alm, mp, st = plan.solve(torch.from_numpy(d).cuda())
+        tr = plan.trace()
+        return alm.cpu().numpy(), mp.cpu().numpy(), st, tr
+
+
+def rel_alm(osht, a, b, lmax):
+    return osht.alm_norm(a - b, lmax) / osht.alm_norm(b, lmax)
+
+
+@pytest.mark.parametrize("nside,kind,seed", [(4, "lognormal", 1), (8, "lognormal", 2),
+                                             (8, "scan", 3)])
+def test_fp64_solve_matches_dense_fixed_point(torch_cuda, osht, odm, nside, kind, seed):
+    torch = torch_cuda
+    kw = {"discs": 5, "disc_radius_deg": 10.0} if kind == "scan" else {}
+    p, d = problem(osht, kind, nside, seed, **kw)
+    alm, mp, st, _ = gpu_solve(torch, p, d, eps_final=1e-13)
+    assert st["converged"] == 1
+    ref = odm.dm_fixed_point_dense(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d, 0.0)
+    assert rel_alm(osht, alm, ref, p.lmax) < 1e-10
+    sref = osht.alm2map(ref, p.nside, p.lmax)
+    assert np.linalg.norm(mp - sref) / np.linalg.norm(sref) < 1e-10
+
+
+def test_fp64_solve_nside32_workload(torch_cuda, osht, odm):
+    """Nside 32, lmax 64, lognormal noise, |b| < 15 deg band + 20 discs of
+    3 deg: the small full-size workload, against the dense fixed point."""
+    torch = torch_cuda
+    p, d = problem(osht, "lognormal", 32, 1000)
+    alm, mp, st, _ = gpu_solve(torch, p, d, eps_final=1e-12)
+    assert st["converged"] == 1
+    Y = osht.ymatrix(p.nside, p.lmax)
+    ref = odm.dm_fixed_point_dense(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d, 0.0, Y=Y)
+    sref = Y @ osht.alm_to_real(ref, p.lmax)
+    assert np.linalg.norm(mp - sref) / np.linalg.norm(sref) < 1e-10
+
+
+def test_error_stop_rule_1e6(torch_cuda, osht, odm):
+    """The default last-stage stop (error estimate < 1e-6) gives a map within
+    a few 1e-6 of the converged solution."""
+    torch = torch_cuda
+    p, d = problem(osht, "lognormal", 16, 7)
+    alm, mp, st, _ = gpu_solve(torch, p, d)
+    ref = odm.dm_fixed_point_dense(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d, 0.0)
+    sref = osht.alm2map(ref, p.nside, p.lmax)
+    assert np.linalg.norm(mp - sref) / np.linalg.norm(sref) < 3e-6
+
+
+@pytest.mark.parametrize("nside", [8, 64])
+def test_uniform_noise_closed_form(torch_cuda, osht, nside):
+    torch = torch_cuda
+    p, d = problem(osht, "uniform", nside, 4)
+    alm, mp, st, tr = gpu_solve(torch, p, d, eps_final=1e-12)
+    om = 4 * np.pi / (12 * nside * nside)
+    from paper_1702_08852_gb300 import inputs
+    ls, _ = inputs.lm_of_slots(p.lmax)
+    s2 = p.noise_var[0]
+    want = (p.cl / (p.cl + s2 * om))[ls] * osht.map2alm(d, nside, p.lmax)
+    assert rel_alm(osht, alm, want, p.lmax) < 1e-12
+    assert st["iterations"] <= 2 * st["stages"] + 1
+
+
+def test_trace_follows_the_oracle(torch_cuda, osht, odm):
+    """Same stage schedule and per-iteration Cauchy ratios as the oracle's
+    Algorithm 2 (up to rounding, over the first stages)."""
+    torch = torch_cuda
+    p, d = problem(osht, "lognormal", 8, 12)
+    otr = []
+    odm.dual_messenger(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d,
+                       eps_final=1e-8, stop="error", trace=otr)
+    _, _, st, tr = gpu_solve(torch, p, d, eps_final=1e-8)
+    ost = np.array([t[0] for t in otr])
+    oc = np.array([t[3] for t in otr])
+    n = min(len(oc), len(tr["cauchy"]), 200)
+    assert np.array_equal(tr["stage"][:n], ost[:n])
+    assert np.allclose(tr["xi"][:n], [t[1] for t in otr[:n]], rtol=1e-14)
+    assert np.allclose(tr["cauchy"][:n], oc[:n], rtol=1e-8, atol=1e-14)
+    assert abs(st["iterations"] - len(otr)) <= max(3, len(otr) // 100)
+
+
+def test_residual_diagnostics(torch_cuda, osht, odm):
+    torch = torch_cuda
+    from paper_1702_08852_gb300 import wf
+    p, d = problem(osht, "lognormal", 8, 21)
+    T = odm.MatrixTransforms(p.nside, p.lmax)
+    xw = odm.wf_exact_dense(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d, Y=T.Y)
+    xd = odm.dm_fixed_point_dense(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d, 0.0, Y=T.Y)
+    nv = torch.from_numpy(p.noise_var).cuda()
+    mk = torch.from_numpy(p.mask.astype(np.uint8)).cuda()
+    dd = torch.from_numpy(d).cuda()
+    with wf.Plan(p.nside, p.lmax, p.cl, nv, mk) as plan:
+        for x in (xw, xd):
+            r = plan.residual(dd, torch.from_numpy(x).cuda())
+            assert r["rel_res_wf"] == pytest.approx(
+                odm.wf_residual(x, p.nside, p.lmax, p.cl, p.noise_var, p.mask, d, T),
+                rel=1e-8, abs=1e-13)
+            assert r["chi2"] == pytest.approx(
+                odm.chi2(x, p.nside, p.lmax, p.cl, p.noise_var, p.mask, d, T), rel=1e-11)
+            assert r["rel_res_fp"] == pytest.approx(
+                odm.fixed_point_residual(x, p.nside, p.lmax, p.cl, p.noise_var, p.mask,
+                                         d, T), rel=1e-6, abs=1e-13)
+
+
+def test_host_entry_point_equals_device(torch_cuda, osht):
+    torch = torch_cuda
+    from paper_1702_08852_gb300 import wf
+    p, d = problem(osht, "lognormal", 8, 30)
+    nv = torch.from_numpy(p.noise_var).cuda()
+    mk = torch.from_numpy(p.mask.astype(np.uint8)).cuda()
+    with wf.Plan(p.nside, p.lmax, p.cl, nv, mk) as plan:
+        a1, m1, _ = plan.solve(torch.from_numpy(d).cuda())
+        a2, m2, _ = plan.solve_host(d)
+        assert np.array_equal(a1.cpu().numpy(), a2)
+        assert np.array_equal(m1.cpu().numpy(), m2)
+
+
+def test_deterministic(torch_cuda, osht):
+    torch = torch_cuda
+    p, d = problem(osht, "scan", 16, 5, discs=10)
+    a1, _, s1, _ = gpu_solve(torch, p, d)
+    a2, _, s2, _ = gpu_solve(torch, p, d)
+    assert np.array_equal(a1, a2) and s1["iterations"] == s2["iterations"]
+
+
+def test_plan_rejects_bad_noise(torch_cuda):
+    torch = torch_cuda
+    from paper_1702_08852_gb300 import wf
+    nside, lmax = 4, 8
+    nv = torch.ones(12 * nside * nside, dtype=torch.float64, device="cuda")
+    nv[3] = -1.0
+    with pytest.raises(wf.WFError) as e:
+        wf.Plan(nside, lmax, np.ones(lmax + 1), nv)
+    assert e.value.status == wf.WF_ERR_ARG
+    mk = torch.ones(12 * nside * nside, dtype=torch.uint8, device="cuda")
+    with pytest.raises(wf.WFError):
+        wf.Plan(nside, lmax, np.ones(lmax + 1), torch.ones_like(nv), mk)
+    nv[3] = 1.0
+    mk[:] = 0
+    mk[3] = 1
+    nv[3] = float("nan")   # masked: ignored
+    wf.Plan(nside, lmax, np.ones(lmax + 1), nv, mk).close()
