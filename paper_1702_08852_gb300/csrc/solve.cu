@@ -143,22 +143,20 @@ __global__ void __launch_bounds__(CTRL_THREADS)
 
 // ---------------------------------------------------------------- reductions
 // sum_lm w_m (a . b), optionally with a per-l factor fl (NULL = 1) applied to
-// both; deterministic two-level reduction (blocks -> out[0..nb), then host)
+// both; blocks stride over m, threads over l; deterministic two-level
+// reduction (blocks -> out[0..gridDim), then host)
 __global__ void k_alm_dot(const double2 *a, const double2 *b, const double *fl,
-                          int lmax, long nalm, double *out) {
+                          int lmax, double *out) {
   __shared__ double sh[256];
   double acc = 0.0;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < nalm;
-       i += (long)gridDim.x * blockDim.x) {
-    // m of slot i: largest m with m (2 lmax + 1 - m) / 2 <= i
-    int m = (int)((2.0 * lmax + 1.0 - sqrt((2.0 * lmax + 1.0) * (2.0 * lmax + 1.0) -
-                                           8.0 * (double)i)) / 2.0);
-    while (m > 0 && (long)m * (2 * lmax + 1 - m) / 2 > i) --m;
-    while ((long)(m + 1) * (2 * lmax + 1 - (m + 1)) / 2 <= i && m < lmax) ++m;
-    const int l = (int)(i - (long)m * (2 * lmax + 1 - m) / 2);
+  for (int m = blockIdx.x; m <= lmax; m += gridDim.x) {
+    const long base = (long)m * (2 * lmax + 1 - m) / 2;  // index of (l, m) = base + l
     const double w = m == 0 ? 1.0 : 2.0;
-    double f = fl ? fl[l] : 1.0;
-    acc += w * f * f * (a[i].x * b[i].x + a[i].y * b[i].y);
+    for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
+      const long i = base + l;
+      const double f = fl ? fl[l] : 1.0;
+      acc += w * f * f * (a[i].x * b[i].x + a[i].y * b[i].y);
+    }
   }
   sh[threadIdx.x] = acc;
   __syncthreads();
@@ -224,7 +222,7 @@ static wf_status host_sum(Plan &P, double *dev, int n, double *res) {
 
 static wf_status alm_dot(Plan &P, const double2 *a, const double2 *b,
                          const double *fl, double *res) {
-  k_alm_dot<<<RED_BLOCKS, 256, 0, P.stream>>>(a, b, fl, P.lmax, P.nalm, P.red);
+  k_alm_dot<<<RED_BLOCKS, 256, 0, P.stream>>>(a, b, fl, P.lmax, P.red);
   WF_CUDA(cudaGetLastError());
   return host_sum(P, P.red, RED_BLOCKS, res);
 }
