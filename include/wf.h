@@ -75,6 +75,9 @@ typedef struct {
                         the truncated spectrum is nonzero (exact; default 1) */
   int graph_chunk;   /* iterations per captured CUDA graph launch; 0 = auto */
   int refine_max;    /* WF_PREC_MIXED: max FP64 refinement steps (default 8) */
+  int timing;        /* 1: time the Legendre kernels of every iteration with
+                        CUDA events recorded inside the captured graphs
+                        (read with wf_kernel_stats; default 0) */
 } wf_opts;
 
 /* Per-solve statistics. */
@@ -159,6 +162,24 @@ long wf_nalm(int lmax);
  * the Cauchy ratio of each iteration. */
 wf_status wf_trace(wf_plan_t plan, int *count, int *stage, double *xi,
                    double *mu, double *cauchy);
+
+/* Device time and work of the Legendre kernels in the solves run with
+ * opts.timing = 1 since plan creation or the last reset.
+ *  kernel    0 = analysis (Omega Y^T with the fused filter), 1 = synthesis.
+ *  ms        summed CUDA-event time of the timed launches.
+ *  launches  number of timed launches (iterations that did work).
+ *  gflop     algorithmic work of those launches: 7 flops (recurrence 3,
+ *            complex accumulate 4) per (l, m, ring pair) with l <= the
+ *            band limit of the launch and |lambda_lm| >= 2^-100 (the terms
+ *            the method needs; the skipped ones are below that).
+ *  reset     nonzero: clear the counters after reading.
+ * Any output pointer may be NULL. */
+wf_status wf_kernel_stats(wf_plan_t plan, int kernel, double *ms, long *launches,
+                          double *gflop, int reset);
+
+/* Algorithmic work of one Legendre transform at band limit L (<= lmax): the
+ * number of (l, m, ring pair) terms with l <= L and |lambda_lm| >= 2^-100. */
+wf_status wf_legendre_terms(wf_plan_t plan, int L, double *terms);
 
 void wf_destroy(wf_plan_t plan);
 const char *wf_status_str(wf_status s);

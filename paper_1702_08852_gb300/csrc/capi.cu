@@ -19,17 +19,18 @@ static wf_status arg_error(const char *msg) {
 
 static void free_plan(wf_plan_s *P) {
   if (!P) return;
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 3; ++i)
     if (P->graph[i]) cudaGraphExecDestroy(P->graph[i]);
   void *bufs[] = {P->pairs, P->cl_d,   P->rc,      P->rg,     P->rc32,   P->seed_l,
                   P->seed_u, P->tw64,  P->tw32,    P->chirp64, P->chirp32, P->bhat64,
                   P->bhat32, P->nvar,  P->F64,     P->G64,    P->F32,    P->G32,
                   P->x,      P->xtmp,  P->dmap,    P->mtmp,   P->partials, P->red,
-                  P->state,  P->trace};
+                  P->state,  P->trace, P->xacc,  P->src};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (P->state_h) cudaFreeHost(P->state_h);
   if (P->capture_stream) cudaStreamDestroy(P->capture_stream);
+  for (cudaEvent_t e : P->tev) cudaEventDestroy(e);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
   delete P;
@@ -43,6 +44,8 @@ static wf_status alloc_work(Plan &P) {
   WF_CUDA(cudaMalloc(&P.G32, sizeof(float2) * nF));
   WF_CUDA(cudaMalloc(&P.x, sizeof(double2) * P.nalm));
   WF_CUDA(cudaMalloc(&P.xtmp, sizeof(double2) * P.nalm));
+  WF_CUDA(cudaMalloc(&P.xacc, sizeof(double2) * P.nalm));
+  WF_CUDA(cudaMalloc(&P.src, sizeof(double2) * P.nalm));
   WF_CUDA(cudaMalloc(&P.dmap, sizeof(double) * P.npix));
   WF_CUDA(cudaMalloc(&P.mtmp, sizeof(double) * P.npix));
   WF_CUDA(cudaMalloc(&P.partials, sizeof(double) * 2 * (P.lmax + 1)));
@@ -278,6 +281,27 @@ wf_status wf_trace(wf_plan_t plan, int *count, int *stage, double *xi, double *m
   }
   *count = n;
   return WF_OK;
+}
+
+wf_status wf_kernel_stats(wf_plan_t plan, int kernel, double *ms, long *launches,
+                          double *gflop, int reset) {
+  if (!plan) return arg_error("wf_kernel_stats: plan is NULL");
+  if (kernel < 0 || kernel > 1) return arg_error("wf_kernel_stats: kernel must be 0 or 1");
+  if (ms) *ms = plan->kern_ms[kernel];
+  if (launches) *launches = plan->kern_launches[kernel];
+  if (gflop) *gflop = plan->kern_flop[kernel] * 1e-9;
+  if (reset) {
+    plan->kern_ms[kernel] = 0.0;
+    plan->kern_launches[kernel] = 0;
+    plan->kern_flop[kernel] = 0.0;
+  }
+  return WF_OK;
+}
+
+wf_status wf_legendre_terms(wf_plan_t plan, int L, double *terms) {
+  if (!plan || !terms) return arg_error("wf_legendre_terms: NULL argument");
+  if (L < 0 || L > plan->lmax) return arg_error("wf_legendre_terms: L out of range");
+  return legendre_terms(*plan, L, terms);
 }
 
 void wf_destroy(wf_plan_t plan) { free_plan(plan); }

@@ -236,6 +236,7 @@ __global__ void __launch_bounds__(ANA_THREADS)
                     const double *__restrict__ cl, double omega,
                     const typename Vec2<T>::type *__restrict__ G,
                     double2 *__restrict__ x, double *__restrict__ partials,
+                    const double2 *__restrict__ src,
                     const SolverState *__restrict__ st, int mode, int lstatic) {
   typedef typename Vec2<T>::type T2;
   const int m = blockIdx.x;
@@ -359,6 +360,10 @@ __global__ void __launch_bounds__(ANA_THREADS)
         const int l = m + j;
         const double sbar = fmax(cl[l] - mu * omega, 0.0);
         const double f = sbar / (sbar + xi * omega);
+        if (src) {  // harmonic source term of a correction solve
+          ar += xi * omega * src[i].x;
+          ai += xi * omega * src[i].y;
+        }
         ar *= f;
         ai *= f;
         const double2 old = x[i];
@@ -428,7 +433,8 @@ wf_status launch_legendre_synth(const Plan &P, const double2 *x, T2 *F,
 
 template <typename T2>
 wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
-                               const SolverState *st, int mode, int lstatic) {
+                               const SolverState *st, int mode, int lstatic,
+                               const double2 *src) {
   typedef typename Kernels<T2>::T T;
   constexpr int NP = 2;
   auto kern = k_legendre_anal<T, NP>;
@@ -436,7 +442,7 @@ wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
       align16(sizeof(T2) * (P.lmax + 1) * ANA_WARPS) + sizeof(T) * (P.lmax + 1);
   kern<<<P.lmax + 1, ANA_THREADS, smem, P.stream>>>(
       P.pairs, P.npairs, P.lmax, P.rc, P.rc32, P.rg, P.seed_l, P.seed_u, P.cl_d,
-      P.omega, G, x, P.partials, st, mode, lstatic);
+      P.omega, G, x, P.partials, src, st, mode, lstatic);
   WF_CUDA(cudaGetLastError());
   return WF_OK;
 }
@@ -461,9 +467,9 @@ template wf_status launch_legendre_synth<float2>(const Plan &, const double2 *,
                                                  float2 *, const SolverState *, int);
 template wf_status launch_legendre_anal<double2>(const Plan &, const double2 *,
                                                  double2 *, const SolverState *,
-                                                 int, int);
+                                                 int, int, const double2 *);
 template wf_status launch_legendre_anal<float2>(const Plan &, const float2 *,
                                                 double2 *, const SolverState *,
-                                                int, int);
+                                                int, int, const double2 *);
 
 }  // namespace wf

@@ -219,12 +219,12 @@ __global__ void __launch_bounds__(RING_THREADS)
         {
           const double v = nvar[pN];
           const double w = xi / (v + mu);  // 0 on masked pixels (v = +inf)
-          tN = sN + w * (in_map[pN] - sN);
+          tN = sN + w * ((in_map ? in_map[pN] : 0.0) - sN);
         }
         if (south) {
           const double v = nvar[pS];
           const double w = xi / (v + mu);
-          tS = sS + w * (in_map[pS] - sS);
+          tS = sS + w * ((in_map ? in_map[pS] : 0.0) - sS);
         }
         const T2 tt = CT<T2>::mk((T)tN, (T)tS);
         buf[q] = blue ? cmulc(tt, chirp[q]) : tt;

@@ -51,6 +51,7 @@ __device__ int band_of(const double *cl, int lmax, double mu, double omega,
 
 constexpr int CTRL_THREADS = 256;
 
+
 __global__ void __launch_bounds__(CTRL_THREADS)
     k_control(SolverState *st, const double *__restrict__ partials, int lmax,
               const double *__restrict__ cl, TraceEntry *trace) {
@@ -76,13 +77,15 @@ __global__ void __launch_bounds__(CTRL_THREADS)
   if (threadIdx.x == 0) {
     num = snum[0];
     den = sden[0];
+    st->last_den = den;
+    if (st->den_fixed > 0.0) den = st->den_fixed;
     const double c = den > 0.0 ? sqrt(num / den) : 0.0;
     const int it = ++st->iter;
     st->stage_iter += 1;
     if (trace && it - 1 < st->trace_cap) {
       TraceEntry e;
       e.stage = st->stage;
-      e.pad = 0;
+      e.lcur = st->lcur;
       e.xi = st->xi;
       e.mu = st->mu;
       e.cauchy = c;
@@ -93,7 +96,13 @@ __global__ void __launch_bounds__(CTRL_THREADS)
       st->numeric_error = 1;
       st->done = 1;
     } else if (st->mu == 0.0) {
-      if (st->stop_rule == WF_STOP_ERROR) {
+      // arithmetic noise floor: the Cauchy ratio has stopped falling
+      st->flat = (st->prev_c > 0.0 && c >= st->prev_c) ? st->flat + 1 : 0;
+      if (st->flat >= 16 && c < 1e-4) {
+        st->done = 1;
+        st->converged = 1;
+        st->stagnated = 1;
+      } else if (st->stop_rule == WF_STOP_ERROR) {
         if (st->prev_c > 0.0 && c > 0.0) {
           const double r = fmin(c / st->prev_c, 0.999999);
           const double err = c * r / (1.0 - r);
@@ -127,6 +136,14 @@ __global__ void __launch_bounds__(CTRL_THREADS)
                       ? st->eps_final
                       : fmin(st->eps_cap, st->eps_final * fmax(1.0, st->mu / st->alpha));
       st->lcur = st->lnext;
+    }
+    if (adv && st->mu == 0.0 && st->handoff) {
+      st->done = 1;
+      st->at_final = 1;
+    }
+    if (!st->done && st->delta_cap2 > 0.0 && st->last_den > st->delta_cap2) {
+      st->done = 1;
+      st->reanchor = 1;
     }
     if (!st->done && st->iter >= st->max_iter) st->done = 1;
     advance = adv;
@@ -280,6 +297,14 @@ static SolverState initial_state(const Plan &P) {
   s.band_limit = o.band_limit;
   s.trace_cap = P.trace_cap;
   s.stage_iter = 0;
+  s.flat = 0;
+  s.stagnated = 0;
+  s.handoff = 0;
+  s.at_final = 0;
+  s.reanchor = 0;
+  s.den_fixed = 0.0;
+  s.delta_cap2 = 0.0;
+  s.last_den = 0.0;
   if (o.band_limit) {
     s.lcur = band_host(P.cl, mu0, P.omega);
     const double xi2 = std::max(P.alpha, o.beta * s.xi);
@@ -291,11 +316,20 @@ static SolverState initial_state(const Plan &P) {
   return s;
 }
 
+// one iteration; data = NULL runs a correction solve (d = 0) driven by the
+// harmonic source `src`
 template <typename T2>
-static wf_status enqueue_iteration(Plan &P, T2 *F, T2 *G) {
-  WF_TRY(launch_legendre_anal<T2>(P, G, P.x, P.state, ANA_FILTER, P.lmax));
+static wf_status enqueue_iteration(Plan &P, T2 *F, T2 *G, const double *data,
+                                   const double2 *src, int slot) {
+  const bool timed = slot >= 0 && P.tev_chunk > 0;
+  const int C = P.tev_chunk;
+  if (timed) WF_CUDA(cudaEventRecord(P.tev[0 * C + slot], P.stream));
+  WF_TRY(launch_legendre_anal<T2>(P, G, P.x, P.state, ANA_FILTER, P.lmax, src));
+  if (timed) WF_CUDA(cudaEventRecord(P.tev[1 * C + slot], P.stream));
+  if (timed) WF_CUDA(cudaEventRecord(P.tev[2 * C + slot], P.stream));
   WF_TRY(launch_legendre_synth<T2>(P, P.x, F, P.state, P.lmax));
-  WF_TRY(launch_ring<T2>(P, RING_FUSED, F, G, P.dmap, nullptr, P.state, P.lmax));
+  if (timed) WF_CUDA(cudaEventRecord(P.tev[3 * C + slot], P.stream));
+  WF_TRY(launch_ring<T2>(P, RING_FUSED, F, G, data, nullptr, P.state, P.lmax));
   k_control<<<1, CTRL_THREADS, 0, P.stream>>>(P.state, P.partials, P.lmax, P.cl_d,
                                               P.trace);
   WF_CUDA(cudaGetLastError());
@@ -308,7 +342,8 @@ static int auto_chunk(const Plan &P) {
 }
 
 template <typename T2>
-static wf_status capture_graph(Plan &P, int which, T2 *F, T2 *G) {
+static wf_status capture_graph(Plan &P, int which, T2 *F, T2 *G, const double *data,
+                               const double2 *src) {
   if (P.graph[which]) return WF_OK;
   const int chunk = P.opts.graph_chunk > 0 ? P.opts.graph_chunk : auto_chunk(P);
   cudaGraph_t g = nullptr;
@@ -316,6 +351,16 @@ static wf_status capture_graph(Plan &P, int which, T2 *F, T2 *G) {
   // legacy default stream, which cannot be captured); launch on P.stream
   if (!P.capture_stream)
     WF_CUDA(cudaStreamCreateWithFlags(&P.capture_stream, cudaStreamNonBlocking));
+  if (P.opts.timing && P.tev_chunk < chunk) {
+    for (cudaEvent_t e : P.tev) cudaEventDestroy(e);
+    P.tev.assign(4 * chunk, nullptr);
+    for (auto &e : P.tev) WF_CUDA(cudaEventCreate(&e));
+    P.tev_chunk = chunk;
+  }
+  if (P.opts.timing && P.tev_chunk != chunk) {
+    set_error("graph capture: timing events sized for another chunk");
+    return WF_ERR_STATE;
+  }
   cudaStream_t user = P.stream;
   P.stream = P.capture_stream;
   cudaError_t eb = cudaStreamBeginCapture(P.stream, cudaStreamCaptureModeThreadLocal);
@@ -325,7 +370,8 @@ static wf_status capture_graph(Plan &P, int which, T2 *F, T2 *G) {
     return WF_ERR_CUDA;
   }
   wf_status s = WF_OK;
-  for (int i = 0; i < chunk && s == WF_OK; ++i) s = enqueue_iteration<T2>(P, F, G);
+  for (int i = 0; i < chunk && s == WF_OK; ++i)
+    s = enqueue_iteration<T2>(P, F, G, data, src, P.opts.timing ? i : -1);
   cudaError_t e = cudaStreamEndCapture(P.stream, &g);
   P.stream = user;
   if (s != WF_OK) {
@@ -347,18 +393,128 @@ static wf_status capture_graph(Plan &P, int which, T2 *F, T2 *G) {
   return WF_OK;
 }
 
+// Run stages until the control kernel sets done.  tinit: initial messenger
+// field (NULL = zero); data / src as in enqueue_iteration.  The state must
+// have been uploaded.
 template <typename T2>
-static wf_status run_loop(Plan &P, int which, T2 *F, T2 *G, const double *tinit) {
-  // G <- FFT of the initial messenger field
-  WF_TRY(launch_ring<T2>(P, RING_ANALYSIS, nullptr, G, tinit, nullptr, nullptr,
-                         P.lmax));
-  WF_TRY(capture_graph<T2>(P, which, F, G));
+static wf_status run_loop(Plan &P, int which, T2 *F, T2 *G, const double *tinit,
+                          const double *data, const double2 *src) {
+  if (tinit) {
+    WF_TRY(launch_ring<T2>(P, RING_ANALYSIS, nullptr, G, tinit, nullptr, nullptr,
+                           P.lmax));
+  } else {
+    WF_CUDA(cudaMemsetAsync(G, 0, sizeof(T2) * (size_t)P.nring * (P.lmax + 1),
+                            P.stream));
+  }
+  WF_TRY(capture_graph<T2>(P, which, F, G, data, src));
+  int it0 = P.state_h->iter;
   for (;;) {
     WF_CUDA(cudaGraphLaunch(P.graph[which], P.stream));
     WF_CUDA(cudaMemcpyAsync(P.state_h, P.state, sizeof(SolverState),
                             cudaMemcpyDeviceToHost, P.stream));
     WF_CUDA(cudaStreamSynchronize(P.stream));
+    if (P.opts.timing) {
+      // iterations that did work in this launch: the first (iter - it0)
+      const int active = std::min(P.state_h->iter - it0, P.graph_chunk[which]);
+      const int C = P.tev_chunk;
+      for (int i = 0; i < active; ++i) {
+        float a = 0.f, b = 0.f;
+        WF_CUDA(cudaEventElapsedTime(&a, P.tev[0 * C + i], P.tev[1 * C + i]));
+        WF_CUDA(cudaEventElapsedTime(&b, P.tev[2 * C + i], P.tev[3 * C + i]));
+        P.kern_ms[0] += a;
+        P.kern_ms[1] += b;
+      }
+      P.kern_launches[0] += active;
+      P.kern_launches[1] += active;
+      it0 = P.state_h->iter;
+    }
     if (P.state_h->done) break;
+  }
+  return WF_OK;
+}
+
+// r = G(x) - x (both FP64 alm) -> source of the correction solve:
+// src = r / (f0_l alpha Omega), f0_l = C_l / (C_l + alpha Omega); 0 where C_l = 0
+__global__ void k_make_source(const double2 *gx, const double2 *x, const double *cl,
+                              double alpha, double omega, int lmax, double2 *src) {
+  const int m = blockIdx.x;
+  const long base = (long)m * (2 * lmax + 1 - m) / 2;
+  const double ao = alpha * omega;
+  for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
+    const long i = base + l;
+    const double c = cl[l];
+    const double s = c > 0.0 ? (c + ao) / (c * ao) : 0.0;
+    src[i] = make_double2(s * (gx[i].x - x[i].x), s * (gx[i].y - x[i].y));
+  }
+}
+
+__global__ void k_alm_add(double2 *x, const double2 *y, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x)
+    x[i] = make_double2(x[i].x + y[i].x, x[i].y + y[i].y);
+}
+
+// FP64 fixed-point map of the last stage: gx = G(x) at xi = alpha, mu = 0;
+// returns ||G(x) - x||^2 in *num
+static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num) {
+  SolverState s = initial_state(P);
+  s.xi = P.alpha;
+  s.mu = 0.0;
+  s.lcur = s.lnext = P.lmax;
+  s.done = 0;
+  *P.state_h = s;
+  WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
+                          cudaMemcpyHostToDevice, P.stream));
+  WF_CUDA(cudaMemcpyAsync(gx, x, sizeof(double2) * P.nalm, cudaMemcpyDeviceToDevice,
+                          P.stream));
+  WF_TRY(launch_legendre_synth<double2>(P, x, P.F64, nullptr, P.lmax));
+  WF_TRY(launch_ring<double2>(P, RING_FUSED, P.F64, P.G64, P.dmap, nullptr, P.state,
+                              P.lmax));
+  WF_TRY(launch_legendre_anal<double2>(P, P.G64, gx, P.state, ANA_FILTER, P.lmax));
+  std::vector<double> part(2 * (P.lmax + 1));
+  WF_CUDA(cudaMemcpyAsync(part.data(), P.partials, sizeof(double) * part.size(),
+                          cudaMemcpyDeviceToHost, P.stream));
+  WF_CUDA(cudaStreamSynchronize(P.stream));
+  double acc = 0.0;
+  for (int m = 0; m <= P.lmax; ++m) acc += part[2 * m];
+  *num = acc;
+  return WF_OK;
+}
+
+// reduced term count of one Legendre transform at band L (cached per L)
+wf_status legendre_terms(Plan &P, int L, double *terms) {
+  if (P.seed_l_h.empty()) {
+    P.seed_l_h.resize((size_t)P.npairs * (P.lmax + 1));
+    WF_CUDA(cudaMemcpy(P.seed_l_h.data(), P.seed_l, sizeof(int) * P.seed_l_h.size(),
+                       cudaMemcpyDeviceToHost));
+    P.work_cache.assign(P.lmax + 1, -1.0);
+  }
+  if (P.work_cache[L] < 0.0) {
+    double w = 0.0;
+    for (int m = 0; m <= L; ++m)
+      for (int k = 0; k < P.npairs; ++k) {
+        const int ls = P.seed_l_h[(size_t)m * P.npairs + k];
+        if (ls <= L) w += (double)(L - ls + 1);
+      }
+    P.work_cache[L] = w;
+  }
+  *terms = P.work_cache[L];
+  return WF_OK;
+}
+
+// add the algorithmic work of the timed launches of iterations [i0, i1)
+static wf_status account_work(Plan &P, int i0, int i1) {
+  i1 = std::min(i1, P.trace_cap);
+  if (i1 <= i0) return WF_OK;
+  std::vector<TraceEntry> h(i1 - i0);
+  WF_CUDA(cudaMemcpy(h.data(), P.trace + i0, sizeof(TraceEntry) * h.size(),
+                     cudaMemcpyDeviceToHost));
+  for (const TraceEntry &e : h) {
+    if (e.lcur < 0) continue;
+    double t = 0.0;
+    WF_TRY(legendre_terms(P, e.lcur, &t));
+    P.kern_flop[0] += 7.0 * t;
+    P.kern_flop[1] += 7.0 * t;
   }
   return WF_OK;
 }
@@ -383,13 +539,88 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
     WF_CUDA(cudaGetLastError());
     tinit = P.mtmp;
   }
+  int refinements = 0, total_iter = 0, first_stages = 0;
+  double fp_res = -1.0;
   *P.state_h = initial_state(P);
-  WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
-                          cudaMemcpyHostToDevice, P.stream));
   if (P.opts.precision == WF_PREC_MIXED) {
-    WF_TRY(run_loop<float2>(P, 1, P.F32, P.G32, tinit));
+    // Stages mu > 0 of Algorithm 2 with FP32 transforms (their fixed points
+    // only steer the iterate towards the last stage's)...
+    bool converged = false;
+    int stage_final = 0;
+    if (P.state_h->mu > 0.0) {
+      P.state_h->handoff = 1;
+      WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
+                              cudaMemcpyHostToDevice, P.stream));
+      WF_TRY(run_loop<float2>(P, 1, P.F32, P.G32, tinit, P.dmap, nullptr));
+      if (P.state_h->numeric_error) {
+        set_error("wf_solve: NaN or Inf in the iteration");
+        return WF_ERR_NUMERIC;
+      }
+      stage_final = P.state_h->stage;
+    }
+    total_iter = P.state_h->iter;
+    first_stages = stage_final + 1;
+    const bool reached_final = P.state_h->at_final || P.state_h->mu == 0.0;
+    // ...then the last stage (xi = alpha, mu = 0) anchored in FP64: with
+    // r = G64(x_a) - x_a, iterate delta <- J32 delta + r (the FP32 transform
+    // error now scales with |delta|, not |x|), x = x_a + delta.  Re-anchor
+    // when |delta| exceeds 1e-2 |x_a|.
+    WF_CUDA(cudaMemcpyAsync(P.xacc, P.x, sizeof(double2) * P.nalm,
+                            cudaMemcpyDeviceToDevice, P.stream));
+    const int lfinal = P.opts.band_limit ? band_host(P.cl, 0.0, P.omega) : P.lmax;
+    for (int k = 0; reached_final && k <= P.opts.refine_max; ++k) {
+      double num = 0.0, xn = 0.0;
+      WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num));
+      WF_TRY(alm_dot(P, P.xacc, P.xacc, nullptr, &xn));
+      k_make_source<<<P.lmax + 1, 128, 0, P.stream>>>(P.xtmp, P.xacc, P.cl_d, P.alpha,
+                                                      P.omega, P.lmax, P.src);
+      WF_CUDA(cudaGetLastError());
+      WF_CUDA(cudaMemsetAsync(P.x, 0, sizeof(double2) * P.nalm, P.stream));
+      SolverState s = initial_state(P);
+      s.xi = P.alpha;
+      s.mu = 0.0;
+      s.stage = stage_final;
+      s.eps_k = P.opts.eps_final;
+      s.lcur = s.lnext = lfinal;
+      s.iter = total_iter;
+      s.max_iter = P.opts.max_iter;
+      s.den_fixed = xn;
+      s.delta_cap2 = 1e-4 * xn;
+      *P.state_h = s;
+      WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
+                              cudaMemcpyHostToDevice, P.stream));
+      WF_TRY(run_loop<float2>(P, 2, P.F32, P.G32, nullptr, nullptr, P.src));
+      total_iter = P.state_h->iter;
+      if (P.state_h->numeric_error) {
+        set_error("wf_solve: NaN or Inf in the anchored last stage");
+        return WF_ERR_NUMERIC;
+      }
+      k_alm_add<<<304, 256, 0, P.stream>>>(P.xacc, P.x, P.nalm);
+      WF_CUDA(cudaGetLastError());
+      ++refinements;
+      if (P.state_h->converged) {
+        converged = true;
+        break;
+      }
+      if (!P.state_h->reanchor) break;  // max_iter
+    }
+    {
+      const SolverState keep = *P.state_h;
+      double num = 0.0, xn = 0.0;
+      WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num));
+      WF_TRY(alm_dot(P, P.xacc, P.xacc, nullptr, &xn));
+      fp_res = xn > 0.0 ? sqrt(num / xn) : 0.0;
+      *P.state_h = keep;
+    }
+    WF_CUDA(cudaMemcpyAsync(P.x, P.xacc, sizeof(double2) * P.nalm,
+                            cudaMemcpyDeviceToDevice, P.stream));
+    P.state_h->converged = converged ? 1 : 0;
   } else {
-    WF_TRY(run_loop<double2>(P, 0, P.F64, P.G64, tinit));
+    WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
+                            cudaMemcpyHostToDevice, P.stream));
+    WF_TRY(run_loop<double2>(P, 0, P.F64, P.G64, tinit, P.dmap, nullptr));
+    total_iter = P.state_h->iter;
+    first_stages = P.state_h->stage + 1;
   }
   if (map) WF_TRY(alm2map(P, reinterpret_cast<const double *>(P.x), map));
   if (alm)
@@ -398,18 +629,19 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
   WF_CUDA(cudaEventRecord(P.ev1, P.stream));
   WF_CUDA(cudaStreamSynchronize(P.stream));
   const SolverState &s = *P.state_h;
-  P.trace_len = std::min(s.iter, P.trace_cap);
+  P.trace_len = std::min(total_iter, P.trace_cap);
+  if (P.opts.timing) WF_TRY(account_work(P, 0, total_iter));
   if (stats) {
     float ms = 0.f;
     WF_CUDA(cudaEventElapsedTime(&ms, P.ev0, P.ev1));
-    stats->iterations = s.iter;
-    stats->stages = s.stage + 1;
+    stats->iterations = total_iter;
+    stats->stages = first_stages;
     stats->converged = s.converged;
-    stats->refinements = 0;
+    stats->refinements = refinements;
     stats->alpha = P.alpha;
     stats->final_cauchy = s.last_c;
     stats->err_estimate = s.err_est;
-    stats->fp_residual = -1.0;
+    stats->fp_residual = fp_res;
     stats->elapsed_ms = ms;
   }
   if (s.numeric_error) {

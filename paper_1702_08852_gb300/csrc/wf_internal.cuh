@@ -61,10 +61,18 @@ struct SolverState {
   int lnext;   // same for the next stage (the ring kernel fills G up to it)
   int max_iter, stop_rule, band_limit, trace_cap;
   int stage_iter;
+  int flat;       // consecutive last-stage iterations without a Cauchy decrease
+  int stagnated;  // the last stage stopped at the arithmetic noise floor
+  int handoff;    // 1: stop (done, not converged) on entering the mu = 0 stage
+  int at_final;   // set when the run stopped because of handoff
+  int reanchor;   // set when the correction grew past delta_cap2
+  double den_fixed;   // > 0: Cauchy denominator ||x||^2 of an anchored stage
+  double delta_cap2;  // > 0: stop when ||delta||^2 exceeds it (re-anchor)
+  double last_den;    // ||x_new||^2 of the last iteration
 };
 
 struct TraceEntry {
-  int stage, pad;
+  int stage, lcur;   // stage index and band limit of the iteration
   double xi, mu, cauchy;
 };
 
@@ -108,6 +116,8 @@ struct Plan {
   float2 *F32 = nullptr, *G32 = nullptr;
   double2 *x = nullptr;          // [nalm] current iterate
   double2 *xtmp = nullptr;       // [nalm]
+  double2 *xacc = nullptr;       // [nalm] refined solution (mixed precision)
+  double2 *src = nullptr;        // [nalm] harmonic source of a correction solve
   double *dmap = nullptr;        // [npix] data with masked pixels zeroed
   double *mtmp = nullptr;        // [npix]
   double *partials = nullptr;    // [lmax+1][2]
@@ -119,9 +129,21 @@ struct Plan {
   int trace_len = 0;
 
   // graphs (one per precision), captured lazily
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  int graph_chunk[2] = {0, 0};
+  // 0: FP64 with data, 1: FP32 with data, 2: FP32 correction (harmonic source)
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  int graph_chunk[3] = {0, 0, 0};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  // optional per-kernel timing inside the captured graphs (opts.timing):
+  // events around the Legendre analysis (k = 0) and synthesis (k = 1) of
+  // every iteration of a chunk; accumulated over active iterations only
+  std::vector<cudaEvent_t> tev;     // [2 kernels][2 (start, stop)][chunk]
+  int tev_chunk = 0;
+  double kern_ms[2] = {0.0, 0.0};
+  long kern_launches[2] = {0, 0};
+  double kern_flop[2] = {0.0, 0.0};  // algorithmic flops of the timed launches
+  std::vector<double> work_cache;    // reduced (l, m, ring-pair) count per band
+  std::vector<int> seed_l_h;         // host copy of seed_l
 };
 
 // ---------------------------------------------------------------- kernels
@@ -131,15 +153,18 @@ enum AnalysisMode { ANA_PLAIN = 0, ANA_FILTER = 1 };
 template <typename T2>
 wf_status launch_legendre_synth(const Plan &P, const double2 *x, T2 *F,
                                 const SolverState *st, int lstatic);
+// src (optional, FP64 alm): adds the harmonic source f_l xi Omega src_lm of a
+// correction solve to the filtered coefficients (ANA_FILTER only).
 template <typename T2>
 wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
-                               const SolverState *st, int mode, int lstatic);
+                               const SolverState *st, int mode, int lstatic,
+                               const double2 *src = nullptr);
 
 // Ring transforms (ringfft.cu).  Modes:
 enum RingMode {
   RING_SYNTH = 0,     // F -> map (write s)
   RING_ANALYSIS = 1,  // map (masked pixels -> 0) -> G
-  RING_FUSED = 2      // F -> s -> t = s + w (d - s) -> G
+  RING_FUSED = 2      // F -> s -> t = s + w (d - s) -> G  (in_map NULL: d = 0)
 };
 template <typename T2>
 wf_status launch_ring(const Plan &P, int mode, const T2 *F, T2 *G,
@@ -161,6 +186,7 @@ wf_status residual(Plan &P, const double *d, const double *alm, double *res_wf,
                    double *res_fp, double *chi2);
 wf_status alm2map(Plan &P, const double *alm, double *map);
 wf_status map2alm(Plan &P, const double *map, double *alm);
+wf_status legendre_terms(Plan &P, int L, double *terms);
 
 }  // namespace wf
 

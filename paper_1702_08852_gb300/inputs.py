@@ -107,17 +107,27 @@ def band_mask(nside, b0_deg):
 
 
 def disc_mask(nside, rng, count, radius_deg):
-    v = unit_vectors(nside)
-    m = np.zeros(len(v), dtype=bool)
+    z, phi = pixel_centres(nside)
+    m = np.zeros(len(z), dtype=bool)
     if count == 0:
         return m
     cz = rng.uniform(-1.0, 1.0, count)
     cp = rng.uniform(0.0, 2.0 * np.pi, count)
-    cs = np.sqrt(1.0 - cz * cz)
-    centres = np.stack([cs * np.cos(cp), cs * np.sin(cp), cz], axis=1)
-    cosr = np.cos(np.deg2rad(radius_deg))
-    for c in centres:
-        m |= (v @ c) > cosr
+    r = np.deg2rad(radius_deg)
+    cosr = np.cos(r)
+    th = np.arccos(cz)
+    # pixels are ordered by decreasing z: test only the z-range of each disc
+    negz = -z
+    for k in range(count):
+        zhi = np.cos(max(th[k] - r, 0.0))
+        zlo = np.cos(min(th[k] + r, np.pi))
+        a = np.searchsorted(negz, -zhi, side="left")
+        b = np.searchsorted(negz, -zlo, side="right")
+        zz = z[a:b]
+        st = np.sqrt(np.maximum(0.0, (1.0 - zz) * (1.0 + zz)))
+        cs = np.sqrt(max(0.0, 1.0 - cz[k] * cz[k]))
+        dot = st * cs * np.cos(phi[a:b] - cp[k]) + zz * cz[k]
+        m[a:b] |= dot > cosr
     return m
 
 

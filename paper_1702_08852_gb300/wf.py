@@ -34,7 +34,8 @@ class wf_opts(ctypes.Structure):
                 ("eps_cap", ctypes.c_double), ("mu0", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("stop_rule", ctypes.c_int),
                 ("precision", ctypes.c_int), ("band_limit", ctypes.c_int),
-                ("graph_chunk", ctypes.c_int), ("refine_max", ctypes.c_int)]
+                ("graph_chunk", ctypes.c_int), ("refine_max", ctypes.c_int),
+                ("timing", ctypes.c_int)]
 
 
 class wf_stats(ctypes.Structure):
@@ -76,6 +77,9 @@ def lib():
             "wf_npix": (ctypes.c_long, [I]),
             "wf_nalm": (ctypes.c_long, [I]),
             "wf_trace": (I, [_P, ctypes.POINTER(I), _P, _P, _P, _P]),
+            "wf_kernel_stats": (I, [_P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long),
+                                    ctypes.POINTER(D), I]),
+            "wf_legendre_terms": (I, [_P, I, ctypes.POINTER(D)]),
             "wf_destroy": (None, [_P]),
             "wf_status_str": (ctypes.c_char_p, [I]),
             "wf_last_error": (ctypes.c_char_p, []),
@@ -253,6 +257,18 @@ class Plan:
         k = n.value
         return {"stage": st[:k], "xi": xi[:k], "mu": mu[:k], "cauchy": c[:k]}
 
+    def kernel_stats(self, kernel=0, reset=False):
+        ms, n, gf = ctypes.c_double(), ctypes.c_long(), ctypes.c_double()
+        _check(lib().wf_kernel_stats(self.handle, int(kernel), ctypes.byref(ms),
+                                     ctypes.byref(n), ctypes.byref(gf), int(reset)))
+        return {"ms": ms.value, "launches": n.value, "gflop": gf.value}
+
+    def legendre_terms(self, L=None):
+        t = ctypes.c_double()
+        _check(lib().wf_legendre_terms(self.handle, self.lmax if L is None else int(L),
+                                       ctypes.byref(t)))
+        return t.value
+
     def close(self):
         if getattr(self, "handle", None):
             lib().wf_destroy(self.handle)
@@ -307,6 +323,14 @@ def wf_set_cl(plan, cl):
 
 def wf_trace(plan):
     return plan.trace()
+
+
+def wf_kernel_stats(plan, kernel=0, reset=False):
+    return plan.kernel_stats(kernel, reset)
+
+
+def wf_legendre_terms(plan, L=None):
+    return plan.legendre_terms(L)
 
 
 def wf_destroy(plan):

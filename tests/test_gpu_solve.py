@@ -174,3 +174,22 @@ def test_plan_rejects_bad_noise(torch_cuda):
     mk[3] = 1
     nv[3] = float("nan")   # masked: ignored
     wf.Plan(nside, lmax, np.ones(lmax + 1), nv, mk).close()
+
+
+@pytest.mark.parametrize("nside,kind,seed", [(16, "lognormal", 8), (32, "lognormal", 1000),
+                                             (32, "scan", 9)])
+def test_mixed_precision_reaches_fp64_fixed_point(torch_cuda, osht, odm, nside, kind, seed):
+    """FP32 transforms for the cooling stages, FP64-anchored last stage: the
+    result matches the FP64 fixed point (dense solve) to 1e-6 relative L2."""
+    torch = torch_cuda
+    kw = {"discs": 40} if kind == "scan" else {}
+    p, d = problem(osht, kind, nside, seed, **kw)
+    alm, mp, st, tr = gpu_solve(torch, p, d, precision=1, eps_final=1e-7)
+    assert st["converged"] == 1
+    assert st["refinements"] >= 1
+    Y = osht.ymatrix(p.nside, p.lmax)
+    ref = odm.dm_fixed_point_dense(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d, 0.0, Y=Y)
+    sref = Y @ osht.alm_to_real(ref, p.lmax)
+    err = np.linalg.norm(mp - sref) / np.linalg.norm(sref)
+    assert err < 1e-6, err
+    assert st["fp_residual"] < 1e-6
