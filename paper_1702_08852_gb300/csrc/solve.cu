@@ -51,6 +51,10 @@ __device__ int band_of(const double *cl, int lmax, double mu, double omega,
 
 constexpr int CTRL_THREADS = 256;
 
+// mixed precision: the anchored last stage re-anchors when |delta| exceeds
+// ANCHOR_CAP |x_a|, which bounds the FP32 transform error it carries
+constexpr double ANCHOR_CAP = 1e-3;
+
 
 __global__ void __launch_bounds__(CTRL_THREADS)
     k_control(SolverState *st, const double *__restrict__ partials, int lmax,
@@ -568,6 +572,12 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
     WF_CUDA(cudaMemcpyAsync(P.xacc, P.x, sizeof(double2) * P.nalm,
                             cudaMemcpyDeviceToDevice, P.stream));
     const int lfinal = P.opts.band_limit ? band_host(P.cl, 0.0, P.omega) : P.lmax;
+    // A cycle runs until its error estimate (relative to |x_a|) is below
+    // eps_final; its correction |delta| is then (up to the FP32 transform
+    // error amplified by the slow modes) the error of the iterate it
+    // corrected.  Done when that correction, or the one predicted for the
+    // next cycle from the observed contraction, is below eps_final.
+    double prev_rel = -1.0;
     for (int k = 0; reached_final && k <= P.opts.refine_max; ++k) {
       double num = 0.0, xn = 0.0;
       WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num));
@@ -585,7 +595,7 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       s.iter = total_iter;
       s.max_iter = P.opts.max_iter;
       s.den_fixed = xn;
-      s.delta_cap2 = 1e-4 * xn;
+      s.delta_cap2 = ANCHOR_CAP * ANCHOR_CAP * xn;
       *P.state_h = s;
       WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
                               cudaMemcpyHostToDevice, P.stream));
@@ -595,14 +605,20 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
         set_error("wf_solve: NaN or Inf in the anchored last stage");
         return WF_ERR_NUMERIC;
       }
+      double dn = 0.0;
+      WF_TRY(alm_dot(P, P.x, P.x, nullptr, &dn));
       k_alm_add<<<304, 256, 0, P.stream>>>(P.xacc, P.x, P.nalm);
       WF_CUDA(cudaGetLastError());
       ++refinements;
-      if (P.state_h->converged) {
+      if (P.state_h->reanchor) continue;   // |delta| hit the cap: new anchor
+      if (!P.state_h->converged) break;    // max_iter
+      const double rel = xn > 0.0 ? sqrt(dn / xn) : 0.0;
+      if (rel < P.opts.eps_final ||
+          (prev_rel > 0.0 && rel * (rel / prev_rel) < P.opts.eps_final / 3.0)) {
         converged = true;
         break;
       }
-      if (!P.state_h->reanchor) break;  // max_iter
+      prev_rel = rel;
     }
     {
       const SolverState keep = *P.state_h;

@@ -191,5 +191,5 @@ def test_mixed_precision_reaches_fp64_fixed_point(torch_cuda, osht, odm, nside, 
     ref = odm.dm_fixed_point_dense(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d, 0.0, Y=Y)
     sref = Y @ osht.alm_to_real(ref, p.lmax)
     err = np.linalg.norm(mp - sref) / np.linalg.norm(sref)
-    assert err < 1e-6, err
+    assert err < 1e-6, (err, st)
     assert st["fp_residual"] < 1e-6
