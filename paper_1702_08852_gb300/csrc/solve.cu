@@ -53,7 +53,8 @@ constexpr int CTRL_THREADS = 256;
 
 // mixed precision: the anchored last stage re-anchors when |delta| exceeds
 // ANCHOR_CAP |x_a|, which bounds the FP32 transform error it carries
-constexpr double ANCHOR_CAP = 1e-3;
+constexpr double ANCHOR_CAP = 1e-2;
+constexpr int MAX_REANCHORS = 64;
 
 
 __global__ void __launch_bounds__(CTRL_THREADS)
@@ -578,7 +579,8 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
     // corrected.  Done when that correction, or the one predicted for the
     // next cycle from the observed contraction, is below eps_final.
     double prev_rel = -1.0;
-    for (int k = 0; reached_final && k <= P.opts.refine_max; ++k) {
+    int cycles = 0, reanchors = 0;
+    while (reached_final && cycles <= P.opts.refine_max && reanchors <= MAX_REANCHORS) {
       double num = 0.0, xn = 0.0;
       WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num));
       WF_TRY(alm_dot(P, P.xacc, P.xacc, nullptr, &xn));
@@ -610,8 +612,12 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       k_alm_add<<<304, 256, 0, P.stream>>>(P.xacc, P.x, P.nalm);
       WF_CUDA(cudaGetLastError());
       ++refinements;
-      if (P.state_h->reanchor) continue;   // |delta| hit the cap: new anchor
-      if (!P.state_h->converged) break;    // max_iter
+      if (P.state_h->reanchor) {  // |delta| hit the cap: new anchor
+        ++reanchors;
+        continue;
+      }
+      if (!P.state_h->converged) break;  // max_iter
+      ++cycles;
       const double rel = xn > 0.0 ? sqrt(dn / xn) : 0.0;
       if (rel < P.opts.eps_final ||
           (prev_rel > 0.0 && rel * (rel / prev_rel) < P.opts.eps_final / 3.0)) {
