@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(CTRL_THREADS)
         st->stagnated = 1;
       } else if (st->stop_rule == WF_STOP_ERROR) {
         if (st->prev_c > 0.0 && c > 0.0) {
-          const double r = fmin(c / st->prev_c, 0.999999);
+          const double r = fmin(fmax(c / st->prev_c, st->rate_floor), 0.999999);
           const double err = c * r / (1.0 - r);
           st->err_est = err;
           if (err < st->eps_final) {
@@ -308,6 +308,7 @@ static SolverState initial_state(const Plan &P) {
   s.at_final = 0;
   s.reanchor = 0;
   s.den_fixed = 0.0;
+  s.rate_floor = 0.0;
   s.delta_cap2 = 0.0;
   s.last_den = 0.0;
   if (o.band_limit) {
@@ -524,6 +525,29 @@ static wf_status account_work(Plan &P, int i0, int i1) {
   return WF_OK;
 }
 
+// Contraction rate of the slow modes, fitted to the Cauchy ratios of the
+// iterations [i0, i1) of the trace: the geometric decay rate over the last
+// stretch where c is still far (30x) above its final value (the FP32 noise
+// floor, where the ratio tends to 1 and says nothing about convergence).
+static wf_status slow_rate(Plan &P, int i0, int i1, double *rate) {
+  *rate = 0.0;
+  i1 = std::min(i1, P.trace_cap);
+  if (i1 - i0 < 8) return WF_OK;
+  std::vector<TraceEntry> h(i1 - i0);
+  WF_CUDA(cudaMemcpy(h.data(), P.trace + i0, sizeof(TraceEntry) * h.size(),
+                     cudaMemcpyDeviceToHost));
+  const int n = (int)h.size();
+  const double cfin = h[n - 1].cauchy;
+  int j = n - 1;
+  while (j > 0 && !(h[j].cauchy > 30.0 * cfin)) --j;
+  const int span = std::max(8, j / 5);
+  const int i = std::max(0, j - span);
+  if (j - i < 4 || !(h[i].cauchy > 0.0) || !(h[j].cauchy > 0.0)) return WF_OK;
+  const double r = pow(h[j].cauchy / h[i].cauchy, 1.0 / (double)(j - i));
+  if (r > 0.0 && r < 1.0) *rate = r;
+  return WF_OK;
+}
+
 wf_status solve(Plan &P, const double *d, double *alm, double *map,
                 const double *init_alm, const double *init_map, wf_stats *stats) {
   if (!P.has_noise) {
@@ -578,8 +602,8 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
     // error amplified by the slow modes) the error of the iterate it
     // corrected.  Done when that correction, or the one predicted for the
     // next cycle from the observed contraction, is below eps_final.
-    double prev_rel = -1.0;
-    int cycles = 0, reanchors = 0;
+    double prev_rel = -1.0, rate_floor = 0.0;
+    int cycles = 0, reanchors = 0, cycle_start = total_iter;
     while (reached_final && cycles <= P.opts.refine_max && reanchors <= MAX_REANCHORS) {
       double num = 0.0, xn = 0.0;
       WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num));
@@ -598,6 +622,7 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       s.max_iter = P.opts.max_iter;
       s.den_fixed = xn;
       s.delta_cap2 = ANCHOR_CAP * ANCHOR_CAP * xn;
+      s.rate_floor = rate_floor;
       *P.state_h = s;
       WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
                               cudaMemcpyHostToDevice, P.stream));
@@ -618,6 +643,14 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       }
       if (!P.state_h->converged) break;  // max_iter
       ++cycles;
+      // later cycles start with a residual in which slow modes are nearly
+      // invisible; their error estimate uses this cycle's slow-mode rate
+      {
+        double r = 0.0;
+        WF_TRY(slow_rate(P, cycle_start, total_iter, &r));
+        rate_floor = std::max(rate_floor, r);
+      }
+      cycle_start = total_iter;
       const double rel = xn > 0.0 ? sqrt(dn / xn) : 0.0;
       if (rel < P.opts.eps_final ||
           (prev_rel > 0.0 && rel * (rel / prev_rel) < P.opts.eps_final / 3.0)) {

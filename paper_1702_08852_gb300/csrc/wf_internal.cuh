@@ -67,6 +67,8 @@ struct SolverState {
   int at_final;   // set when the run stopped because of handoff
   int reanchor;   // set when the correction grew past delta_cap2
   double den_fixed;   // > 0: Cauchy denominator ||x||^2 of an anchored stage
+  double rate_floor;  // lower bound of the contraction rate used by the
+                      // error estimate (slow-mode rate of an earlier cycle)
   double delta_cap2;  // > 0: stop when ||delta||^2 exceeds it (re-anchor)
   double last_den;    // ||x_new||^2 of the last iteration
 };
