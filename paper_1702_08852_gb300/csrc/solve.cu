@@ -329,12 +329,12 @@ static wf_status enqueue_iteration(Plan &P, T2 *F, T2 *G, const double *data,
                                    const double2 *src, int slot) {
   const bool timed = slot >= 0 && P.tev_chunk > 0;
   const int C = P.tev_chunk;
-  if (timed) WF_CUDA(cudaEventRecord(P.tev[0 * C + slot], P.stream));
+  if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[0 * C + slot], P.stream, cudaEventRecordExternal));
   WF_TRY(launch_legendre_anal<T2>(P, G, P.x, P.state, ANA_FILTER, P.lmax, src));
-  if (timed) WF_CUDA(cudaEventRecord(P.tev[1 * C + slot], P.stream));
-  if (timed) WF_CUDA(cudaEventRecord(P.tev[2 * C + slot], P.stream));
+  if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[1 * C + slot], P.stream, cudaEventRecordExternal));
+  if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[2 * C + slot], P.stream, cudaEventRecordExternal));
   WF_TRY(launch_legendre_synth<T2>(P, P.x, F, P.state, P.lmax));
-  if (timed) WF_CUDA(cudaEventRecord(P.tev[3 * C + slot], P.stream));
+  if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[3 * C + slot], P.stream, cudaEventRecordExternal));
   WF_TRY(launch_ring<T2>(P, RING_FUSED, F, G, data, nullptr, P.state, P.lmax));
   k_control<<<1, CTRL_THREADS, 0, P.stream>>>(P.state, P.partials, P.lmax, P.cl_d,
                                               P.trace);
