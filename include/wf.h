@@ -153,6 +153,13 @@ wf_status wf_residual(wf_plan_t plan, const double *d_dev, const double *alm_dev
 wf_status wf_alm2map(wf_plan_t plan, const double *alm_dev, double *map_dev);
 wf_status wf_map2alm(wf_plan_t plan, const double *map_dev, double *alm_dev);
 
+/* The same transforms computed with the FP32 kernels of WF_PREC_MIXED (FP64
+ * recurrence seeds, FP32 recurrence, accumulation and ring FFTs); FP64 in
+ * and out.  Their error against wf_alm2map / wf_map2alm is the transform
+ * error the mixed-precision solve works with. */
+wf_status wf_alm2map_f32(wf_plan_t plan, const double *alm_dev, double *map_dev);
+wf_status wf_map2alm_f32(wf_plan_t plan, const double *map_dev, double *alm_dev);
+
 /* Sizes of a plan. */
 long wf_npix(int nside);
 long wf_nalm(int lmax);

@@ -265,6 +265,22 @@ wf_status wf_map2alm(wf_plan_t plan, const double *map_dev, double *alm_dev) {
   return WF_OK;
 }
 
+wf_status wf_alm2map_f32(wf_plan_t plan, const double *alm_dev, double *map_dev) {
+  if (!plan) return arg_error("wf_alm2map_f32: plan is NULL");
+  if (!alm_dev || !map_dev) return arg_error("wf_alm2map_f32: NULL buffer");
+  WF_TRY(alm2map_f32(*plan, alm_dev, map_dev));
+  WF_CUDA(cudaStreamSynchronize(plan->stream));
+  return WF_OK;
+}
+
+wf_status wf_map2alm_f32(wf_plan_t plan, const double *map_dev, double *alm_dev) {
+  if (!plan) return arg_error("wf_map2alm_f32: plan is NULL");
+  if (!alm_dev || !map_dev) return arg_error("wf_map2alm_f32: NULL buffer");
+  WF_TRY(map2alm_f32(*plan, map_dev, alm_dev));
+  WF_CUDA(cudaStreamSynchronize(plan->stream));
+  return WF_OK;
+}
+
 wf_status wf_trace(wf_plan_t plan, int *count, int *stage, double *xi, double *mu,
                    double *cauchy) {
   if (!plan || !count) return arg_error("wf_trace: NULL argument");

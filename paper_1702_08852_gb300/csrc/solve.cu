@@ -55,6 +55,8 @@ constexpr int CTRL_THREADS = 256;
 // ANCHOR_CAP |x_a|, which bounds the FP32 transform error it carries
 constexpr double ANCHOR_CAP = 1e-2;
 constexpr int MAX_REANCHORS = 64;
+// tolerance scale of the FP32 cooling stages (their fixed points only steer)
+constexpr double STAGE_EPS_FP32 = 1e-5;
 
 
 __global__ void __launch_bounds__(CTRL_THREADS)
@@ -125,8 +127,9 @@ __global__ void __launch_bounds__(CTRL_THREADS)
         st->done = 1;
         st->converged = 1;
       }
-    } else if (c < st->eps_k) {
-      adv = 1;
+    } else {
+      st->flat = (st->prev_c > 0.0 && c >= st->prev_c) ? st->flat + 1 : 0;
+      if (c < st->eps_k || (st->noise_guard && st->flat >= 16 && c < 1e-3)) adv = 1;
     }
     st->prev_c = c;
     st->last_c = c;
@@ -137,6 +140,7 @@ __global__ void __launch_bounds__(CTRL_THREADS)
       st->stage += 1;
       st->stage_iter = 0;
       st->prev_c = -1.0;
+      st->flat = 0;
       st->eps_k = st->mu == 0.0
                       ? st->eps_final
                       : fmin(st->eps_cap, st->eps_final * fmax(1.0, st->mu / st->alpha));
@@ -266,6 +270,22 @@ wf_status map2alm(Plan &P, const double *map, double *alm) {
   return WF_OK;
 }
 
+wf_status alm2map_f32(Plan &P, const double *alm, double *map) {
+  const double2 *a = reinterpret_cast<const double2 *>(alm);
+  WF_TRY(launch_legendre_synth<float2>(P, a, P.F32, nullptr, P.lmax));
+  WF_TRY(launch_ring<float2>(P, RING_SYNTH, P.F32, nullptr, nullptr, map, nullptr,
+                             P.lmax));
+  return WF_OK;
+}
+
+wf_status map2alm_f32(Plan &P, const double *map, double *alm) {
+  WF_TRY(launch_ring<float2>(P, RING_ANALYSIS, nullptr, P.G32, map, nullptr, nullptr,
+                             P.lmax));
+  WF_TRY(launch_legendre_anal<float2>(P, P.G32, reinterpret_cast<double2 *>(alm),
+                                      nullptr, ANA_PLAIN, P.lmax));
+  return WF_OK;
+}
+
 // ---------------------------------------------------------------- solve
 static int band_host(const std::vector<double> &cl, double mu, double omega) {
   int b = -1;
@@ -305,6 +325,7 @@ static SolverState initial_state(const Plan &P) {
   s.flat = 0;
   s.stagnated = 0;
   s.handoff = 0;
+  s.noise_guard = 0;
   s.at_final = 0;
   s.reanchor = 0;
   s.den_fixed = 0.0;
@@ -578,6 +599,11 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
     int stage_final = 0;
     if (P.state_h->mu > 0.0) {
       P.state_h->handoff = 1;
+      P.state_h->noise_guard = 1;
+      // stage tolerances above the FP32 noise floor
+      P.state_h->eps_final = std::max(P.opts.eps_final, STAGE_EPS_FP32);
+      P.state_h->eps_k = std::min(P.opts.eps_cap, P.state_h->eps_final *
+                                                      std::max(1.0, P.state_h->mu / P.alpha));
       WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
                               cudaMemcpyHostToDevice, P.stream));
       WF_TRY(run_loop<float2>(P, 1, P.F32, P.G32, tinit, P.dmap, nullptr));
@@ -623,6 +649,7 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       s.den_fixed = xn;
       s.delta_cap2 = ANCHOR_CAP * ANCHOR_CAP * xn;
       s.rate_floor = rate_floor;
+      s.noise_guard = 1;
       *P.state_h = s;
       WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
                               cudaMemcpyHostToDevice, P.stream));

@@ -64,6 +64,9 @@ struct SolverState {
   int flat;       // consecutive last-stage iterations without a Cauchy decrease
   int stagnated;  // the last stage stopped at the arithmetic noise floor
   int handoff;    // 1: stop (done, not converged) on entering the mu = 0 stage
+  int noise_guard;  // 1 (FP32 passes): a stage whose Cauchy ratio stops
+                    // falling below 1e-3 has reached the arithmetic noise
+                    // floor and ends
   int at_final;   // set when the run stopped because of handoff
   int reanchor;   // set when the correction grew past delta_cap2
   double den_fixed;   // > 0: Cauchy denominator ||x||^2 of an anchored stage
@@ -188,6 +191,8 @@ wf_status residual(Plan &P, const double *d, const double *alm, double *res_wf,
                    double *res_fp, double *chi2);
 wf_status alm2map(Plan &P, const double *alm, double *map);
 wf_status map2alm(Plan &P, const double *map, double *alm);
+wf_status alm2map_f32(Plan &P, const double *alm, double *map);
+wf_status map2alm_f32(Plan &P, const double *map, double *alm);
 wf_status legendre_terms(Plan &P, int L, double *terms);
 
 }  // namespace wf

@@ -74,6 +74,8 @@ def lib():
                                 ctypes.POINTER(D)]),
             "wf_alm2map": (I, [_P, _P, _P]),
             "wf_map2alm": (I, [_P, _P, _P]),
+            "wf_alm2map_f32": (I, [_P, _P, _P]),
+            "wf_map2alm_f32": (I, [_P, _P, _P]),
             "wf_npix": (ctypes.c_long, [I]),
             "wf_nalm": (ctypes.c_long, [I]),
             "wf_trace": (I, [_P, ctypes.POINTER(I), _P, _P, _P, _P]),
@@ -243,6 +245,24 @@ class Plan:
         _check(lib().wf_map2alm(self.handle,
                                 _dev_ptr(m, torch.float64, self.npix, "map"),
                                 _dev_ptr(out, torch.complex128, self.nalm, "alm")))
+        return out
+
+    def alm2map_f32(self, alm, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.npix, dtype=torch.float64, device=alm.device)
+        _check(lib().wf_alm2map_f32(self.handle,
+                                    _dev_ptr(alm, torch.complex128, self.nalm, "alm"),
+                                    _dev_ptr(out, torch.float64, self.npix, "map")))
+        return out
+
+    def map2alm_f32(self, m, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.nalm, dtype=torch.complex128, device=m.device)
+        _check(lib().wf_map2alm_f32(self.handle,
+                                    _dev_ptr(m, torch.float64, self.npix, "map"),
+                                    _dev_ptr(out, torch.complex128, self.nalm, "alm")))
         return out
 
     def trace(self, cap=1 << 20):
