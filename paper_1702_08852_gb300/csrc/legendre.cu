@@ -71,6 +71,24 @@ __device__ __forceinline__ int warp_max(int v) {
   return v;
 }
 
+// One step of u_l = c_l z u_{l-1} - u_{l-2}.  In FP32, z = cos(theta) is
+// carried as zh + zl (two floats): rounding z alone to FP32 displaces a ring
+// near the pole by ~6e-8 / sin(theta) rad, a phase error of l times that.
+__device__ __forceinline__ double rec_step(double c, double zh, double, double u1,
+                                           double u2) {
+  return fma(c * zh, u1, -u2);
+}
+__device__ __forceinline__ float rec_step(float c, float zh, float zl, float u1,
+                                          float u2) {
+  const float a = c * u1;
+  return fmaf(a, zh, fmaf(a, zl, -u2));
+}
+template <typename T>
+__device__ __forceinline__ void split_z(double z, T &zh, T &zl) {
+  zh = (T)z;
+  zl = (T)(z - (double)zh);
+}
+
 static inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 __device__ __forceinline__ size_t align16d(size_t b) { return (b + 15) & ~(size_t)15; }
 
@@ -111,7 +129,7 @@ __global__ void __launch_bounds__(SYN_THREADS)
   const int pair0 = (blockIdx.x * (SYN_THREADS / 32) + warp) * 32 * NP;
   if (pair0 >= npairs) return;
 
-  T z[NP], u1[NP], u2[NP], s0[NP], s1[NP];
+  T zh[NP], zl[NP], u1[NP], u2[NP], s0[NP], s1[NP];
   T er[NP], ei[NP], orr[NP], oi[NP];
   int ls[NP];
   int lmin = INT_MAX, linj = -1;
@@ -120,13 +138,13 @@ __global__ void __launch_bounds__(SYN_THREADS)
     const int k = pair0 + lane + 32 * j;
     u1[j] = u2[j] = er[j] = ei[j] = orr[j] = oi[j] = (T)0;
     if (k < npairs) {
-      z[j] = (T)pairs[k].z;
+      split_z<T>(pairs[k].z, zh[j], zl[j]);
       ls[j] = seed_l[(long)m * npairs + k];
       const double2 su = seed_u[(long)m * npairs + k];
       s0[j] = (T)su.x;
       s1[j] = (T)su.y;
     } else {
-      z[j] = (T)0;
+      zh[j] = zl[j] = (T)0;
       ls[j] = INT_MAX - 2;
       s0[j] = s1[j] = (T)0;
     }
@@ -152,7 +170,7 @@ __global__ void __launch_bounds__(SYN_THREADS)
         if (ll > L) xv = Vec2<T>::make((T)0, (T)0);
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-          T u = fma(c * z[j], u1[j], -u2[j]);
+          T u = rec_step(c, zh[j], zl[j], u1[j], u2[j]);
           u = (ll == ls[j]) ? s0[j] : u;
           u = (ll == ls[j] + 1) ? s1[j] : u;
           u2[j] = u1[j];
@@ -173,10 +191,10 @@ __global__ void __launch_bounds__(SYN_THREADS)
       const T2 x0 = sx[l - m], x1 = sx[l + 1 - m];
 #pragma unroll
       for (int j = 0; j < NP; ++j) {
-        T u = fma(c0 * z[j], u1[j], -u2[j]);
+        T u = rec_step(c0, zh[j], zl[j], u1[j], u2[j]);
         er[j] = fma(u, x0.x, er[j]);
         ei[j] = fma(u, x0.y, ei[j]);
-        T v = fma(c1 * z[j], u, -u1[j]);
+        T v = rec_step(c1, zh[j], zl[j], u, u1[j]);
         orr[j] = fma(v, x1.x, orr[j]);
         oi[j] = fma(v, x1.y, oi[j]);
         u2[j] = u;
@@ -188,7 +206,7 @@ __global__ void __launch_bounds__(SYN_THREADS)
       const T2 x0 = sx[l - m];
 #pragma unroll
       for (int j = 0; j < NP; ++j) {
-        T u = fma(c0 * z[j], u1[j], -u2[j]);
+        T u = rec_step(c0, zh[j], zl[j], u1[j], u2[j]);
         er[j] = fma(u, x0.x, er[j]);
         ei[j] = fma(u, x0.y, ei[j]);
       }
@@ -210,6 +228,7 @@ __global__ void __launch_bounds__(SYN_THREADS)
 constexpr int ANA_THREADS = 128;
 constexpr int ANA_WARPS = ANA_THREADS / 32;
 constexpr int LCHUNK = 16;
+constexpr int ANA_NP = 4;  // ring pairs per thread in the analysis
 
 // v[0..31] per lane -> lane i returns sum over lanes of v[i]
 template <typename T>
@@ -269,7 +288,7 @@ __global__ void __launch_bounds__(ANA_THREADS)
     for (int tile = 0; tile < npairs; tile += ANA_THREADS * NP) {
       const int pair0 = tile + warp * 32 * NP;
       if (pair0 >= npairs) continue;  // warp-uniform
-      T z[NP], u1[NP], u2[NP], s0[NP], s1[NP];
+      T zh[NP], zl[NP], u1[NP], u2[NP], s0[NP], s1[NP];
       T pr[NP], pim[NP], qr[NP], qim[NP];
       int ls[NP];
       int lmin = INT_MAX, linj = -1;
@@ -279,7 +298,7 @@ __global__ void __launch_bounds__(ANA_THREADS)
         u1[j] = u2[j] = (T)0;
         if (k < npairs) {
           const RingPair &rp = pairs[k];
-          z[j] = (T)rp.z;
+          split_z<T>(rp.z, zh[j], zl[j]);
           ls[j] = seed_l[(long)m * npairs + k];
           const double2 su = seed_u[(long)m * npairs + k];
           s0[j] = (T)su.x;
@@ -292,7 +311,7 @@ __global__ void __launch_bounds__(ANA_THREADS)
           qr[j] = gn.x - gs.x;
           qim[j] = gn.y - gs.y;
         } else {
-          z[j] = s0[j] = s1[j] = pr[j] = pim[j] = qr[j] = qim[j] = (T)0;
+          zh[j] = zl[j] = s0[j] = s1[j] = pr[j] = pim[j] = qr[j] = qim[j] = (T)0;
           ls[j] = INT_MAX - 2;
         }
         if (ls[j] <= L) {
@@ -315,7 +334,7 @@ __global__ void __launch_bounds__(ANA_THREADS)
             const T c = sc[l - m];
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
-              T u = fma(c * z[j], u1[j], -u2[j]);
+              T u = rec_step(c, zh[j], zl[j], u1[j], u2[j]);
               if (inj) {
                 u = (l == ls[j]) ? s0[j] : u;
                 u = (l == ls[j] + 1) ? s1[j] : u;
@@ -436,7 +455,7 @@ wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
                                const SolverState *st, int mode, int lstatic,
                                const double2 *src) {
   typedef typename Kernels<T2>::T T;
-  constexpr int NP = 2;
+  constexpr int NP = ANA_NP;
   auto kern = k_legendre_anal<T, NP>;
   const size_t smem =
       align16(sizeof(T2) * (P.lmax + 1) * ANA_WARPS) + sizeof(T) * (P.lmax + 1);
@@ -453,9 +472,9 @@ wf_status init_legendre_attributes() {
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   WF_CUDA(cudaFuncSetAttribute(k_legendre_synth<float, 2>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal<double, 2>,
+  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal<double, ANA_NP>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal<float, 2>,
+  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal<float, ANA_NP>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return WF_OK;
 }

@@ -50,6 +50,7 @@ __device__ int band_of(const double *cl, int lmax, double mu, double omega,
 }
 
 constexpr int CTRL_THREADS = 256;
+constexpr int PLATEAU_ITERS = 64;
 
 // mixed precision: the anchored last stage re-anchors when |delta| exceeds
 // ANCHOR_CAP |x_a|, which bounds the FP32 transform error it carries
@@ -99,13 +100,22 @@ __global__ void __launch_bounds__(CTRL_THREADS)
       trace[it - 1] = e;
     }
     int adv = 0;
+    // progress tracker: an FP32 pass whose Cauchy ratio has not fallen by 1%
+    // in PLATEAU_ITERS iterations sits at its arithmetic noise floor
+    if (!(st->cmin > 0.0) || c < 0.99 * st->cmin) {
+      st->cmin = c;
+      st->since_min = 0;
+    } else {
+      st->since_min += 1;
+    }
+    const bool plateau = st->noise_guard && st->since_min >= PLATEAU_ITERS && c < 1e-3;
     if (!isfinite(c) || !isfinite(num)) {
       st->numeric_error = 1;
       st->done = 1;
     } else if (st->mu == 0.0) {
       // arithmetic noise floor: the Cauchy ratio has stopped falling
       st->flat = (st->prev_c > 0.0 && c >= st->prev_c) ? st->flat + 1 : 0;
-      if (st->flat >= 16 && c < 1e-4) {
+      if ((st->flat >= 16 && c < 1e-4) || plateau) {
         st->done = 1;
         st->converged = 1;
         st->stagnated = 1;
@@ -128,8 +138,7 @@ __global__ void __launch_bounds__(CTRL_THREADS)
         st->converged = 1;
       }
     } else {
-      st->flat = (st->prev_c > 0.0 && c >= st->prev_c) ? st->flat + 1 : 0;
-      if (c < st->eps_k || (st->noise_guard && st->flat >= 16 && c < 1e-3)) adv = 1;
+      if (c < st->eps_k || plateau) adv = 1;
     }
     st->prev_c = c;
     st->last_c = c;
@@ -141,6 +150,8 @@ __global__ void __launch_bounds__(CTRL_THREADS)
       st->stage_iter = 0;
       st->prev_c = -1.0;
       st->flat = 0;
+      st->cmin = -1.0;
+      st->since_min = 0;
       st->eps_k = st->mu == 0.0
                       ? st->eps_final
                       : fmin(st->eps_cap, st->eps_final * fmax(1.0, st->mu / st->alpha));
@@ -330,6 +341,8 @@ static SolverState initial_state(const Plan &P) {
   s.reanchor = 0;
   s.den_fixed = 0.0;
   s.rate_floor = 0.0;
+  s.cmin = -1.0;
+  s.since_min = 0;
   s.delta_cap2 = 0.0;
   s.last_den = 0.0;
   if (o.band_limit) {

@@ -74,6 +74,8 @@ struct SolverState {
                       // error estimate (slow-mode rate of an earlier cycle)
   double delta_cap2;  // > 0: stop when ||delta||^2 exceeds it (re-anchor)
   double last_den;    // ||x_new||^2 of the last iteration
+  double cmin;        // smallest Cauchy ratio of the stage so far
+  int since_min;      // iterations since cmin last fell by 1%
 };
 
 struct TraceEntry {
