@@ -104,7 +104,8 @@ def dual_messenger(nside, lmax, cl, noise_var, mask, d, beta=0.75,
 
     Returns (alm, info).  ``stop`` = "cauchy" ends the last stage when the
     Cauchy ratio drops below eps_final; "error" ends it when the geometric
-    error estimate c_i * r/(1-r), r = c_i / c_{i-1}, does.
+    error estimate c_i * r/(1-r) does, r = max(c_i / c_{i-1},
+    (c_i / c_{i-16})^(1/16)).
     ``stage_callback(stage, xi, mu, alm)`` is called at the end of each
     stage; ``trace`` (a list) receives (stage, xi, mu, cauchy) per iteration.
     """
@@ -128,6 +129,7 @@ def dual_messenger(nside, lmax, cl, noise_var, mask, d, beta=0.75,
         w = pixel_weight(noise_var, mask, xi, mu)
         eps = stage_eps(mu, a, eps_final, eps_cap)
         prev_c = None
+        hist = []
         while True:
             x_new = f * (om * T.adjoint(t))
             s = T.synth(x_new)
@@ -140,9 +142,13 @@ def dual_messenger(nside, lmax, cl, noise_var, mask, d, beta=0.75,
             if trace is not None:
                 trace.append((stage, xi, mu, c))
             if mu == 0.0 and stop == "error":
-                # last stage: stop on the geometric error estimate instead
-                if prev_c is not None and prev_c > 0 and c > 0:
-                    r = min(c / prev_c, 0.999999)
+                # last stage: stop on the geometric error estimate c r/(1-r);
+                # r is the larger of the last ratio and the mean ratio over
+                # 16 iterations, so at least 17 iterations are needed
+                hist.append(c)
+                if len(hist) > 16 and prev_c and c > 0:
+                    r = max(c / prev_c, (c / hist[-17]) ** (1.0 / 16.0))
+                    r = min(r, 0.999999)
                     if c * r / (1.0 - r) < eps_final:
                         converged = True
                         break

@@ -89,7 +89,10 @@ __global__ void __launch_bounds__(CTRL_THREADS)
     if (st->den_fixed > 0.0) den = st->den_fixed;
     const double c = den > 0.0 ? sqrt(num / den) : 0.0;
     const int it = ++st->iter;
-    st->stage_iter += 1;
+    const int si = st->stage_iter;          // iterations of this stage before this one
+    const double c16 = si >= 16 ? st->chist[si % 16] : -1.0;  // 16 iterations ago
+    st->chist[si % 16] = c;
+    st->stage_iter = si + 1;
     if (trace && it - 1 < st->trace_cap) {
       TraceEntry e;
       e.stage = st->stage;
@@ -120,8 +123,13 @@ __global__ void __launch_bounds__(CTRL_THREADS)
         st->converged = 1;
         st->stagnated = 1;
       } else if (st->stop_rule == WF_STOP_ERROR) {
-        if (st->prev_c > 0.0 && c > 0.0) {
-          const double r = fmin(fmax(c / st->prev_c, st->rate_floor), 0.999999);
+        if (c16 > 0.0 && st->prev_c > 0.0 && c > 0.0) {
+          // contraction rate: the larger of the last ratio and the mean rate
+          // over 16 iterations (a few fast modes can make a single ratio
+          // small while slower modes still carry the error)
+          const double r1 = c / st->prev_c;
+          const double r16 = pow(c / c16, 1.0 / 16.0);
+          const double r = fmin(fmax(fmax(r1, r16), st->rate_floor), 0.999999);
           const double err = c * r / (1.0 - r);
           st->err_est = err;
           if (err < st->eps_final) {

@@ -74,6 +74,7 @@ struct SolverState {
                       // error estimate (slow-mode rate of an earlier cycle)
   double delta_cap2;  // > 0: stop when ||delta||^2 exceeds it (re-anchor)
   double last_den;    // ||x_new||^2 of the last iteration
+  double chist[16];   // Cauchy ratios of the last 16 iterations of the stage
   double cmin;        // smallest Cauchy ratio of the stage so far
   int since_min;      // iterations since cmin last fell by 1%
 };
