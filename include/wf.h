@@ -57,7 +57,8 @@ typedef enum { WF_PREC_FP64 = 0, WF_PREC_MIXED = 1 } wf_precision;
 typedef enum {
   WF_STOP_CAUCHY = 0, /* last stage ends when ||x_i - x_{i-1}|| / ||x_i|| < eps_final */
   WF_STOP_ERROR = 1   /* last stage ends when the geometric error estimate
-                         c_i r / (1 - r), r = c_i / c_{i-1}, is < eps_final */
+                         c_i r / (1 - r) is < eps_final, with r the larger of
+                         c_i / c_{i-1} and (c_i / c_{i-16})^(1/16) */
 } wf_stop_rule;
 
 /* Solver options.  Start from wf_opts_default() and override fields. */
@@ -69,7 +70,8 @@ typedef struct {
   double mu0;        /* initial mu in pixel-variance units; < 0 selects
                         mu0 * Omega = beta * max_l C_l (default -1) */
   int max_iter;      /* bound on the total number of iterations (default 200000) */
-  int stop_rule;     /* wf_stop_rule (default WF_STOP_ERROR) */
+  int stop_rule;     /* wf_stop_rule (default WF_STOP_CAUCHY, the paper's
+                        criterion of Sect. 3) */
   int precision;     /* wf_precision (default WF_PREC_FP64) */
   int band_limit;    /* 1: restrict each stage's transforms to the band where
                         the truncated spectrum is nonzero (exact; default 1) */

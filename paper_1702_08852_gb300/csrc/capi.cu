@@ -91,7 +91,7 @@ void wf_opts_default(wf_opts *o) {
   o->eps_cap = 1e-2;
   o->mu0 = -1.0;
   o->max_iter = 200000;
-  o->stop_rule = WF_STOP_ERROR;
+  o->stop_rule = WF_STOP_CAUCHY;
   o->precision = WF_PREC_FP64;
   o->band_limit = 1;
   o->graph_chunk = 0;

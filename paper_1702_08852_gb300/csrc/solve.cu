@@ -690,6 +690,17 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
         continue;
       }
       if (!P.state_h->converged) break;  // max_iter
+      // Cauchy rule (the paper's): the anchored stage ends like the FP64 one
+      // once ||x_i - x_{i-1}|| / ||x_i|| < eps_final; a stop at the FP32 noise
+      // floor instead re-anchors (the next delta is smaller, so is its floor)
+      if (P.opts.stop_rule == WF_STOP_CAUCHY) {
+        if (!P.state_h->stagnated) {
+          converged = true;
+          break;
+        }
+        ++reanchors;
+        continue;
+      }
       ++cycles;
       // later cycles start with a residual in which slow modes are nearly
       // invisible; their error estimate uses this cycle's slow-mode rate

@@ -75,7 +75,7 @@ def test_error_stop_rule_1e6(torch_cuda, osht, odm):
     a few 1e-6 of the converged solution."""
     torch = torch_cuda
     p, d = problem(osht, "lognormal", 16, 7)
-    alm, mp, st, _ = gpu_solve(torch, p, d)
+    alm, mp, st, _ = gpu_solve(torch, p, d, stop_rule=1)
     ref = odm.dm_fixed_point_dense(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d, 0.0)
     sref = osht.alm2map(ref, p.nside, p.lmax)
     assert np.linalg.norm(mp - sref) / np.linalg.norm(sref) < 3e-6
@@ -103,7 +103,7 @@ def test_trace_follows_the_oracle(torch_cuda, osht, odm):
     otr = []
     odm.dual_messenger(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d,
                        eps_final=1e-8, stop="error", trace=otr)
-    _, _, st, tr = gpu_solve(torch, p, d, eps_final=1e-8)
+    _, _, st, tr = gpu_solve(torch, p, d, eps_final=1e-8, stop_rule=1)
     ost = np.array([t[0] for t in otr])
     oc = np.array([t[3] for t in otr])
     n = min(len(oc), len(tr["cauchy"]), 200)
@@ -149,6 +149,22 @@ def test_host_entry_point_equals_device(torch_cuda, osht):
         assert np.array_equal(m1.cpu().numpy(), m2)
 
 
+def test_cauchy_rule_matches_oracle_and_mixed(torch_cuda, osht, odm):
+    """The paper's criterion (Cauchy ratio < eps in the last stage): FP64
+    stops at the oracle's iteration and result; the mixed path stops with a
+    Cauchy ratio below eps as well."""
+    torch = torch_cuda
+    p, d = problem(osht, "lognormal", 8, 41)
+    otr = []
+    xo, info = odm.dual_messenger(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d,
+                                  eps_final=1e-6, stop="cauchy", trace=otr)
+    alm, mp, st, tr = gpu_solve(torch, p, d, eps_final=1e-6)
+    assert abs(st["iterations"] - info["iterations"]) <= 2
+    assert rel_alm(osht, alm, xo, p.lmax) < 1e-8
+    alm2, mp2, st2, tr2 = gpu_solve(torch, p, d, eps_final=1e-6, precision=1)
+    assert st2["converged"] == 1 and tr2["cauchy"][-1] < 1e-6
+
+
 def test_deterministic(torch_cuda, osht):
     torch = torch_cuda
     p, d = problem(osht, "scan", 16, 5, discs=10)
@@ -184,7 +200,7 @@ def test_mixed_precision_reaches_fp64_fixed_point(torch_cuda, osht, odm, nside, 
     torch = torch_cuda
     kw = {"discs": 40} if kind == "scan" else {}
     p, d = problem(osht, kind, nside, seed, **kw)
-    alm, mp, st, tr = gpu_solve(torch, p, d, precision=1, eps_final=1e-7)
+    alm, mp, st, tr = gpu_solve(torch, p, d, precision=1, eps_final=1e-7, stop_rule=1)
     assert st["converged"] == 1
     assert st["refinements"] >= 1
     Y = osht.ymatrix(p.nside, p.lmax)
