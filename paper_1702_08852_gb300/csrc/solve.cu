@@ -50,14 +50,15 @@ __device__ int band_of(const double *cl, int lmax, double mu, double omega,
 }
 
 constexpr int CTRL_THREADS = 256;
-constexpr int PLATEAU_ITERS = 64;
+constexpr int PLATEAU_ITERS = 256;
 
 // mixed precision: the anchored last stage re-anchors when |delta| exceeds
 // ANCHOR_CAP |x_a|, which bounds the FP32 transform error it carries
 constexpr double ANCHOR_CAP = 1e-2;
-constexpr int MAX_REANCHORS = 64;
-// tolerance scale of the FP32 cooling stages (their fixed points only steer)
-constexpr double STAGE_EPS_FP32 = 1e-5;
+constexpr int MAX_REANCHORS = 4096;
+// stages whose tolerance is below ANCHOR_EPS run anchored (the plain FP32
+// iteration has a Cauchy noise floor near 1e-5 at lmax = 2048)
+constexpr double ANCHOR_EPS = 1e-4;
 
 
 __global__ void __launch_bounds__(CTRL_THREADS)
@@ -146,7 +147,16 @@ __global__ void __launch_bounds__(CTRL_THREADS)
         st->converged = 1;
       }
     } else {
-      if (c < st->eps_k || plateau) adv = 1;
+      if (c < st->eps_k) {
+        adv = 1;
+      } else if (plateau) {
+        if (st->boundary_stop) {  // anchored: stalled progress -> new anchor
+          st->done = 1;
+          st->reanchor = 1;
+        } else {
+          adv = 1;  // plain FP32 pass: the stage sits at its noise floor
+        }
+      }
     }
     st->prev_c = c;
     st->last_c = c;
@@ -168,6 +178,10 @@ __global__ void __launch_bounds__(CTRL_THREADS)
     if (adv && st->mu == 0.0 && st->handoff) {
       st->done = 1;
       st->at_final = 1;
+    }
+    if (adv && (st->boundary_stop || (st->anchor_eps > 0.0 && st->eps_k < st->anchor_eps))) {
+      st->done = 1;
+      st->at_boundary = 1;
     }
     if (!st->done && st->delta_cap2 > 0.0 && st->last_den > st->delta_cap2) {
       st->done = 1;
@@ -345,6 +359,9 @@ static SolverState initial_state(const Plan &P) {
   s.stagnated = 0;
   s.handoff = 0;
   s.noise_guard = 0;
+  s.boundary_stop = 0;
+  s.at_boundary = 0;
+  s.anchor_eps = 0.0;
   s.at_final = 0;
   s.reanchor = 0;
   s.den_fixed = 0.0;
@@ -481,17 +498,20 @@ static wf_status run_loop(Plan &P, int which, T2 *F, T2 *G, const double *tinit,
   return WF_OK;
 }
 
-// r = G(x) - x (both FP64 alm) -> source of the correction solve:
-// src = r / (f0_l alpha Omega), f0_l = C_l / (C_l + alpha Omega); 0 where C_l = 0
+// r = G(x) - x (both FP64 alm) -> source of an anchored stage at (xi, mu):
+// the analysis adds f_l xi Omega src, so src = r (Sbar + xi Omega) /
+// (Sbar xi Omega), Sbar = max(C_l - mu Omega, 0); 0 where Sbar = 0 (there
+// r = 0 as well)
 __global__ void k_make_source(const double2 *gx, const double2 *x, const double *cl,
-                              double alpha, double omega, int lmax, double2 *src) {
+                              double xi, double mu, double omega, int lmax,
+                              double2 *src) {
   const int m = blockIdx.x;
   const long base = (long)m * (2 * lmax + 1 - m) / 2;
-  const double ao = alpha * omega;
+  const double xo = xi * omega;
   for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
     const long i = base + l;
-    const double c = cl[l];
-    const double s = c > 0.0 ? (c + ao) / (c * ao) : 0.0;
+    const double sb = fmax(cl[l] - mu * omega, 0.0);
+    const double s = sb > 0.0 ? (sb + xo) / (sb * xo) : 0.0;
     src[i] = make_double2(s * (gx[i].x - x[i].x), s * (gx[i].y - x[i].y));
   }
 }
@@ -502,20 +522,21 @@ __global__ void k_alm_add(double2 *x, const double2 *y, long n) {
     x[i] = make_double2(x[i].x + y[i].x, x[i].y + y[i].y);
 }
 
-// FP64 fixed-point map of the last stage: gx = G(x) at xi = alpha, mu = 0;
-// returns ||G(x) - x||^2 in *num
-static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num) {
+// One FP64 iteration map of stage (xi, mu) with band L: gx = G(x); returns
+// ||G(x) - x||^2 in *num.  (Defaults: the last stage, full band.)
+static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
+                           double xi, double mu, int L) {
   SolverState s = initial_state(P);
-  s.xi = P.alpha;
-  s.mu = 0.0;
-  s.lcur = s.lnext = P.lmax;
+  s.xi = xi;
+  s.mu = mu;
+  s.lcur = s.lnext = L;
   s.done = 0;
   *P.state_h = s;
   WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
                           cudaMemcpyHostToDevice, P.stream));
   WF_CUDA(cudaMemcpyAsync(gx, x, sizeof(double2) * P.nalm, cudaMemcpyDeviceToDevice,
                           P.stream));
-  WF_TRY(launch_legendre_synth<double2>(P, x, P.F64, nullptr, P.lmax));
+  WF_TRY(launch_legendre_synth<double2>(P, x, P.F64, nullptr, std::max(L, 0)));
   WF_TRY(launch_ring<double2>(P, RING_FUSED, P.F64, P.G64, P.dmap, nullptr, P.state,
                               P.lmax));
   WF_TRY(launch_legendre_anal<double2>(P, P.G64, gx, P.state, ANA_FILTER, P.lmax));
@@ -527,6 +548,9 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num) 
   for (int m = 0; m <= P.lmax; ++m) acc += part[2 * m];
   *num = acc;
   return WF_OK;
+}
+static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num) {
+  return fp64_step(P, x, gx, num, P.alpha, 0.0, P.lmax);
 }
 
 // reduced term count of one Legendre transform at band L (cached per L)
@@ -614,70 +638,69 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
   double fp_res = -1.0;
   *P.state_h = initial_state(P);
   if (P.opts.precision == WF_PREC_MIXED) {
-    // Stages mu > 0 of Algorithm 2 with FP32 transforms (their fixed points
-    // only steer the iterate towards the last stage's)...
+    // Mixed precision.  Stages with a loose tolerance (>= ANCHOR_EPS) run
+    // Algorithm 2 with FP32 transforms on x itself.  Every later stage runs
+    // anchored: with x_a the iterate at the anchor and r = G64(x_a) - x_a
+    // (one FP64 iteration map of the stage), iterate
+    //   delta <- J32 delta + r,   x = x_a + delta,
+    // which is the same iteration x <- G(x) written as a correction, so the
+    // FP32 transform error scales with |delta| instead of |x|.  A new anchor
+    // is taken at each stage change, when |delta| exceeds ANCHOR_CAP |x_a|,
+    // and when progress stalls.
     bool converged = false;
-    int stage_final = 0;
-    if (P.state_h->mu > 0.0) {
-      P.state_h->handoff = 1;
-      P.state_h->noise_guard = 1;
-      // stage tolerances above the FP32 noise floor
-      P.state_h->eps_final = std::max(P.opts.eps_final, STAGE_EPS_FP32);
-      P.state_h->eps_k = std::min(P.opts.eps_cap, P.state_h->eps_final *
-                                                      std::max(1.0, P.state_h->mu / P.alpha));
-      WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
-                              cudaMemcpyHostToDevice, P.stream));
-      WF_TRY(run_loop<float2>(P, 1, P.F32, P.G32, tinit, P.dmap, nullptr));
-      if (P.state_h->numeric_error) {
-        set_error("wf_solve: NaN or Inf in the iteration");
-        return WF_ERR_NUMERIC;
-      }
-      stage_final = P.state_h->stage;
+    SolverState &h = *P.state_h;
+    h.noise_guard = 1;
+    h.anchor_eps = ANCHOR_EPS;
+    if (h.eps_k < ANCHOR_EPS) h.max_iter = 1;  // one plain step from t0 = d
+    WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
+                            cudaMemcpyHostToDevice, P.stream));
+    WF_TRY(run_loop<float2>(P, 1, P.F32, P.G32, tinit, P.dmap, nullptr));
+    if (h.numeric_error) {
+      set_error("wf_solve: NaN or Inf in the iteration");
+      return WF_ERR_NUMERIC;
     }
-    total_iter = P.state_h->iter;
-    first_stages = stage_final + 1;
-    const bool reached_final = P.state_h->at_final || P.state_h->mu == 0.0;
-    // ...then the last stage (xi = alpha, mu = 0) anchored in FP64: with
-    // r = G64(x_a) - x_a, iterate delta <- J32 delta + r (the FP32 transform
-    // error now scales with |delta|, not |x|), x = x_a + delta.  Re-anchor
-    // when |delta| exceeds 1e-2 |x_a|.
+    total_iter = h.iter;
+    bool anchored = h.at_boundary || h.max_iter == 1;
+    if (h.max_iter == 1 && !h.at_boundary) {
+      // the single plain step did not advance: stay in the initial stage
+      const SolverState keep = h;
+      h = initial_state(P);
+      h.iter = keep.iter;
+    }
     WF_CUDA(cudaMemcpyAsync(P.xacc, P.x, sizeof(double2) * P.nalm,
                             cudaMemcpyDeviceToDevice, P.stream));
-    const int lfinal = P.opts.band_limit ? band_host(P.cl, 0.0, P.omega) : P.lmax;
-    // A cycle runs until its error estimate (relative to |x_a|) is below
-    // eps_final; its correction |delta| is then (up to the FP32 transform
-    // error amplified by the slow modes) the error of the iterate it
-    // corrected.  Done when that correction, or the one predicted for the
-    // next cycle from the observed contraction, is below eps_final.
     double prev_rel = -1.0, rate_floor = 0.0;
     int cycles = 0, reanchors = 0, cycle_start = total_iter;
-    while (reached_final && cycles <= P.opts.refine_max && reanchors <= MAX_REANCHORS) {
+    while (anchored && reanchors <= MAX_REANCHORS && cycles <= P.opts.refine_max) {
+      const SolverState stage = h;  // stage parameters of this anchor
       double num = 0.0, xn = 0.0;
-      WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num));
+      WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num, stage.xi, stage.mu, stage.lcur));
       WF_TRY(alm_dot(P, P.xacc, P.xacc, nullptr, &xn));
-      k_make_source<<<P.lmax + 1, 128, 0, P.stream>>>(P.xtmp, P.xacc, P.cl_d, P.alpha,
-                                                      P.omega, P.lmax, P.src);
+      k_make_source<<<P.lmax + 1, 128, 0, P.stream>>>(P.xtmp, P.xacc, P.cl_d, stage.xi,
+                                                      stage.mu, P.omega, P.lmax, P.src);
       WF_CUDA(cudaGetLastError());
       WF_CUDA(cudaMemsetAsync(P.x, 0, sizeof(double2) * P.nalm, P.stream));
       SolverState s = initial_state(P);
-      s.xi = P.alpha;
-      s.mu = 0.0;
-      s.stage = stage_final;
-      s.eps_k = P.opts.eps_final;
-      s.lcur = s.lnext = lfinal;
+      s.xi = stage.xi;
+      s.mu = stage.mu;
+      s.stage = stage.stage;
+      s.eps_k = stage.eps_k;
+      s.lcur = stage.lcur;
+      s.lnext = stage.lnext;
       s.iter = total_iter;
       s.max_iter = P.opts.max_iter;
       s.den_fixed = xn;
       s.delta_cap2 = ANCHOR_CAP * ANCHOR_CAP * xn;
-      s.rate_floor = rate_floor;
+      s.rate_floor = stage.mu == 0.0 ? rate_floor : 0.0;
       s.noise_guard = 1;
-      *P.state_h = s;
+      s.boundary_stop = 1;
+      h = s;
       WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
                               cudaMemcpyHostToDevice, P.stream));
       WF_TRY(run_loop<float2>(P, 2, P.F32, P.G32, nullptr, nullptr, P.src));
-      total_iter = P.state_h->iter;
-      if (P.state_h->numeric_error) {
-        set_error("wf_solve: NaN or Inf in the anchored last stage");
+      total_iter = h.iter;
+      if (h.numeric_error) {
+        set_error("wf_solve: NaN or Inf in an anchored stage");
         return WF_ERR_NUMERIC;
       }
       double dn = 0.0;
@@ -685,25 +708,20 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       k_alm_add<<<304, 256, 0, P.stream>>>(P.xacc, P.x, P.nalm);
       WF_CUDA(cudaGetLastError());
       ++refinements;
-      if (P.state_h->reanchor) {  // |delta| hit the cap: new anchor
-        ++reanchors;
+      if (h.at_boundary) continue;  // next stage: h holds its parameters
+      if (h.reanchor || (h.stagnated && h.mu == 0.0)) {
+        ++reanchors;  // same stage, new anchor
+        h.stagnated = 0;
+        h.converged = 0;
         continue;
       }
-      if (!P.state_h->converged) break;  // max_iter
-      // Cauchy rule (the paper's): the anchored stage ends like the FP64 one
-      // once ||x_i - x_{i-1}|| / ||x_i|| < eps_final; a stop at the FP32 noise
-      // floor instead re-anchors (the next delta is smaller, so is its floor)
+      if (!h.converged) break;  // max_iter
       if (P.opts.stop_rule == WF_STOP_CAUCHY) {
-        if (!P.state_h->stagnated) {
-          converged = true;
-          break;
-        }
-        ++reanchors;
-        continue;
+        converged = true;
+        break;
       }
+      // error-estimate rule: confirm with further cycles (see the header)
       ++cycles;
-      // later cycles start with a residual in which slow modes are nearly
-      // invisible; their error estimate uses this cycle's slow-mode rate
       {
         double r = 0.0;
         WF_TRY(slow_rate(P, cycle_start, total_iter, &r));
@@ -717,18 +735,21 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
         break;
       }
       prev_rel = rel;
+      h.converged = 0;
     }
+    if (!anchored) converged = h.converged;  // finished inside the data pass
+    first_stages = h.stage + 1;
     {
-      const SolverState keep = *P.state_h;
+      const SolverState keep = h;
       double num = 0.0, xn = 0.0;
       WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num));
       WF_TRY(alm_dot(P, P.xacc, P.xacc, nullptr, &xn));
       fp_res = xn > 0.0 ? sqrt(num / xn) : 0.0;
-      *P.state_h = keep;
+      h = keep;
     }
     WF_CUDA(cudaMemcpyAsync(P.x, P.xacc, sizeof(double2) * P.nalm,
                             cudaMemcpyDeviceToDevice, P.stream));
-    P.state_h->converged = converged ? 1 : 0;
+    h.converged = converged ? 1 : 0;
   } else {
     WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
                             cudaMemcpyHostToDevice, P.stream));

@@ -64,6 +64,10 @@ struct SolverState {
   int flat;       // consecutive last-stage iterations without a Cauchy decrease
   int stagnated;  // the last stage stopped at the arithmetic noise floor
   int handoff;    // 1: stop (done, not converged) on entering the mu = 0 stage
+  int boundary_stop;  // 1: stop (done) at every stage advance (anchored runs)
+  int at_boundary;    // set when a run stopped at a stage advance
+  double anchor_eps;  // > 0: stop at an advance into a stage whose tolerance
+                      // is below it (FP32 data pass -> anchored stages)
   int noise_guard;  // 1 (FP32 passes): a stage whose Cauchy ratio stops
                     // falling below 1e-3 has reached the arithmetic noise
                     // floor and ends

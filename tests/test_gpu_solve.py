@@ -62,7 +62,7 @@ def test_fp64_solve_nside32_workload(torch_cuda, osht, odm):
     3 deg: the small full-size workload, against the dense fixed point."""
     torch = torch_cuda
     p, d = problem(osht, "lognormal", 32, 1000)
-    alm, mp, st, _ = gpu_solve(torch, p, d, eps_final=1e-12)
+    alm, mp, st, _ = gpu_solve(torch, p, d, eps_final=1e-12, stop_rule=1)
     assert st["converged"] == 1
     Y = osht.ymatrix(p.nside, p.lmax)
     ref = odm.dm_fixed_point_dense(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d, 0.0, Y=Y)
