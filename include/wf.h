@@ -93,6 +93,7 @@ typedef struct {
   double err_estimate; /* last geometric error estimate (WF_STOP_ERROR) */
   double fp_residual;  /* WF_PREC_MIXED: final FP64 fixed-point residual */
   double elapsed_ms;   /* device time of the solve (CUDA events) */
+  long kernel_launches; /* kernels of this library launched by the solve */
 } wf_stats;
 
 void wf_opts_default(wf_opts *opts);

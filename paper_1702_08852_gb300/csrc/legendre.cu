@@ -443,6 +443,7 @@ wf_status launch_legendre_synth(const Plan &P, const double2 *x, T2 *F,
   const size_t smem = align16(sizeof(T2) * (P.lmax + 1)) + sizeof(T) * (P.lmax + 1);
   const int pairs_per_cta = SYN_THREADS * NP;
   dim3 grid((P.npairs + pairs_per_cta - 1) / pairs_per_cta, P.lmax + 1);
+  ++P.nlaunch;
   kern<<<grid, SYN_THREADS, smem, P.stream>>>(P.pairs, P.npairs, P.lmax, P.rc,
                                               P.rc32, P.rg, P.seed_l, P.seed_u,
                                               x, F, st, lstatic);
@@ -459,6 +460,7 @@ wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
   auto kern = k_legendre_anal<T, NP>;
   const size_t smem =
       align16(sizeof(T2) * (P.lmax + 1) * ANA_WARPS) + sizeof(T) * (P.lmax + 1);
+  ++P.nlaunch;
   kern<<<P.lmax + 1, ANA_THREADS, smem, P.stream>>>(
       P.pairs, P.npairs, P.lmax, P.rc, P.rc32, P.rg, P.seed_l, P.seed_u, P.cl_d,
       P.omega, G, x, P.partials, src, st, mode, lstatic);

@@ -300,6 +300,7 @@ static wf_status launch_ring_mode(const Plan &P, const T2 *F, T2 *G,
     int Mg = 1;
     for (int k = b; k < e; ++k) Mg = std::max(Mg, P.pairs_h[k].fftM);
     const size_t smem = sizeof(T2) * Mg;
+    ++P.nlaunch;
     kern<<<e - b, RING_THREADS, smem, P.stream>>>(
         P.pairs, b, P.lmax, F, G, in_map, out_map, P.nvar, Tables<T2>::tw(P),
         P.fftMmax, Tables<T2>::ch(P), Tables<T2>::bh(P), st, lstatic);

@@ -281,6 +281,7 @@ static wf_status host_sum(Plan &P, double *dev, int n, double *res) {
 
 static wf_status alm_dot(Plan &P, const double2 *a, const double2 *b,
                          const double *fl, double *res) {
+  ++P.nlaunch;
   k_alm_dot<<<RED_BLOCKS, 256, 0, P.stream>>>(a, b, fl, P.lmax, P.red);
   WF_CUDA(cudaGetLastError());
   return host_sum(P, P.red, RED_BLOCKS, res);
@@ -395,6 +396,7 @@ static wf_status enqueue_iteration(Plan &P, T2 *F, T2 *G, const double *data,
   WF_TRY(launch_legendre_synth<T2>(P, P.x, F, P.state, P.lmax));
   if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[3 * C + slot], P.stream, cudaEventRecordExternal));
   WF_TRY(launch_ring<T2>(P, RING_FUSED, F, G, data, nullptr, P.state, P.lmax));
+  ++P.nlaunch;
   k_control<<<1, CTRL_THREADS, 0, P.stream>>>(P.state, P.partials, P.lmax, P.cl_d,
                                               P.trace);
   WF_CUDA(cudaGetLastError());
@@ -435,8 +437,11 @@ static wf_status capture_graph(Plan &P, int which, T2 *F, T2 *G, const double *d
     return WF_ERR_CUDA;
   }
   wf_status s = WF_OK;
+  const long n0 = P.nlaunch;
   for (int i = 0; i < chunk && s == WF_OK; ++i)
     s = enqueue_iteration<T2>(P, F, G, data, src, P.opts.timing ? i : -1);
+  P.graph_kernels[which] = P.nlaunch - n0;  // nodes of the graph, not yet run
+  P.nlaunch = n0;
   cudaError_t e = cudaStreamEndCapture(P.stream, &g);
   P.stream = user;
   if (s != WF_OK) {
@@ -475,6 +480,7 @@ static wf_status run_loop(Plan &P, int which, T2 *F, T2 *G, const double *tinit,
   int it0 = P.state_h->iter;
   for (;;) {
     WF_CUDA(cudaGraphLaunch(P.graph[which], P.stream));
+    P.nlaunch += P.graph_kernels[which];
     WF_CUDA(cudaMemcpyAsync(P.state_h, P.state, sizeof(SolverState),
                             cudaMemcpyDeviceToHost, P.stream));
     WF_CUDA(cudaStreamSynchronize(P.stream));
@@ -621,6 +627,8 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
     return WF_ERR_STATE;
   }
   WF_CUDA(cudaEventRecord(P.ev0, P.stream));
+  const long launches0 = P.nlaunch;
+  ++P.nlaunch;
   k_mask_data<<<304, 256, 0, P.stream>>>(d, P.nvar, P.npix, P.dmap);
   WF_CUDA(cudaGetLastError());
   if (init_alm)
@@ -630,6 +638,7 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
     WF_CUDA(cudaMemsetAsync(P.x, 0, sizeof(double2) * P.nalm, P.stream));
   const double *tinit = P.dmap;
   if (init_map) {
+    ++P.nlaunch;
     k_mask_data<<<304, 256, 0, P.stream>>>(init_map, P.nvar, P.npix, P.mtmp);
     WF_CUDA(cudaGetLastError());
     tinit = P.mtmp;
@@ -676,6 +685,7 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       double num = 0.0, xn = 0.0;
       WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num, stage.xi, stage.mu, stage.lcur));
       WF_TRY(alm_dot(P, P.xacc, P.xacc, nullptr, &xn));
+      ++P.nlaunch;
       k_make_source<<<P.lmax + 1, 128, 0, P.stream>>>(P.xtmp, P.xacc, P.cl_d, stage.xi,
                                                       stage.mu, P.omega, P.lmax, P.src);
       WF_CUDA(cudaGetLastError());
@@ -705,6 +715,7 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       }
       double dn = 0.0;
       WF_TRY(alm_dot(P, P.x, P.x, nullptr, &dn));
+      ++P.nlaunch;
       k_alm_add<<<304, 256, 0, P.stream>>>(P.xacc, P.x, P.nalm);
       WF_CUDA(cudaGetLastError());
       ++refinements;
@@ -717,8 +728,20 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       }
       if (!h.converged) break;  // max_iter
       if (P.opts.stop_rule == WF_STOP_CAUCHY) {
-        converged = true;
-        break;
+        // accept when the FP64 step from the result passes the same test:
+        // ||G64(x) - x|| / ||x|| < eps_final (else re-anchor and go on)
+        double num = 0.0, xn2 = 0.0;
+        WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num, stage.xi, stage.mu, stage.lcur));
+        WF_TRY(alm_dot(P, P.xacc, P.xacc, nullptr, &xn2));
+        const double c64 = xn2 > 0.0 ? sqrt(num / xn2) : 0.0;
+        h = stage;
+        h.iter = total_iter;
+        if (c64 < P.opts.eps_final) {
+          converged = true;
+          break;
+        }
+        ++reanchors;
+        continue;
       }
       // error-estimate rule: confirm with further cycles (see the header)
       ++cycles;
@@ -778,6 +801,7 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
     stats->err_estimate = s.err_est;
     stats->fp_residual = fp_res;
     stats->elapsed_ms = ms;
+    stats->kernel_launches = P.nlaunch - launches0;
   }
   if (s.numeric_error) {
     set_error("wf_solve: NaN or Inf in the iteration");
@@ -811,8 +835,10 @@ wf_status residual(Plan &P, const double *d, const double *alm, double *res_wf,
   WF_CUDA(cudaMalloc(&cp12, sizeof(double) * (P.lmax + 1)));
   wf_status status = WF_OK;
   do {
+    ++P.nlaunch;
     k_mask_data<<<304, 256, 0, P.stream>>>(d, P.nvar, npix, P.dmap);
     if ((status = alm2map(P, alm, P.mtmp)) != WF_OK) break;
+    ++P.nlaunch;
     k_pix_resid<<<RED_BLOCKS, 256, 0, P.stream>>>(P.dmap, P.mtmp, P.nvar, npix, pr,
                                                   py, P.red);
     double chi_pix = 0.0;
@@ -840,6 +866,7 @@ wf_status residual(Plan &P, const double *d, const double *alm, double *res_wf,
     for (int l = 0; l <= P.lmax; ++l) hp_om[l] = hp[l] / P.omega;
     cudaMemcpyAsync(cp12, hp_om.data(), sizeof(double) * (P.lmax + 1),
                     cudaMemcpyHostToDevice, P.stream);
+    ++P.nlaunch;
     k_alm_combine<<<P.lmax + 1, 128, 0, P.stream>>>(x, u, cm12, cp12, P.lmax, rr);
     double rn = 0.0, yn = 0.0;
     if ((status = alm_dot(P, rr, rr, nullptr, &rn)) != WF_OK) break;

@@ -146,6 +146,11 @@ struct Plan {
   int graph_chunk[3] = {0, 0, 0};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
+  // kernel launches issued for this plan (graph launches count their kernel
+  // nodes); mutable so that const launch helpers can count
+  mutable long nlaunch = 0;
+  long graph_kernels[3] = {0, 0, 0};
+
   // optional per-kernel timing inside the captured graphs (opts.timing):
   // events around the Legendre analysis (k = 0) and synthesis (k = 1) of
   // every iteration of a chunk; accumulated over active iterations only

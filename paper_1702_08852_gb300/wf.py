@@ -43,7 +43,7 @@ class wf_stats(ctypes.Structure):
                 ("converged", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("final_cauchy", ctypes.c_double),
                 ("err_estimate", ctypes.c_double), ("fp_residual", ctypes.c_double),
-                ("elapsed_ms", ctypes.c_double)]
+                ("elapsed_ms", ctypes.c_double), ("kernel_launches", ctypes.c_long)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
