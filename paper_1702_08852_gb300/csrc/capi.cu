@@ -25,7 +25,7 @@ static void free_plan(wf_plan_s *P) {
                   P->seed_u, P->tw64,  P->tw32,    P->chirp64, P->chirp32, P->bhat64,
                   P->bhat32, P->nvar,  P->F64,     P->G64,    P->F32,    P->G32,
                   P->x,      P->xtmp,  P->dmap,    P->mtmp,   P->partials, P->red,
-                  P->state,  P->trace, P->xacc,  P->src};
+                  P->state,  P->trace, P->xacc,  P->src, P->xs64, P->xs32};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (P->state_h) cudaFreeHost(P->state_h);
@@ -45,6 +45,8 @@ static wf_status alloc_work(Plan &P) {
   WF_CUDA(cudaMalloc(&P.x, sizeof(double2) * P.nalm));
   WF_CUDA(cudaMalloc(&P.xtmp, sizeof(double2) * P.nalm));
   WF_CUDA(cudaMalloc(&P.xacc, sizeof(double2) * P.nalm));
+  WF_CUDA(cudaMalloc(&P.xs64, sizeof(double2) * P.nalm));
+  WF_CUDA(cudaMalloc(&P.xs32, sizeof(float2) * P.nalm));
   WF_CUDA(cudaMalloc(&P.src, sizeof(double2) * P.nalm));
   WF_CUDA(cudaMalloc(&P.dmap, sizeof(double) * P.npix));
   WF_CUDA(cudaMalloc(&P.mtmp, sizeof(double) * P.npix));

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(SYN_THREADS)
                      const double *__restrict__ rc, const float *__restrict__ rc32,
                      const double *__restrict__ rg, const int *__restrict__ seed_l,
                      const double2 *__restrict__ seed_u,
-                     const double2 *__restrict__ x,
+                     const typename Vec2<T>::type *__restrict__ xs,
                      typename Vec2<T>::type *__restrict__ F,
                      const SolverState *__restrict__ st, int lstatic) {
   typedef typename Vec2<T>::type T2;
@@ -120,9 +120,7 @@ __global__ void __launch_bounds__(SYN_THREADS)
   for (int j = threadIdx.x; j < nl; j += blockDim.x) {
     const long i = base + j;
     sc[j] = coef<T>(rc, rc32, i);
-    const double g = rg[i];
-    const double2 xv = x[i];
-    sx[j] = Vec2<T>::make((T)(g * xv.x), (T)(g * xv.y));
+    sx[j] = xs[i];
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -228,7 +226,11 @@ __global__ void __launch_bounds__(SYN_THREADS)
 constexpr int ANA_THREADS = 128;
 constexpr int ANA_WARPS = ANA_THREADS / 32;
 constexpr int LCHUNK = 16;
-constexpr int ANA_NP = 4;  // ring pairs per thread in the analysis
+// ring pairs per thread in the analysis: more pairs amortise the warp
+// reduction (FP32); FP64 is bound by its arithmetic pipe and keeps registers low
+template <typename T> struct AnaNP;
+template <> struct AnaNP<float> { static constexpr int v = 8; };
+template <> struct AnaNP<double> { static constexpr int v = 4; };
 
 // v[0..31] per lane -> lane i returns sum over lanes of v[i]
 template <typename T>
@@ -256,6 +258,7 @@ __global__ void __launch_bounds__(ANA_THREADS)
                     const typename Vec2<T>::type *__restrict__ G,
                     double2 *__restrict__ x, double *__restrict__ partials,
                     const double2 *__restrict__ src,
+                    typename Vec2<T>::type *__restrict__ xs_out,
                     const SolverState *__restrict__ st, int mode, int lstatic) {
   typedef typename Vec2<T>::type T2;
   const int m = blockIdx.x;
@@ -391,6 +394,7 @@ __global__ void __launch_bounds__(ANA_THREADS)
         den += wm * (ar * ar + ai * ai);
       }
       x[i] = make_double2(ar, ai);
+      if (xs_out) xs_out[i] = Vec2<T>::make((T)(rg[i] * ar), (T)(rg[i] * ai));
     }
   }
   // coefficients of this m above the band are zero
@@ -402,6 +406,7 @@ __global__ void __launch_bounds__(ANA_THREADS)
       num += wm * (old.x * old.x + old.y * old.y);
     }
     x[i] = make_double2(0.0, 0.0);
+    if (xs_out) xs_out[i] = Vec2<T>::make((T)0, (T)0);
   }
   if (mode == ANA_FILTER) {
     red_num[tid] = num;
@@ -435,7 +440,7 @@ struct Kernels<float2> {
 };
 
 template <typename T2>
-wf_status launch_legendre_synth(const Plan &P, const double2 *x, T2 *F,
+wf_status launch_legendre_synth(const Plan &P, const T2 *xs, T2 *F,
                                 const SolverState *st, int lstatic) {
   typedef typename Kernels<T2>::T T;
   constexpr int NP = 2;
@@ -446,7 +451,7 @@ wf_status launch_legendre_synth(const Plan &P, const double2 *x, T2 *F,
   ++P.nlaunch;
   kern<<<grid, SYN_THREADS, smem, P.stream>>>(P.pairs, P.npairs, P.lmax, P.rc,
                                               P.rc32, P.rg, P.seed_l, P.seed_u,
-                                              x, F, st, lstatic);
+                                              xs, F, st, lstatic);
   WF_CUDA(cudaGetLastError());
   return WF_OK;
 }
@@ -454,16 +459,16 @@ wf_status launch_legendre_synth(const Plan &P, const double2 *x, T2 *F,
 template <typename T2>
 wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
                                const SolverState *st, int mode, int lstatic,
-                               const double2 *src) {
+                               const double2 *src, T2 *xs_out) {
   typedef typename Kernels<T2>::T T;
-  constexpr int NP = ANA_NP;
+  constexpr int NP = AnaNP<T>::v;
   auto kern = k_legendre_anal<T, NP>;
   const size_t smem =
       align16(sizeof(T2) * (P.lmax + 1) * ANA_WARPS) + sizeof(T) * (P.lmax + 1);
   ++P.nlaunch;
   kern<<<P.lmax + 1, ANA_THREADS, smem, P.stream>>>(
       P.pairs, P.npairs, P.lmax, P.rc, P.rc32, P.rg, P.seed_l, P.seed_u, P.cl_d,
-      P.omega, G, x, P.partials, src, st, mode, lstatic);
+      P.omega, G, x, P.partials, src, xs_out, st, mode, lstatic);
   WF_CUDA(cudaGetLastError());
   return WF_OK;
 }
@@ -474,23 +479,43 @@ wf_status init_legendre_attributes() {
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   WF_CUDA(cudaFuncSetAttribute(k_legendre_synth<float, 2>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal<double, ANA_NP>,
+  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal<double, AnaNP<double>::v>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal<float, ANA_NP>,
+  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal<float, AnaNP<float>::v>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return WF_OK;
 }
 
+// xs = g_lm x_lm in the transform precision (the synthesis input)
+template <typename T2>
+__global__ void k_prescale(const double2 *__restrict__ x, const double *__restrict__ rg,
+                           long n, T2 *__restrict__ xs) {
+  typedef typename Scalar<T2>::type T;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x)
+    xs[i] = Vec2<T>::make((T)(rg[i] * x[i].x), (T)(rg[i] * x[i].y));
+}
+
+template <typename T2>
+wf_status launch_prescale(const Plan &P, const double2 *x, T2 *xs) {
+  ++P.nlaunch;
+  k_prescale<T2><<<304, 256, 0, P.stream>>>(x, P.rg, P.nalm, xs);
+  WF_CUDA(cudaGetLastError());
+  return WF_OK;
+}
+
+template wf_status launch_prescale<double2>(const Plan &, const double2 *, double2 *);
+template wf_status launch_prescale<float2>(const Plan &, const double2 *, float2 *);
 template wf_status launch_legendre_synth<double2>(const Plan &, const double2 *,
                                                   double2 *, const SolverState *,
                                                   int);
-template wf_status launch_legendre_synth<float2>(const Plan &, const double2 *,
+template wf_status launch_legendre_synth<float2>(const Plan &, const float2 *,
                                                  float2 *, const SolverState *, int);
 template wf_status launch_legendre_anal<double2>(const Plan &, const double2 *,
                                                  double2 *, const SolverState *,
-                                                 int, int, const double2 *);
+                                                 int, int, const double2 *, double2 *);
 template wf_status launch_legendre_anal<float2>(const Plan &, const float2 *,
                                                 double2 *, const SolverState *,
-                                                int, int, const double2 *);
+                                                int, int, const double2 *, float2 *);
 
 }  // namespace wf

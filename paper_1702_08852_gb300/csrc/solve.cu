@@ -290,7 +290,8 @@ static wf_status alm_dot(Plan &P, const double2 *a, const double2 *b,
 // ---------------------------------------------------------------- transforms
 wf_status alm2map(Plan &P, const double *alm, double *map) {
   const double2 *a = reinterpret_cast<const double2 *>(alm);
-  WF_TRY(launch_legendre_synth<double2>(P, a, P.F64, nullptr, P.lmax));
+  WF_TRY(launch_prescale<double2>(P, a, P.xs64));
+  WF_TRY(launch_legendre_synth<double2>(P, P.xs64, P.F64, nullptr, P.lmax));
   WF_TRY(launch_ring<double2>(P, RING_SYNTH, P.F64, nullptr, nullptr, map, nullptr,
                               P.lmax));
   return WF_OK;
@@ -306,7 +307,8 @@ wf_status map2alm(Plan &P, const double *map, double *alm) {
 
 wf_status alm2map_f32(Plan &P, const double *alm, double *map) {
   const double2 *a = reinterpret_cast<const double2 *>(alm);
-  WF_TRY(launch_legendre_synth<float2>(P, a, P.F32, nullptr, P.lmax));
+  WF_TRY(launch_prescale<float2>(P, a, P.xs32));
+  WF_TRY(launch_legendre_synth<float2>(P, P.xs32, P.F32, nullptr, P.lmax));
   WF_TRY(launch_ring<float2>(P, RING_SYNTH, P.F32, nullptr, nullptr, map, nullptr,
                              P.lmax));
   return WF_OK;
@@ -382,6 +384,14 @@ static SolverState initial_state(const Plan &P) {
   return s;
 }
 
+template <typename T2> struct Scaled;
+template <> struct Scaled<double2> {
+  static double2 *get(Plan &P) { return P.xs64; }
+};
+template <> struct Scaled<float2> {
+  static float2 *get(Plan &P) { return P.xs32; }
+};
+
 // one iteration; data = NULL runs a correction solve (d = 0) driven by the
 // harmonic source `src`
 template <typename T2>
@@ -390,10 +400,11 @@ static wf_status enqueue_iteration(Plan &P, T2 *F, T2 *G, const double *data,
   const bool timed = slot >= 0 && P.tev_chunk > 0;
   const int C = P.tev_chunk;
   if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[0 * C + slot], P.stream, cudaEventRecordExternal));
-  WF_TRY(launch_legendre_anal<T2>(P, G, P.x, P.state, ANA_FILTER, P.lmax, src));
+  T2 *xs = Scaled<T2>::get(P);
+  WF_TRY(launch_legendre_anal<T2>(P, G, P.x, P.state, ANA_FILTER, P.lmax, src, xs));
   if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[1 * C + slot], P.stream, cudaEventRecordExternal));
   if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[2 * C + slot], P.stream, cudaEventRecordExternal));
-  WF_TRY(launch_legendre_synth<T2>(P, P.x, F, P.state, P.lmax));
+  WF_TRY(launch_legendre_synth<T2>(P, xs, F, P.state, P.lmax));
   if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[3 * C + slot], P.stream, cudaEventRecordExternal));
   WF_TRY(launch_ring<T2>(P, RING_FUSED, F, G, data, nullptr, P.state, P.lmax));
   ++P.nlaunch;
@@ -542,7 +553,8 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
                           cudaMemcpyHostToDevice, P.stream));
   WF_CUDA(cudaMemcpyAsync(gx, x, sizeof(double2) * P.nalm, cudaMemcpyDeviceToDevice,
                           P.stream));
-  WF_TRY(launch_legendre_synth<double2>(P, x, P.F64, nullptr, std::max(L, 0)));
+  WF_TRY(launch_prescale<double2>(P, x, P.xs64));
+  WF_TRY(launch_legendre_synth<double2>(P, P.xs64, P.F64, nullptr, std::max(L, 0)));
   WF_TRY(launch_ring<double2>(P, RING_FUSED, P.F64, P.G64, P.dmap, nullptr, P.state,
                               P.lmax));
   WF_TRY(launch_legendre_anal<double2>(P, P.G64, gx, P.state, ANA_FILTER, P.lmax));
@@ -884,7 +896,8 @@ wf_status residual(Plan &P, const double *d, const double *alm, double *res_wf,
                       P.stream);
       cudaMemcpyAsync(P.xtmp, x, sizeof(double2) * P.nalm, cudaMemcpyDeviceToDevice,
                       P.stream);
-      if ((status = launch_legendre_synth<double2>(P, x, P.F64, nullptr, P.lmax)) !=
+      if ((status = launch_prescale<double2>(P, x, P.xs64)) != WF_OK) break;
+      if ((status = launch_legendre_synth<double2>(P, P.xs64, P.F64, nullptr, P.lmax)) !=
           WF_OK)
         break;
       if ((status = launch_ring<double2>(P, RING_FUSED, P.F64, P.G64, P.dmap, nullptr,

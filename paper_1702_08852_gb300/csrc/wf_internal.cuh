@@ -129,6 +129,8 @@ struct Plan {
   double2 *x = nullptr;          // [nalm] current iterate
   double2 *xtmp = nullptr;       // [nalm]
   double2 *xacc = nullptr;       // [nalm] refined solution (mixed precision)
+  double2 *xs64 = nullptr;       // [nalm] g_lm x_lm, synthesis input (FP64)
+  float2 *xs32 = nullptr;        // [nalm] g_lm x_lm, synthesis input (FP32)
   double2 *src = nullptr;        // [nalm] harmonic source of a correction solve
   double *dmap = nullptr;        // [npix] data with masked pixels zeroed
   double *mtmp = nullptr;        // [npix]
@@ -167,15 +169,20 @@ struct Plan {
 // Legendre transforms (legendre.cu).  Modes of the analysis:
 enum AnalysisMode { ANA_PLAIN = 0, ANA_FILTER = 1 };
 
+// The synthesis reads xs = g_lm a_lm in its own precision (written by the
+// analysis of the previous iteration, or by launch_prescale).
 template <typename T2>
-wf_status launch_legendre_synth(const Plan &P, const double2 *x, T2 *F,
+wf_status launch_prescale(const Plan &P, const double2 *x, T2 *xs);
+template <typename T2>
+wf_status launch_legendre_synth(const Plan &P, const T2 *xs, T2 *F,
                                 const SolverState *st, int lstatic);
-// src (optional, FP64 alm): adds the harmonic source f_l xi Omega src_lm of a
-// correction solve to the filtered coefficients (ANA_FILTER only).
+// src (optional, FP64 alm): adds the harmonic source f_l xi Omega src_lm of an
+// anchored stage to the filtered coefficients (ANA_FILTER only).
+// xs_out (optional): also write g_lm a_lm in the transform precision.
 template <typename T2>
 wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
                                const SolverState *st, int mode, int lstatic,
-                               const double2 *src = nullptr);
+                               const double2 *src = nullptr, T2 *xs_out = nullptr);
 
 // Ring transforms (ringfft.cu).  Modes:
 enum RingMode {
