@@ -10,7 +10,12 @@
 
 namespace wf {
 static thread_local std::string g_last_error;
-void set_error(const std::string &msg) { g_last_error = msg; }
+static thread_local const char *g_last_error_static = nullptr;
+void set_error(const std::string &msg) {
+  g_last_error = msg;
+  g_last_error_static = nullptr;
+}
+void set_error_static(const char *msg) { g_last_error_static = msg; }
 
 static wf_status arg_error(const char *msg) {
   set_error(msg);
@@ -117,7 +122,9 @@ const char *wf_status_str(wf_status s) {
   return "unknown status";
 }
 
-const char *wf_last_error(void) { return g_last_error.c_str(); }
+const char *wf_last_error(void) {
+  return g_last_error_static ? g_last_error_static : g_last_error.c_str();
+}
 
 wf_status wf_plan(wf_plan_t *out, int nside, int lmax, const double *cl_host,
                   const double *noise_var_dev, const uint8_t *mask_dev,
@@ -249,6 +256,13 @@ wf_status wf_residual(wf_plan_t plan, const double *d_dev, const double *alm_dev
   if (!plan) return arg_error("wf_residual: plan is NULL");
   if (!d_dev || !alm_dev) return arg_error("wf_residual: NULL input");
   return residual(*plan, d_dev, alm_dev, rel_res_wf, rel_res_fp, chi2);
+}
+
+wf_status wf_residual_static(wf_plan_t plan, const double *d_dev, const double *alm_dev,
+                             double *rel_res_wf, double *rel_res_fp, double *chi2) {
+  if (!plan) return arg_error("wf_residual_static: plan is NULL");
+  if (!d_dev || !alm_dev) return arg_error("wf_residual_static: NULL input");
+  return residual_static(*plan, d_dev, alm_dev, rel_res_wf, rel_res_fp, chi2);
 }
 
 wf_status wf_alm2map(wf_plan_t plan, const double *alm_dev, double *map_dev) {

@@ -330,7 +330,7 @@ static int band_host(const std::vector<double> &cl, double mu, double omega) {
   return b;
 }
 
-static SolverState initial_state(const Plan &P) {
+SolverState initial_state(const Plan &P) {
   SolverState s{};
   const wf_opts &o = P.opts;
   double cmax = 0.0;

@@ -14,6 +14,8 @@ namespace wf {
 
 // ---------------------------------------------------------------- errors
 void set_error(const std::string &msg);
+// records a message with static storage (no allocation)
+void set_error_static(const char *msg);
 
 #define WF_CUDA(call)                                                        \
   do {                                                                       \
@@ -213,6 +215,18 @@ wf_status map2alm(Plan &P, const double *map, double *alm);
 wf_status alm2map_f32(Plan &P, const double *alm, double *map);
 wf_status map2alm_f32(Plan &P, const double *map, double *alm);
 wf_status legendre_terms(Plan &P, int L, double *terms);
+SolverState initial_state(const Plan &P);
+wf_status residual_static(Plan &P, const double *d, const double *alm, double *res_wf,
+                          double *res_fp, double *chi2);
+
+// helper kernels of solve.cu shared with noalloc.cu
+__global__ void k_mask_data(const double *d, const double *nvar, long npix, double *out);
+__global__ void k_alm_dot(const double2 *a, const double2 *b, const double *fl, int lmax,
+                          double *out);
+__global__ void k_alm_combine(const double2 *x, const double2 *u, const double *cm12,
+                              const double *cp12, int lmax, double2 *r);
+__global__ void k_pix_resid(const double *d, const double *s, const double *nvar,
+                            long npix, double *r, double *y, double *out);
 
 }  // namespace wf
 

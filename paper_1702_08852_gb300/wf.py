@@ -72,6 +72,8 @@ def lib():
             "wf_solve_host": (I, [_P, _P, _P, _P, ctypes.POINTER(wf_stats)]),
             "wf_residual": (I, [_P, _P, _P, ctypes.POINTER(D), ctypes.POINTER(D),
                                 ctypes.POINTER(D)]),
+            "wf_residual_static": (I, [_P, _P, _P, ctypes.POINTER(D), ctypes.POINTER(D),
+                                       ctypes.POINTER(D)]),
             "wf_alm2map": (I, [_P, _P, _P]),
             "wf_map2alm": (I, [_P, _P, _P]),
             "wf_alm2map_f32": (I, [_P, _P, _P]),
@@ -227,6 +229,18 @@ class Plan:
                                  _dev_ptr(d, torch.float64, self.npix, "d"),
                                  _dev_ptr(alm, torch.complex128, self.nalm, "alm"),
                                  ctypes.byref(r1), ctypes.byref(r2), ctypes.byref(c2)))
+        return {"rel_res_wf": r1.value, "rel_res_fp": r2.value, "chi2": c2.value}
+
+    def residual_static(self, d, alm):
+        """wf_residual without allocation during the call (see include/wf.h):
+        for callers that must not allocate device memory, e.g. inside a
+        captured CUDA graph.  Small plans only."""
+        import torch
+        r1, r2, c2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().wf_residual_static(
+            self.handle, _dev_ptr(d, torch.float64, self.npix, "d"),
+            _dev_ptr(alm, torch.complex128, self.nalm, "alm"),
+            ctypes.byref(r1), ctypes.byref(r2), ctypes.byref(c2)))
         return {"rel_res_wf": r1.value, "rel_res_fp": r2.value, "chi2": c2.value}
 
     def alm2map(self, alm, out=None):
