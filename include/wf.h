@@ -80,6 +80,9 @@ typedef struct {
   int timing;        /* 1: time the Legendre kernels of every iteration with
                         CUDA events recorded inside the captured graphs
                         (read with wf_kernel_stats; default 0) */
+  int autotune;      /* 1: at plan creation, time the launch variants of the
+                        Legendre kernels for this geometry and keep the
+                        fastest (cached per nside, lmax; default 0) */
 } wf_opts;
 
 /* Per-solve statistics. */
@@ -135,6 +138,19 @@ wf_status wf_set_cl(wf_plan_t plan, const double *cl_host);
 wf_status wf_solve(wf_plan_t plan, const double *d_dev, double *alm_dev,
                    double *map_dev, const double *init_alm_dev,
                    const double *init_map_dev, wf_stats *stats);
+
+/* Solve n independent problems together (Sect. 2.2 per map).  plans[i] must
+ * be distinct plans with noise; each may have its own nside, lmax, spectrum,
+ * noise, mask and options.  d_dev[i] / alm_dev[i] / map_dev[i] as in
+ * wf_solve (alm_dev, map_dev and their entries may be NULL).  The maps run
+ * concurrently on private streams, each driven by its own host thread with
+ * its own captured iteration graphs and device-side stage control; results
+ * equal wf_solve's map by map.  stats: NULL or n entries.  elapsed_ms: device
+ * time from the start of the first map to the end of the last.  Returns the
+ * first error, else WF_ERR_NOT_CONVERGED if a map hit max_iter, else WF_OK. */
+wf_status wf_solve_batch(wf_plan_t *plans, int n, const double *const *d_dev,
+                         double *const *alm_dev, double *const *map_dev, wf_stats *stats,
+                         double *elapsed_ms);
 
 /* Same as wf_solve with host buffers: copies d in, solves, copies the
  * requested outputs back (both copies are part of the call). */

@@ -1,0 +1,115 @@
+// autotune.cu -- pick the launch variant (ring pairs per thread) of each
+// Legendre kernel for a geometry by timing them once at full band.
+//
+// The best variant depends on the number of ring pairs and the band limit:
+// more pairs per thread give more independent recurrences (latency hiding)
+// and amortise the analysis' warp reduction, but cost registers and
+// occupancy.  Results are cached per (nside, lmax) for the process.
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "wf_internal.cuh"
+
+namespace wf {
+
+namespace {
+struct Choice {
+  int syn[2], ana[2];
+};
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, Choice> g_tune_cache;
+}  // namespace
+
+template <typename T2>
+static wf_status time_synth(Plan &P, T2 *xs, T2 *F, cudaEvent_t e0, cudaEvent_t e1,
+                            float *ms) {
+  WF_TRY(launch_legendre_synth<T2>(P, xs, F, nullptr, P.lmax));  // warm
+  WF_CUDA(cudaEventRecord(e0, P.stream));
+  for (int r = 0; r < 2; ++r) WF_TRY(launch_legendre_synth<T2>(P, xs, F, nullptr, P.lmax));
+  WF_CUDA(cudaEventRecord(e1, P.stream));
+  WF_CUDA(cudaEventSynchronize(e1));
+  WF_CUDA(cudaEventElapsedTime(ms, e0, e1));
+  return WF_OK;
+}
+
+template <typename T2>
+static wf_status time_anal(Plan &P, T2 *G, cudaEvent_t e0, cudaEvent_t e1, float *ms) {
+  WF_TRY(launch_legendre_anal<T2>(P, G, P.xtmp, nullptr, ANA_PLAIN, P.lmax));
+  WF_CUDA(cudaEventRecord(e0, P.stream));
+  for (int r = 0; r < 2; ++r)
+    WF_TRY(launch_legendre_anal<T2>(P, G, P.xtmp, nullptr, ANA_PLAIN, P.lmax));
+  WF_CUDA(cudaEventRecord(e1, P.stream));
+  WF_CUDA(cudaEventSynchronize(e1));
+  WF_CUDA(cudaEventElapsedTime(ms, e0, e1));
+  return WF_OK;
+}
+
+wf_status autotune(Plan &P) {
+  const std::pair<int, int> key(P.nside, P.lmax);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      for (int k = 0; k < 2; ++k) {
+        P.syn_np[k] = it->second.syn[k];
+        P.ana_np[k] = it->second.ana[k];
+      }
+      return WF_OK;
+    }
+  }
+  // inputs are zeros: the kernels' work does not depend on the values
+  WF_CUDA(cudaMemsetAsync(P.xs32, 0, sizeof(float2) * P.nalm, P.stream));
+  WF_CUDA(cudaMemsetAsync(P.xs64, 0, sizeof(double2) * P.nalm, P.stream));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  WF_CUDA(cudaEventCreate(&e0));
+  WF_CUDA(cudaEventCreate(&e1));
+  static const int syn_cand[3] = {1, 2, 4};
+  static const int ana_cand32[4] = {2, 4, 8, 16};
+  static const int ana_cand64[3] = {2, 4, 8};
+  wf_status st = WF_OK;
+  for (int k = 0; k < 2 && st == WF_OK; ++k) {  // 0 = FP64, 1 = FP32
+    float best = 1e30f;
+    int pick = P.syn_np[k];
+    for (int c : syn_cand) {
+      P.syn_np[k] = c;
+      float ms = 0.f;
+      st = k ? time_synth<float2>(P, P.xs32, P.F32, e0, e1, &ms)
+             : time_synth<double2>(P, P.xs64, P.F64, e0, e1, &ms);
+      if (st != WF_OK) break;
+      if (ms < best) {
+        best = ms;
+        pick = c;
+      }
+    }
+    P.syn_np[k] = pick;
+    best = 1e30f;
+    pick = P.ana_np[k];
+    const int *cand = k ? ana_cand32 : ana_cand64;
+    const int nc = k ? 4 : 3;
+    for (int i = 0; i < nc && st == WF_OK; ++i) {
+      P.ana_np[k] = cand[i];
+      float ms = 0.f;
+      st = k ? time_anal<float2>(P, P.G32, e0, e1, &ms)
+             : time_anal<double2>(P, P.G64, e0, e1, &ms);
+      if (st == WF_OK && ms < best) {
+        best = ms;
+        pick = cand[i];
+      }
+    }
+    P.ana_np[k] = pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != WF_OK) return st;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  Choice c;
+  for (int k = 0; k < 2; ++k) {
+    c.syn[k] = P.syn_np[k];
+    c.ana[k] = P.ana_np[k];
+  }
+  g_tune_cache[key] = c;
+  return WF_OK;
+}
+
+}  // namespace wf

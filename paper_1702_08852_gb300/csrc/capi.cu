@@ -5,6 +5,7 @@
 
 #include <new>
 #include <string>
+#include <vector>
 
 #include "wf_internal.cuh"
 
@@ -159,6 +160,7 @@ wf_status wf_plan(wf_plan_t *out, int nside, int lmax, const double *cl_host,
     s = build_tables(*P);
     if (s == WF_OK) s = alloc_work(*P);
     if (s == WF_OK && noise_var_dev) s = upload_noise(*P, noise_var_dev, mask_dev);
+    if (s == WF_OK && o.autotune) s = autotune(*P);
     if (s == WF_OK) {
       cudaError_t e = cudaStreamSynchronize(P->stream);
       if (e != cudaSuccess) {
@@ -256,6 +258,22 @@ wf_status wf_residual(wf_plan_t plan, const double *d_dev, const double *alm_dev
   if (!plan) return arg_error("wf_residual: plan is NULL");
   if (!d_dev || !alm_dev) return arg_error("wf_residual: NULL input");
   return residual(*plan, d_dev, alm_dev, rel_res_wf, rel_res_fp, chi2);
+}
+
+wf_status wf_solve_batch(wf_plan_t *plans, int n, const double *const *d_dev,
+                         double *const *alm_dev, double *const *map_dev, wf_stats *stats,
+                         double *elapsed_ms) {
+  if (!plans || n < 1 || !d_dev) return arg_error("wf_solve_batch: NULL or empty batch");
+  if (n > 4096) return arg_error("wf_solve_batch: at most 4096 maps");
+  std::vector<Plan *> ps(n);
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i] || !d_dev[i]) return arg_error("wf_solve_batch: NULL plan or data");
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return arg_error("wf_solve_batch: a plan appears twice");
+    if (!plans[i]->has_noise) return arg_error("wf_solve_batch: a plan has no noise");
+    ps[i] = plans[i];
+  }
+  return solve_batch(ps.data(), n, d_dev, alm_dev, map_dev, stats, elapsed_ms);
 }
 
 wf_status wf_residual_static(wf_plan_t plan, const double *d_dev, const double *alm_dev,

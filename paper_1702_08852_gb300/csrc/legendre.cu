@@ -226,11 +226,7 @@ __global__ void __launch_bounds__(SYN_THREADS)
 constexpr int ANA_THREADS = 128;
 constexpr int ANA_WARPS = ANA_THREADS / 32;
 constexpr int LCHUNK = 16;
-// ring pairs per thread in the analysis: more pairs amortise the warp
-// reduction (FP32); FP64 is bound by its arithmetic pipe and keeps registers low
-template <typename T> struct AnaNP;
-template <> struct AnaNP<float> { static constexpr int v = 8; };
-template <> struct AnaNP<double> { static constexpr int v = 4; };
+
 
 // v[0..31] per lane -> lane i returns sum over lanes of v[i]
 template <typename T>
@@ -439,19 +435,42 @@ struct Kernels<float2> {
   typedef float T;
 };
 
+template <typename T, int NP>
+static void synth_variant(const Plan &P, const typename Vec2<T>::type *xs,
+                          typename Vec2<T>::type *F, const SolverState *st, int lstatic) {
+  typedef typename Vec2<T>::type T2;
+  const size_t smem = align16(sizeof(T2) * (P.lmax + 1)) + sizeof(T) * (P.lmax + 1);
+  const int pairs_per_cta = SYN_THREADS * NP;
+  dim3 grid((P.npairs + pairs_per_cta - 1) / pairs_per_cta, P.lmax + 1);
+  k_legendre_synth<T, NP><<<grid, SYN_THREADS, smem, P.stream>>>(
+      P.pairs, P.npairs, P.lmax, P.rc, P.rc32, P.rg, P.seed_l, P.seed_u, xs, F, st,
+      lstatic);
+}
+
+template <typename T, int NP>
+static void anal_variant(const Plan &P, const typename Vec2<T>::type *G, double2 *x,
+                         const SolverState *st, int mode, int lstatic, const double2 *src,
+                         typename Vec2<T>::type *xs_out) {
+  typedef typename Vec2<T>::type T2;
+  const size_t smem =
+      align16(sizeof(T2) * (P.lmax + 1) * ANA_WARPS) + sizeof(T) * (P.lmax + 1);
+  k_legendre_anal<T, NP><<<P.lmax + 1, ANA_THREADS, smem, P.stream>>>(
+      P.pairs, P.npairs, P.lmax, P.rc, P.rc32, P.rg, P.seed_l, P.seed_u, P.cl_d, P.omega,
+      G, x, P.partials, src, xs_out, st, mode, lstatic);
+}
+
+// ring pairs per thread: the autotuner's choice for this plan and precision
 template <typename T2>
 wf_status launch_legendre_synth(const Plan &P, const T2 *xs, T2 *F,
                                 const SolverState *st, int lstatic) {
   typedef typename Kernels<T2>::T T;
-  constexpr int NP = 2;
-  auto kern = k_legendre_synth<T, NP>;
-  const size_t smem = align16(sizeof(T2) * (P.lmax + 1)) + sizeof(T) * (P.lmax + 1);
-  const int pairs_per_cta = SYN_THREADS * NP;
-  dim3 grid((P.npairs + pairs_per_cta - 1) / pairs_per_cta, P.lmax + 1);
+  const int np = P.syn_np[sizeof(T) == 4];
   ++P.nlaunch;
-  kern<<<grid, SYN_THREADS, smem, P.stream>>>(P.pairs, P.npairs, P.lmax, P.rc,
-                                              P.rc32, P.rg, P.seed_l, P.seed_u,
-                                              xs, F, st, lstatic);
+  switch (np) {
+    case 1: synth_variant<T, 1>(P, xs, F, st, lstatic); break;
+    case 4: synth_variant<T, 4>(P, xs, F, st, lstatic); break;
+    default: synth_variant<T, 2>(P, xs, F, st, lstatic); break;
+  }
   WF_CUDA(cudaGetLastError());
   return WF_OK;
 }
@@ -461,28 +480,45 @@ wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
                                const SolverState *st, int mode, int lstatic,
                                const double2 *src, T2 *xs_out) {
   typedef typename Kernels<T2>::T T;
-  constexpr int NP = AnaNP<T>::v;
-  auto kern = k_legendre_anal<T, NP>;
-  const size_t smem =
-      align16(sizeof(T2) * (P.lmax + 1) * ANA_WARPS) + sizeof(T) * (P.lmax + 1);
+  const int np = P.ana_np[sizeof(T) == 4];
   ++P.nlaunch;
-  kern<<<P.lmax + 1, ANA_THREADS, smem, P.stream>>>(
-      P.pairs, P.npairs, P.lmax, P.rc, P.rc32, P.rg, P.seed_l, P.seed_u, P.cl_d,
-      P.omega, G, x, P.partials, src, xs_out, st, mode, lstatic);
+  switch (np) {
+    case 2: anal_variant<T, 2>(P, G, x, st, mode, lstatic, src, xs_out); break;
+    case 4: anal_variant<T, 4>(P, G, x, st, mode, lstatic, src, xs_out); break;
+    case 16: anal_variant<T, 16>(P, G, x, st, mode, lstatic, src, xs_out); break;
+    default: anal_variant<T, 8>(P, G, x, st, mode, lstatic, src, xs_out); break;
+  }
   WF_CUDA(cudaGetLastError());
   return WF_OK;
 }
 
+template <typename T, int NP>
+static cudaError_t set_big_smem_synth(int big) {
+  return cudaFuncSetAttribute(k_legendre_synth<T, NP>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+template <typename T, int NP>
+static cudaError_t set_big_smem_anal(int big) {
+  return cudaFuncSetAttribute(k_legendre_anal<T, NP>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+}
+
 wf_status init_legendre_attributes() {
   const int big = 220 * 1024;
-  WF_CUDA(cudaFuncSetAttribute(k_legendre_synth<double, 2>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  WF_CUDA(cudaFuncSetAttribute(k_legendre_synth<float, 2>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal<double, AnaNP<double>::v>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal<float, AnaNP<float>::v>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  WF_CUDA((set_big_smem_synth<double, 1>(big)));
+  WF_CUDA((set_big_smem_synth<double, 2>(big)));
+  WF_CUDA((set_big_smem_synth<double, 4>(big)));
+  WF_CUDA((set_big_smem_synth<float, 1>(big)));
+  WF_CUDA((set_big_smem_synth<float, 2>(big)));
+  WF_CUDA((set_big_smem_synth<float, 4>(big)));
+  WF_CUDA((set_big_smem_anal<double, 2>(big)));
+  WF_CUDA((set_big_smem_anal<double, 4>(big)));
+  WF_CUDA((set_big_smem_anal<double, 8>(big)));
+  WF_CUDA((set_big_smem_anal<double, 16>(big)));
+  WF_CUDA((set_big_smem_anal<float, 2>(big)));
+  WF_CUDA((set_big_smem_anal<float, 4>(big)));
+  WF_CUDA((set_big_smem_anal<float, 8>(big)));
+  WF_CUDA((set_big_smem_anal<float, 16>(big)));
   return WF_OK;
 }
 

@@ -110,6 +110,11 @@ struct Plan {
   int *seed_l = nullptr;         // [lmax+1][npairs] first l with |lambda| >= 2^-100
   double2 *seed_u = nullptr;     // [lmax+1][npairs] (u_ls, u_ls+1)
 
+  // launch variants (ring pairs per thread), [0] = FP64, [1] = FP32; set by
+  // the autotuner (opts.autotune) or the defaults below
+  int syn_np[2] = {2, 2};
+  int ana_np[2] = {4, 8};
+
   // FFT tables
   int fftMmax = 1;
   double2 *tw64 = nullptr;       // e^{-2 pi i k / Mmax}, k < Mmax/2
@@ -200,6 +205,13 @@ wf_status launch_ring(const Plan &P, int mode, const T2 *F, T2 *G,
 // once per plan (kernel attributes; allowed outside stream capture only)
 wf_status init_legendre_attributes();
 wf_status init_ring_attributes();
+
+// autotune.cu: time the Legendre launch variants once per geometry
+wf_status autotune(Plan &P);
+
+// batch.cu
+wf_status solve_batch(Plan **plans, int n, const double *const *d, double *const *alm,
+                      double *const *map, wf_stats *stats, double *wall_ms);
 
 // plan.cu
 wf_status build_tables(Plan &P);

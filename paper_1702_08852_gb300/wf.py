@@ -35,7 +35,7 @@ class wf_opts(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("stop_rule", ctypes.c_int),
                 ("precision", ctypes.c_int), ("band_limit", ctypes.c_int),
                 ("graph_chunk", ctypes.c_int), ("refine_max", ctypes.c_int),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class wf_stats(ctypes.Structure):
@@ -72,6 +72,9 @@ def lib():
             "wf_solve_host": (I, [_P, _P, _P, _P, ctypes.POINTER(wf_stats)]),
             "wf_residual": (I, [_P, _P, _P, ctypes.POINTER(D), ctypes.POINTER(D),
                                 ctypes.POINTER(D)]),
+            "wf_solve_batch": (I, [ctypes.POINTER(_P), I, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                   ctypes.POINTER(_P), ctypes.POINTER(wf_stats),
+                                   ctypes.POINTER(D)]),
             "wf_residual_static": (I, [_P, _P, _P, ctypes.POINTER(D), ctypes.POINTER(D),
                                        ctypes.POINTER(D)]),
             "wf_alm2map": (I, [_P, _P, _P]),
@@ -319,6 +322,31 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def wf_solve_batch(plans, ds, want_alm=True, want_map=False, check=True):
+    """Solve several independent problems together (one plan per map).
+    Returns (alms, maps, stats list, elapsed_ms)."""
+    import torch
+    n = len(plans)
+    if len(ds) != n:
+        raise ValueError("one data map per plan")
+    alms = [torch.empty(p.nalm, dtype=torch.complex128, device=d.device) if want_alm else None
+            for p, d in zip(plans, ds)]
+    maps = [torch.empty(p.npix, dtype=torch.float64, device=d.device) if want_map else None
+            for p, d in zip(plans, ds)]
+    P = (_P * n)(*[p.handle for p in plans])
+    D = (_P * n)(*[_dev_ptr(d, torch.float64, p.npix, "d") for p, d in zip(plans, ds)])
+    A = (_P * n)(*[(_dev_ptr(a, torch.complex128, p.nalm, "alm") if a is not None else None)
+                   for p, a in zip(plans, alms)])
+    M = (_P * n)(*[(_dev_ptr(m, torch.float64, p.npix, "map") if m is not None else None)
+                   for p, m in zip(plans, maps)])
+    st = (wf_stats * n)()
+    ms = ctypes.c_double()
+    status = lib().wf_solve_batch(P, n, D, A, M, st, ctypes.byref(ms))
+    if check and status != WF_OK:
+        _check(status)
+    return alms, maps, [s.as_dict() for s in st], ms.value
 
 
 # -- functional names of the C ABI ------------------------------------------

@@ -1,0 +1,52 @@
+"""bench.py's multi-rank bookkeeping (weak scaling over independent maps),
+run as two gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    mx = bench.max_over_ranks(100.0 + 50.0 * rank, dist, torch.device("cpu"))
+    out[rank] = (mx, bench.aggregate_value(world, 3, mx))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_value():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    for r in range(world):
+        mx, val = out[r]
+        assert mx == 150.0
+        assert val == pytest.approx(2 * 3 / 0.150)
+
+
+def test_single_rank_defaults():
+    import bench
+    assert bench.max_over_ranks(12.5) == 12.5
+    assert bench.aggregate_value(1, 2, 4000.0) == pytest.approx(0.5)
