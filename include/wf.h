@@ -226,6 +226,39 @@ wf_status wf_kernel_stats(wf_plan_t plan, int kernel, double *ms, long *launches
  * number of (l, m, ring pair) terms with l <= L and |lambda_lm| >= 2^-100. */
 wf_status wf_legendre_terms(wf_plan_t plan, int L, double *terms);
 
+/* ---- learned warm start (the paper has none; an extension of the method)
+ * A small network maps (d, log sigma^2, mask) to an initial messenger field
+ * t0 (Npix) and initial signal coefficients a0 (Nalm), for wf_solve's
+ * init_map_dev / init_alm_dev.  Architecture: per-ring circular 1-D
+ * convolutions (3 -> channels -> channels -> 1, odd kernel width) that
+ * correct the masked data, t0 = (1-m) d + sigma_d r; a = Omega Y^T t0; a
+ * per-l MLP (4 features -> hidden -> hidden -> 1, sigmoid) gives a gain q_l,
+ * a0 = q_l a.  Weights are FP32 masters used rounded to BF16 (bf16 = 1) or
+ * as FP32 (bf16 = 0); accumulation is FP32.  The net uses the plan's
+ * geometry, spectrum, noise and mask (it reads them at each call) and the
+ * plan's stream; it must not be used while the plan solves.
+ * Parameters are one flat float vector (conv W1 [c][3][k], b1, W2 [c][c][k],
+ * b2, W3 [1][c][k], b3, then MLP V1 [h][4], c1, V2 [h][h], c2, V3 [1][h], c3);
+ * they start at zero -- set them with wf_net_set_params. */
+typedef struct wf_net_s *wf_net_t;
+wf_status wf_net_create(wf_net_t *out, wf_plan_t plan, int channels, int kernel,
+                        int hidden, int bf16);
+long wf_net_num_params(wf_net_t net);
+wf_status wf_net_set_params(wf_net_t net, const float *params_host, long n);
+wf_status wf_net_get_params(wf_net_t net, float *params_host, long n);
+/* Forward pass on data d (device, Npix); t0_dev (Npix) and alm0_dev
+ * (2 Nalm doubles) may be NULL. */
+wf_status wf_net_forward(wf_net_t net, const double *d_dev, double *t0_dev,
+                         double *alm0_dev);
+/* Loss L = sum w |a0 - a*|^2 / sum w |a*|^2 against alm_target_dev (the
+ * solver's solution) and its gradient w.r.t. every parameter (kept on the
+ * device for wf_net_adam_step; copied to grad_host if not NULL). */
+wf_status wf_net_loss_grad(wf_net_t net, const double *d_dev,
+                           const double *alm_target_dev, double *loss, float *grad_host);
+/* One Adam update with the last gradient. */
+wf_status wf_net_adam_step(wf_net_t net, float lr, float beta1, float beta2, float eps);
+void wf_net_destroy(wf_net_t net);
+
 void wf_destroy(wf_plan_t plan);
 const char *wf_status_str(wf_status s);
 const char *wf_last_error(void);

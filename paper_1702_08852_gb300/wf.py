@@ -87,6 +87,15 @@ def lib():
             "wf_kernel_stats": (I, [_P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long),
                                     ctypes.POINTER(D), I]),
             "wf_legendre_terms": (I, [_P, I, ctypes.POINTER(D)]),
+            "wf_net_create": (I, [ctypes.POINTER(_P), _P, I, I, I, I]),
+            "wf_net_num_params": (ctypes.c_long, [_P]),
+            "wf_net_set_params": (I, [_P, _P, ctypes.c_long]),
+            "wf_net_get_params": (I, [_P, _P, ctypes.c_long]),
+            "wf_net_forward": (I, [_P, _P, _P, _P]),
+            "wf_net_loss_grad": (I, [_P, _P, _P, ctypes.POINTER(D), _P]),
+            "wf_net_adam_step": (I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float]),
+            "wf_net_destroy": (None, [_P]),
             "wf_destroy": (None, [_P]),
             "wf_status_str": (ctypes.c_char_p, [I]),
             "wf_last_error": (ctypes.c_char_p, []),
@@ -347,6 +356,65 @@ def wf_solve_batch(plans, ds, want_alm=True, want_map=False, check=True):
     if check and status != WF_OK:
         _check(status)
     return alms, maps, [s.as_dict() for s in st], ms.value
+
+
+class Net:
+    """The warm-start network of a plan (include/wf.h, wf_net_*)."""
+
+    def __init__(self, plan, channels=16, kernel=9, hidden=32, bf16=True):
+        h = ctypes.c_void_p()
+        _check(lib().wf_net_create(ctypes.byref(h), plan.handle, int(channels), int(kernel),
+                                   int(hidden), int(bool(bf16))))
+        self.handle, self.plan = h, plan
+        self.channels, self.kernel, self.hidden = channels, kernel, hidden
+        self.nparams = int(lib().wf_net_num_params(h))
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        _check(lib().wf_net_set_params(self.handle, theta.ctypes.data_as(ctypes.c_void_p),
+                                       theta.size))
+
+    def get_params(self):
+        out = np.empty(self.nparams, dtype=np.float32)
+        _check(lib().wf_net_get_params(self.handle, out.ctypes.data_as(ctypes.c_void_p),
+                                       out.size))
+        return out
+
+    def forward(self, d):
+        import torch
+        p = self.plan
+        t0 = torch.empty(p.npix, dtype=torch.float64, device=d.device)
+        a0 = torch.empty(p.nalm, dtype=torch.complex128, device=d.device)
+        _check(lib().wf_net_forward(self.handle, _dev_ptr(d, torch.float64, p.npix, "d"),
+                                    _dev_ptr(t0, torch.float64, p.npix, "t0"),
+                                    _dev_ptr(a0, torch.complex128, p.nalm, "a0")))
+        return t0, a0
+
+    def loss_grad(self, d, target, want_grad=False):
+        import torch
+        p = self.plan
+        loss = ctypes.c_double()
+        g = np.empty(self.nparams, dtype=np.float32) if want_grad else None
+        _check(lib().wf_net_loss_grad(
+            self.handle, _dev_ptr(d, torch.float64, p.npix, "d"),
+            _dev_ptr(target, torch.complex128, p.nalm, "target"), ctypes.byref(loss),
+            g.ctypes.data_as(ctypes.c_void_p) if g is not None else None))
+        return loss.value, g
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(lib().wf_net_adam_step(self.handle, float(lr), float(beta1), float(beta2),
+                                      float(eps)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().wf_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # -- functional names of the C ABI ------------------------------------------
