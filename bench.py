@@ -48,7 +48,11 @@ def parse():
                     help="run only the Legendre kernels of one transform pair "
                          "(small case for profiling) and exit")
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--workload", choices=["nside1024", "batch64"], default="nside1024",
+    ap.add_argument("--train-maps", type=int, default=64)
+    ap.add_argument("--eval-maps", type=int, default=8)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--workload", choices=["nside1024", "batch64", "learned"],
+                    default="nside1024",
                     help="batch64: 64 maps, Nside drawn from {64, 128, 256}, solved "
                          "together (maps/s)")
     return ap.parse_args()
@@ -418,6 +422,110 @@ def run_batch(args, rank, world):
             "clocks": clk}
 
 
+def run_learned(args, rank, world):
+    """Learned warm start at Nside 256 (lmax 512): train the network on
+    solutions of the plain solver for --train-maps seeds of the Nside-256
+    scan workload, then compare cold and warm solves on --eval-maps held-out
+    seeds (iterations, time, fallback, agreement)."""
+    import numpy as np
+    import torch
+    from paper_1702_08852_gb300 import inputs, wf, learned
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    ns = 256
+    H, K, Hm = 16, 9, 32
+    t_start = time.perf_counter()
+
+    def make(seed):
+        p = inputs.scan_problem(ns, seed=seed, mask_fraction=0.25, discs=500,
+                                disc_radius_deg=0.5)
+        nv = torch.from_numpy(p.noise_var).to(dev)
+        mk = torch.from_numpy(p.mask.astype(np.uint8)).to(dev)
+        return p, nv, mk
+
+    samples = []
+    gen_plan = None
+    for i in range(args.train_maps):
+        p, nv, mk = make(5000 + i)
+        if gen_plan is None:
+            gen_plan = wf.Plan(p.nside, p.lmax, p.cl, nv, mk, precision=wf.WF_PREC_MIXED,
+                               eps_final=args.eps)
+        else:
+            gen_plan.set_noise(nv, mk)
+            gen_plan.set_cl(p.cl)
+        s = gen_plan.alm2map(torch.from_numpy(p.alm_true).to(dev))
+        d = s + torch.from_numpy(p.noise).to(dev)
+        d[torch.from_numpy(p.mask).to(dev)] = 0.0
+        a, _, _ = gen_plan.solve(d, want_map=False)
+        samples.append((nv, mk, p.cl, d, a))
+    t_gen = time.perf_counter() - t_start
+    net = wf.Net(gen_plan, H, K, Hm, bf16=True)
+    net.set_params(learned.init_params(H, K, Hm, seed=0))
+    t0 = time.perf_counter()
+    hist = learned.train(net, samples, epochs=args.epochs, lr=2e-3)
+    t_train = time.perf_counter() - t0
+    theta = net.get_params()
+    rows = []
+    for i in range(args.eval_maps):
+        p, nv, mk = make(9000 + i)
+        gen_plan.set_noise(nv, mk)
+        gen_plan.set_cl(p.cl)
+        s = gen_plan.alm2map(torch.from_numpy(p.alm_true).to(dev))
+        d = s + torch.from_numpy(p.noise).to(dev)
+        d[torch.from_numpy(p.mask).to(dev)] = 0.0
+        alpha = float(np.min(p.noise_var[~p.mask]))
+        cold = wf.Plan(p.nside, p.lmax, p.cl, nv, mk, precision=wf.WF_PREC_MIXED,
+                       eps_final=args.eps)
+        warm = wf.Plan(p.nside, p.lmax, p.cl, nv, mk, precision=wf.WF_PREC_MIXED,
+                       eps_final=args.eps, mu0=30.0 * alpha)
+        wnet = wf.Net(warm, H, K, Hm, bf16=True)
+        wnet.set_params(theta)
+        cold.solve(d, want_map=False)          # warm-up (graph capture)
+        learned.warm_solve(wnet, warm, d)
+        torch.cuda.synchronize()
+        tc = time.perf_counter()
+        ac, mc, sc = cold.solve(d)
+        torch.cuda.synchronize()
+        tc = time.perf_counter() - tc
+        tw = time.perf_counter()
+        aw, mw, sw, used, res = learned.warm_solve(wnet, warm, d)
+        torch.cuda.synchronize()
+        tw = time.perf_counter() - tw
+        rows.append({"cold_iterations": sc["iterations"], "cold_s": tc,
+                     "warm_iterations": sw["iterations"], "warm_s": tw, "used_warm": used,
+                     "warm_start_residual": res,
+                     "warm_vs_cold_rel_l2": float(torch.linalg.norm(mw - mc) /
+                                                  torch.linalg.norm(mc)),
+                     "warm_fp64_cauchy": sw["fp_residual"]})
+        wnet.close()
+        cold.close()
+        warm.close()
+    net.close()
+    gen_plan.close()
+    if rank != 0:
+        return None
+    ci = sum(r["cold_iterations"] for r in rows) / len(rows)
+    wi = sum(r["warm_iterations"] for r in rows) / len(rows)
+    ct = sum(r["cold_s"] for r in rows) / len(rows)
+    wt = sum(r["warm_s"] for r in rows) / len(rows)
+    return {"metric": "learned warm start, Nside 256: held-out iterations and time to the "
+                      "1e-6 criterion, warm vs cold",
+            "value": ct / wt, "unit": "x (cold time / warm time)", "n_gpus": world,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "Nside 256 lmax 512 scan noise 25 % mask",
+                       "train_maps": args.train_maps, "eval_maps": args.eval_maps,
+                       "epochs": args.epochs, "net": {"channels": H, "kernel": K,
+                                                      "hidden": Hm, "params": len(theta),
+                                                      "weights": "bf16 (fp32 master)"},
+                       "warm_mu0": "30 alpha"},
+            "train": {"loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
+                      "data_gen_s": t_gen, "train_s": t_train},
+            "eval": {"cold_iterations_mean": ci, "warm_iterations_mean": wi,
+                     "cold_s_mean": ct, "warm_s_mean": wt,
+                     "fallbacks": sum(1 for r in rows if not r["used_warm"]),
+                     "per_map": rows}}
+
+
 def run_kernel_case(args):
     """One FP32 (or FP64) synthesis + analysis pair at full band on a random
     band-limited field, repeated --reps times; prints the event timings."""
@@ -463,6 +571,8 @@ def main():
         out = run_reference(args, rank, world)
     elif args.workload == "batch64":
         out = run_batch(args, rank, world)
+    elif args.workload == "learned":
+        out = run_learned(args, rank, world)
     else:
         out = run_ours(args, rank, world)
     if rank == 0 and out is not None:
