@@ -481,14 +481,14 @@ def run_learned(args, rank, world):
         wnet = wf.Net(warm, H, K, Hm, bf16=True)
         wnet.set_params(theta)
         cold.solve(d, want_map=False)          # warm-up (graph capture)
-        learned.warm_solve(wnet, warm, d)
+        learned.warm_solve(wnet, warm, d, cold_plan=cold)
         torch.cuda.synchronize()
         tc = time.perf_counter()
         ac, mc, sc = cold.solve(d)
         torch.cuda.synchronize()
         tc = time.perf_counter() - tc
         tw = time.perf_counter()
-        aw, mw, sw, used, res = learned.warm_solve(wnet, warm, d)
+        aw, mw, sw, used, res = learned.warm_solve(wnet, warm, d, cold_plan=cold)
         torch.cuda.synchronize()
         tw = time.perf_counter() - tw
         rows.append({"cold_iterations": sc["iterations"], "cold_s": tc,

@@ -5,10 +5,14 @@ warm-or-cold decision).
 
 The net maps (d, log sigma^2, mask) to (t0, a0).  A warm solve starts
 Algorithm 2 from (a0, t0) with a cooling start mu0 = mu0_over_alpha * alpha
-instead of the cold start (s = 0, t = d, mu0 Omega = beta max C_l).  It is
-used only when it helps on the problem at hand: if the Wiener-filter residual
-||A x - y|| / ||y|| (App. C) of a0 is not below that of the zero start
-(which is 1), the cold start is used instead.
+instead of the cold start (s = 0, t = d, mu0 Omega = beta max C_l), i.e. it
+skips the stages above mu0.  The plain method judges the warm start: it is
+used only if its Wiener-filter residual ||A x - y|| / ||y|| (App. C) is
+below both the zero start's (1) and the tolerance of the stage it enters,
+eps_k = min(eps_cap, eps_final mu0 / alpha); the cold stages would hand that
+stage an iterate within its tolerance, and a start farther away costs more
+late-stage iterations than the skipped early stages save.  Otherwise the
+cold start is used.
 """
 import numpy as np
 
@@ -52,15 +56,21 @@ def train(net, samples, epochs=20, lr=3e-3, seed=0, plans=None, log=None):
     return hist
 
 
-def warm_solve(net, plan, d, mu0_over_alpha=30.0):
-    """Solve with the net's warm start when it beats the zero start (see the
-    module docstring).  ``plan`` must be the net's plan geometry with the
-    problem's noise/mask/spectrum and its cooling start set to
-    mu0_over_alpha * alpha.  Returns (alm, map, stats, used_warm, residual)."""
+def entry_tolerance(plan, mu0_over_alpha):
+    o = plan.opts
+    return min(o.eps_cap, o.eps_final * max(1.0, mu0_over_alpha))
+
+
+def warm_solve(net, plan, d, mu0_over_alpha=30.0, cold_plan=None):
+    """Solve with the net's warm start when the plain method accepts it (see
+    the module docstring).  ``plan`` is the net's plan (the problem's noise,
+    mask, spectrum) with its cooling start set to mu0_over_alpha * alpha;
+    ``cold_plan`` (default: ``plan``) runs the cold start when the warm one
+    is rejected.  Returns (alm, map, stats, used_warm, residual)."""
     t0, a0 = net.forward(d)
     res = plan.residual(d, a0)["rel_res_wf"]
-    if not (res < 1.0):
-        alm, mp, st = plan.solve(d)
-        return alm, mp, st, False, res
-    alm, mp, st = plan.solve(d, init_alm=a0, init_map=t0)
-    return alm, mp, st, True, res
+    if res < min(1.0, entry_tolerance(plan, mu0_over_alpha)):
+        alm, mp, st = plan.solve(d, init_alm=a0, init_map=t0)
+        return alm, mp, st, True, res
+    alm, mp, st = (cold_plan or plan).solve(d)
+    return alm, mp, st, False, res

@@ -107,6 +107,8 @@ def test_training_lowers_the_loss_and_warm_solve_is_exact(torch_cuda, osht, odm)
             wnet = wf.Net(wp, 8, 5, 16)
             wnet.set_params(net.get_params())
             alm, mp, st, used, res = learned.warm_solve(wnet, wp, torch.from_numpy(d).cuda())
+            # the judge: warm only when within the entry stage's tolerance
+            assert used == (res < learned.entry_tolerance(wp, 30.0))
             wnet.close()
         net.close()
     ref = odm.dm_fixed_point_dense(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d, 0.0)
