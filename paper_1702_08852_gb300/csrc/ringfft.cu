@@ -71,36 +71,80 @@ __device__ __forceinline__ T2 cconj(T2 a) {
   return CT<T2>::mk(a.x, -a.y);
 }
 
-// natural -> bit-reversed; INV uses e^{+2 pi i jk/M}
+// multiply by -i (forward) or +i (inverse)
+template <typename T2, bool INV>
+__device__ __forceinline__ T2 rot_q(T2 a) {
+  return INV ? CT<T2>::mk(-a.y, a.x) : CT<T2>::mk(a.y, -a.x);
+}
+
+// natural -> bit-reversed; INV uses e^{+2 pi i jk/M}.  Two radix-2 stages
+// (spans h and h/2) per pass over shared memory ("radix-2^2"): the output
+// order stays bit-reversed, and the barriers and shared-memory round trips
+// halve.  An odd number of stages ends with one radix-2 pass of span 1.
 template <typename T2, bool INV>
 __device__ void fft_dif(T2 *buf, int M, const T2 *__restrict__ tw, int Mmax) {
-  for (int h = M >> 1; h >= 1; h >>= 1) {
+  int h = M >> 1;
+  for (; h >= 2; h >>= 2) {
+    const int q = h >> 1;
     const int ts = Mmax / (2 * h);
+    for (int b = threadIdx.x; b < (M >> 2); b += blockDim.x) {
+      const int j = b & (q - 1);
+      const int i0 = ((b - j) << 2) + j, i1 = i0 + q, i2 = i0 + h, i3 = i2 + q;
+      const T2 w1 = tw[j * ts], w2 = tw[2 * j * ts];  // W_2h^j, W_h^j
+      const T2 x0 = buf[i0], x1 = buf[i1], x2 = buf[i2], x3 = buf[i3];
+      const T2 a0 = cadd(x0, x2), a1 = cadd(x1, x3);
+      const T2 a2 = INV ? cmulc(csub(x0, x2), w1) : cmul(csub(x0, x2), w1);
+      const T2 a3 = rot_q<T2, INV>(INV ? cmulc(csub(x1, x3), w1) : cmul(csub(x1, x3), w1));
+      buf[i0] = cadd(a0, a1);
+      buf[i1] = INV ? cmulc(csub(a0, a1), w2) : cmul(csub(a0, a1), w2);
+      buf[i2] = cadd(a2, a3);
+      buf[i3] = INV ? cmulc(csub(a2, a3), w2) : cmul(csub(a2, a3), w2);
+    }
+    __syncthreads();
+  }
+  if (h == 1) {
     for (int b = threadIdx.x; b < (M >> 1); b += blockDim.x) {
-      const int j = b & (h - 1);
-      const int i0 = ((b - j) << 1) + j, i1 = i0 + h;
-      const T2 a = buf[i0], c = buf[i1];
-      const T2 w = tw[j * ts];
-      buf[i0] = cadd(a, c);
-      buf[i1] = INV ? cmulc(csub(a, c), w) : cmul(csub(a, c), w);
+      const T2 a = buf[2 * b], c = buf[2 * b + 1];
+      buf[2 * b] = cadd(a, c);
+      buf[2 * b + 1] = csub(a, c);
     }
     __syncthreads();
   }
 }
 
-// bit-reversed -> natural
+// bit-reversed -> natural; an odd number of stages starts with one radix-2
+// pass of span 1, then pairs of stages (spans h and 2h) per pass
 template <typename T2, bool INV>
 __device__ void fft_dit(T2 *buf, int M, const T2 *__restrict__ tw, int Mmax) {
-  for (int h = 1; h < M; h <<= 1) {
-    const int ts = Mmax / (2 * h);
+  int h = 1;
+  int bits = 0;
+  while ((1 << bits) < M) ++bits;
+  if (bits & 1) {
     for (int b = threadIdx.x; b < (M >> 1); b += blockDim.x) {
+      const T2 a = buf[2 * b], c = buf[2 * b + 1];
+      buf[2 * b] = cadd(a, c);
+      buf[2 * b + 1] = csub(a, c);
+    }
+    __syncthreads();
+    h = 2;
+  }
+  for (; h < M; h <<= 2) {
+    const int ta = Mmax / (2 * h), tb = Mmax / (4 * h);
+    for (int b = threadIdx.x; b < (M >> 2); b += blockDim.x) {
       const int j = b & (h - 1);
-      const int i0 = ((b - j) << 1) + j, i1 = i0 + h;
-      const T2 w = tw[j * ts];
-      const T2 a = buf[i0];
-      const T2 c = INV ? cmulc(buf[i1], w) : cmul(buf[i1], w);
-      buf[i0] = cadd(a, c);
-      buf[i1] = csub(a, c);
+      const int i0 = ((b - j) << 2) + j, i1 = i0 + h, i2 = i0 + 2 * h, i3 = i2 + h;
+      const T2 wa = tw[j * ta], wb = tw[j * tb];  // W_2h^j, W_4h^j
+      const T2 x0 = buf[i0], x1 = buf[i1], x2 = buf[i2], x3 = buf[i3];
+      const T2 c1 = INV ? cmulc(x1, wa) : cmul(x1, wa);
+      const T2 c3 = INV ? cmulc(x3, wa) : cmul(x3, wa);
+      const T2 a0 = cadd(x0, c1), a1 = csub(x0, c1);
+      const T2 a2 = cadd(x2, c3), a3 = csub(x2, c3);
+      const T2 d2 = INV ? cmulc(a2, wb) : cmul(a2, wb);
+      const T2 d3 = rot_q<T2, INV>(INV ? cmulc(a3, wb) : cmul(a3, wb));
+      buf[i0] = cadd(a0, d2);
+      buf[i2] = csub(a0, d2);
+      buf[i1] = cadd(a1, d3);
+      buf[i3] = csub(a1, d3);
     }
     __syncthreads();
   }
