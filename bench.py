@@ -175,7 +175,7 @@ def run_ours(args, rank, world):
         dist.init_process_group("nccl", device_id=dev)
     p, nv, mk, d = make_workload(args.nside, seed=3000 + rank)
     plan = wf.Plan(p.nside, p.lmax, p.cl, nv, mk, precision=wf.WF_PREC_MIXED,
-                   eps_final=args.eps, timing=1)
+                   eps_final=args.eps, timing=1, autotune=1)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     for _ in range(args.warmup):
@@ -217,7 +217,7 @@ def run_ours(args, rank, world):
     fp64 = {}
     if rank == 0 and not args.no_fp64:
         p64 = wf.Plan(p.nside, p.lmax, p.cl, nv, mk, precision=wf.WF_PREC_FP64,
-                      eps_final=args.eps, timing=1)
+                      eps_final=args.eps, timing=1, autotune=1)
         a64, m64, s64 = p64.solve(d)
         k64 = [p64.kernel_stats(k) for k in (0, 1)]
         fp64 = {"solve_s": s64["elapsed_ms"] / 1e3, "iterations": s64["iterations"],

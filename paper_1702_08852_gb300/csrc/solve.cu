@@ -750,6 +750,7 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
         h.iter = total_iter;
         if (c64 < P.opts.eps_final) {
           converged = true;
+          fp_res = c64;  // the accepted step is the reported residual
           break;
         }
         ++reanchors;
@@ -774,7 +775,7 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
     }
     if (!anchored) converged = h.converged;  // finished inside the data pass
     first_stages = h.stage + 1;
-    {
+    if (!(converged && P.opts.stop_rule == WF_STOP_CAUCHY)) {
       const SolverState keep = h;
       double num = 0.0, xn = 0.0;
       WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num));
