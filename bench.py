@@ -125,6 +125,19 @@ def fp32_alu_peak_tflops(sm_mhz=2070.0):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def ring_roofline(k, peaks, peak_src):
+    """HBM roofline of the ring step (fold, ring FFTs, t-update): algorithmic
+    bytes (ring coefficients in and out, d and sigma^2) per timed launch pair
+    over its CUDA-event time."""
+    if not k["ms"]:
+        return None
+    gbs = k["gbytes"] / (k["ms"] / 1e3)
+    return {"bound": "hbm", "achieved": gbs, "unit": "GB/s", "peak": peaks["hbm_gbs"],
+            "frac": gbs / peaks["hbm_gbs"], "peak_source": peak_src,
+            "avg_launch_ms": k["ms"] / max(1, k["launches"]),
+            "bytes_per_launch": k["gbytes"] * 1e9 / max(1, k["launches"])}
+
+
 # ---------------------------------------------------------------- workload
 def make_workload(nside, seed):
     import numpy as np
@@ -180,8 +193,8 @@ def run_ours(args, rank, world):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     for _ in range(args.warmup):
         alm, mp, st = plan.solve(d)
-    plan.kernel_stats(0, reset=True)
-    plan.kernel_stats(1, reset=True)
+    for k in (0, 1, 2):
+        plan.kernel_stats(k, reset=True)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -200,7 +213,7 @@ def run_ours(args, rank, world):
         stats.append(st)
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(step_ms), dist, dev)
-    kern = [plan.kernel_stats(k) for k in (0, 1)]
+    kern = [plan.kernel_stats(k) for k in (0, 1, 2)]
     ms_step_mean = sum(step_ms) / len(step_ms)
 
     # end to end through the C ABI with host buffers (pinned)
@@ -273,7 +286,8 @@ def run_ours(args, rank, world):
                      "launches": k0["launches"], "avg_launch_ms": k0["ms"] / max(1, k0["launches"]),
                      "synthesis": {"achieved": (kern[1]["gflop"] / (kern[1]["ms"] / 1e3) / 1e3)
                                    if kern[1]["ms"] > 0 else None,
-                                   "avg_launch_ms": kern[1]["ms"] / max(1, kern[1]["launches"])}},
+                                   "avg_launch_ms": kern[1]["ms"] / max(1, kern[1]["launches"])},
+                     "ring_step": ring_roofline(kern[2], peaks, peak_src)},
         "clocks": clk,
         "e2e": {"value": 1.0 / (sum(e2e_s) / len(e2e_s)), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * 12 * args.nside ** 2,

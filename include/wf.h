@@ -208,15 +208,21 @@ long wf_nalm(int lmax);
 wf_status wf_trace(wf_plan_t plan, int *count, int *stage, double *xi,
                    double *mu, double *cauchy);
 
-/* Device time and work of the Legendre kernels in the solves run with
+/* Device time and work of the iteration's kernels in the solves run with
  * opts.timing = 1 since plan creation or the last reset.
- *  kernel    0 = analysis (Omega Y^T with the fused filter), 1 = synthesis.
+ *  kernel    0 = Legendre analysis (Omega Y^T with the fused filter),
+ *            1 = Legendre synthesis, 2 = ring step (fold, inverse ring
+ *            FFTs, the t-update of Eq. 14, forward ring FFTs; both launches).
  *  ms        summed CUDA-event time of the timed launches.
  *  launches  number of timed launches (iterations that did work).
- *  gflop     algorithmic work of those launches: 7 flops (recurrence 3,
- *            complex accumulate 4) per (l, m, ring pair) with l <= the
- *            band limit of the launch and |lambda_lm| >= 2^-100 (the terms
- *            the method needs; the skipped ones are below that).
+ *  gflop     algorithmic work of those launches.  Kernels 0, 1: GFLOP, 7
+ *            flops (recurrence 3, complex accumulate 4) per (l, m, ring pair)
+ *            with l <= the band limit of the launch and |lambda_lm| >=
+ *            2^-100 (the terms the method needs; the skipped ones are below
+ *            that).  Kernel 2: GB of DRAM traffic the step cannot avoid --
+ *            ring coefficients read and written for m <= the band limit
+ *            (8 bytes each in FP32 stages, 16 in FP64) and d, sigma^2 read
+ *            (16 bytes per pixel).
  *  reset     nonzero: clear the counters after reading.
  * Any output pointer may be NULL. */
 wf_status wf_kernel_stats(wf_plan_t plan, int kernel, double *ms, long *launches,

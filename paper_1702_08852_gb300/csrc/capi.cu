@@ -336,7 +336,7 @@ wf_status wf_trace(wf_plan_t plan, int *count, int *stage, double *xi, double *m
 wf_status wf_kernel_stats(wf_plan_t plan, int kernel, double *ms, long *launches,
                           double *gflop, int reset) {
   if (!plan) return arg_error("wf_kernel_stats: plan is NULL");
-  if (kernel < 0 || kernel > 1) return arg_error("wf_kernel_stats: kernel must be 0 or 1");
+  if (kernel < 0 || kernel > 2) return arg_error("wf_kernel_stats: kernel must be 0, 1 or 2");
   if (ms) *ms = plan->kern_ms[kernel];
   if (launches) *launches = plan->kern_launches[kernel];
   if (gflop) *gflop = plan->kern_flop[kernel] * 1e-9;

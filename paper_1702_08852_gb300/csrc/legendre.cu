@@ -184,9 +184,20 @@ __global__ void __launch_bounds__(SYN_THREADS)
       }
     }
     // phase B: plain recurrence
+    // l - m is even here: (c_l, c_l+1) is one aligned pair of T and, in
+    // FP32, (x_l, x_l+1) one aligned 16-byte load
     for (; l + 1 <= L; l += 2) {
-      const T c0 = sc[l - m], c1 = sc[l + 1 - m];
-      const T2 x0 = sx[l - m], x1 = sx[l + 1 - m];
+      const T2 cp = *reinterpret_cast<const T2 *>(sc + (l - m));
+      const T c0 = cp.x, c1 = cp.y;
+      T2 x0, x1;
+      if constexpr (sizeof(T) == 4) {
+        const float4 xp = *reinterpret_cast<const float4 *>(sx + (l - m));
+        x0 = Vec2<T>::make(xp.x, xp.y);
+        x1 = Vec2<T>::make(xp.z, xp.w);
+      } else {
+        x0 = sx[l - m];
+        x1 = sx[l + 1 - m];
+      }
 #pragma unroll
       for (int j = 0; j < NP; ++j) {
         T u = rec_step(c0, zh[j], zl[j], u1[j], u2[j]);
@@ -242,6 +253,64 @@ __device__ __forceinline__ T transpose_reduce32(T (&v)[32], int lane) {
     }
   }
   return v[0];
+}
+
+// One chunk of LCHUNK consecutive l for NP ring pairs per lane: v[2 jj] and
+// v[2 jj + 1] receive this lane's contribution (re, im) to a_{lc+jj, m}.
+// INJ: some lane of the warp still has its seed (ls, ls + 1) in or after this
+// chunk.  TAIL: the chunk runs past L (l > L contributes 0).  In FP32 full
+// chunks the coefficients c_l come from shared memory in 16-byte loads
+// (lc - m is a multiple of LCHUNK and the table starts 16-byte aligned).
+template <typename T, int NP, bool INJ, bool TAIL>
+__device__ __forceinline__ void anal_chunk(T (&v)[32], int lc, int L, int m,
+                                           const T *__restrict__ sc, const T (&zh)[NP],
+                                           const T (&zl)[NP], T (&u1)[NP], T (&u2)[NP],
+                                           const T (&s0)[NP], const T (&s1)[NP],
+                                           const int (&ls)[NP], const T (&pr)[NP],
+                                           const T (&pim)[NP], const T (&qr)[NP],
+                                           const T (&qim)[NP]) {
+  // FP32 full chunks: the 16 coefficients in four 16-byte loads
+  constexpr bool VEC = sizeof(T) == 4 && !TAIL;
+  T cc[VEC ? LCHUNK : 1];
+  if constexpr (VEC) {
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(sc + (lc - m));
+#pragma unroll
+    for (int q = 0; q < LCHUNK / 4; ++q) {
+      const uint4 w = s4[q];
+      memcpy(&cc[4 * q], &w, 16);
+    }
+  }
+#pragma unroll
+  for (int jj = 0; jj < LCHUNK; ++jj) {
+    const int l = lc + jj;
+    T a_re = (T)0, a_im = (T)0;
+    if (!TAIL || l <= L) {
+      T c;
+      if constexpr (VEC)
+        c = cc[jj];
+      else
+        c = sc[l - m];
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        T u = rec_step(c, zh[j], zl[j], u1[j], u2[j]);
+        if (INJ) {
+          u = (l == ls[j]) ? s0[j] : u;
+          u = (l == ls[j] + 1) ? s1[j] : u;
+        }
+        u2[j] = u1[j];
+        u1[j] = u;
+        if ((jj & 1) == 0) {
+          a_re = fma(u, pr[j], a_re);
+          a_im = fma(u, pim[j], a_im);
+        } else {
+          a_re = fma(u, qr[j], a_re);
+          a_im = fma(u, qim[j], a_im);
+        }
+      }
+    }
+    v[2 * jj] = a_re;
+    v[2 * jj + 1] = a_im;
+  }
 }
 
 template <typename T, int NP>
@@ -324,34 +393,19 @@ __global__ void __launch_bounds__(ANA_THREADS)
       const int lc0 = m + ((lmin - m) / LCHUNK) * LCHUNK;
       for (int lc = lc0; lc <= L; lc += LCHUNK) {
         T v[32];
-        const bool inj = lc <= linj;
-#pragma unroll
-        for (int jj = 0; jj < LCHUNK; ++jj) {
-          const int l = lc + jj;
-          T a_re = (T)0, a_im = (T)0;
-          if (l <= L) {
-            const T c = sc[l - m];
-#pragma unroll
-            for (int j = 0; j < NP; ++j) {
-              T u = rec_step(c, zh[j], zl[j], u1[j], u2[j]);
-              if (inj) {
-                u = (l == ls[j]) ? s0[j] : u;
-                u = (l == ls[j] + 1) ? s1[j] : u;
-              }
-              u2[j] = u1[j];
-              u1[j] = u;
-              if ((jj & 1) == 0) {
-                a_re = fma(u, pr[j], a_re);
-                a_im = fma(u, pim[j], a_im);
-              } else {
-                a_re = fma(u, qr[j], a_re);
-                a_im = fma(u, qim[j], a_im);
-              }
-            }
-          }
-          v[2 * jj] = a_re;
-          v[2 * jj + 1] = a_im;
-        }
+        // three specialisations of the chunk body: seeds still to come in
+        // this warp (selects on every step), a full chunk with every seed of
+        // the warp already in (the plain recurrence: 5 FP instructions per
+        // term), and the last, partial chunk
+        if (lc + LCHUNK - 1 > L)
+          anal_chunk<T, NP, true, true>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
+                                        pr, pim, qr, qim);
+        else if (lc <= linj)
+          anal_chunk<T, NP, true, false>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
+                                         pr, pim, qr, qim);
+        else
+          anal_chunk<T, NP, false, false>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
+                                          pr, pim, qr, qim);
         const T tot = transpose_reduce32<T>(v, lane);
         const int l = lc + (lane >> 1);
         if (l <= L) {

@@ -168,27 +168,46 @@ __device__ __forceinline__ int bitrev_n(int x, int bits) {
   return (int)(__brev((unsigned)x) >> (32 - bits));
 }
 
-// e^{i m phi0}, phi0 = pi num / den, with exact integer argument reduction
+// Ring offsets of HEALPix: phi0 = pi num / den with num = 0, or num = 1 and
+// den = n (the ring's pixel count), so e^{i n phi0} = sgn = -1 or +1 and
+// e^{i m phi0} = sgn^j e^{i k phi0} for m = k + j n: one phase per Fourier
+// index k < n of the ring, not one per m.
+//
+// e^{i k phi0}, 0 <= k < den.  When 2 den divides the twiddle table's length
+// (every equatorial ring) the value is a table entry: e^{i pi k / den} =
+// conj(tw[k Mmax / (2 den)]), tw[i] = e^{-2 pi i i / Mmax}; otherwise
+// sincospi with the exact rational argument k / den.
 template <typename T2>
-__device__ __forceinline__ T2 phase(int m, int num, int den) {
+__device__ __forceinline__ T2 ring_phase(int k, int num, int den, int tstep,
+                                         const T2 *__restrict__ tw) {
   typedef typename CT<T2>::T T;
   if (num == 0) return CT<T2>::mk((T)1, (T)0);
-  const int r = (int)(((long long)m * num) % (2LL * den));
+  if (tstep > 0) return cconj(tw[k * tstep]);
   T s, c;
-  CT<T2>::sincospi_(r, den, &s, &c);
+  CT<T2>::sincospi_(k, den, &s, &c);
   return CT<T2>::mk(c, s);
 }
 
 // c_k = sum over m = +-k mod n, |m| <= L, of F[m] e^{i m phi0}
+//     = e^{i k phi0} (sum_j sgn^j F[k + j n] + sum_{j >= 1} sgn^j conj F[j n - k])
 template <typename T2>
 __device__ __forceinline__ T2 fold(const T2 *__restrict__ Fr, int k, int n, int L,
-                                   int num, int den) {
+                                   typename CT<T2>::T sgn, T2 ph) {
   typedef typename CT<T2>::T T;
   T2 acc = CT<T2>::mk((T)0, (T)0);
-  for (int m = k; m <= L; m += n) acc = cadd(acc, cmul(Fr[m], phase<T2>(m, num, den)));
-  for (int m = n - k; m <= L; m += n)
-    if (m > 0) acc = cadd(acc, cconj(cmul(Fr[m], phase<T2>(m, num, den))));
-  return acc;
+  T s = (T)1;
+  for (int m = k; m <= L; m += n) {
+    const T2 f = Fr[m];
+    acc = CT<T2>::mk(acc.x + s * f.x, acc.y + s * f.y);
+    s *= sgn;
+  }
+  s = sgn;
+  for (int m = n - k; m <= L; m += n) {  // m >= 1 since k < n
+    const T2 f = Fr[m];
+    acc = CT<T2>::mk(acc.x + s * f.x, acc.y - s * f.y);
+    s *= sgn;
+  }
+  return cmul(acc, ph);
 }
 
 constexpr int RING_THREADS = 256;
@@ -223,15 +242,18 @@ __global__ void __launch_bounds__(RING_THREADS)
   const long stride = lmax + 1;
   const bool south = rp.ringS >= 0;
   const T2 zero = CT<T2>::mk((T)0, (T)0);
+  const T sgn = rp.phi_num ? (T)-1 : (T)1;  // e^{i n phi0}
+  const int tstep = (rp.phi_num && Mmax % (2 * rp.phi_den) == 0) ? Mmax / (2 * rp.phi_den) : 0;
 
   if (MODE != RING_ANALYSIS) {
     const T2 *FN = F + rp.ringN * stride;
     const T2 *FS = south ? F + rp.ringS * stride : nullptr;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       T2 cN = zero, cS = zero;
-      if (Lf >= 0) {
-        cN = fold(FN, k, n, Lf, rp.phi_num, rp.phi_den);
-        if (south) cS = fold(FS, k, n, Lf, rp.phi_num, rp.phi_den);
+      if (Lf >= 0 && (k <= Lf || n - k <= Lf)) {
+        const T2 ph = ring_phase<T2>(k, rp.phi_num, rp.phi_den, tstep, tw);
+        cN = fold(FN, k, n, Lf, sgn, ph);
+        if (south) cS = fold(FS, k, n, Lf, sgn, ph);
       }
       const T2 Zk = CT<T2>::mk(cN.x - cS.y, cN.y + cS.x);  // cN + i cS
       buf[k] = blue ? cmulc(cconj(Zk), chirp[k]) : Zk;
@@ -297,22 +319,25 @@ __global__ void __launch_bounds__(RING_THREADS)
     bluestein<T2>(buf, n, M, tw, Mmax, chirp, bhat);
   else
     fft_dit<T2, false>(buf, M, tw, Mmax);
-  // split the two real rings and apply e^{-i m phi0}
+  // split the two real rings and apply e^{-i m phi0}: for m = k + j n,
+  // G[m] = sgn^j e^{-i k phi0} X_k (X^N or X^S)
   T2 *GN = G + rp.ringN * stride;
   T2 *GS = south ? G + rp.ringS * stride : nullptr;
   const T half = (T)0.5;
-  for (int m = threadIdx.x; m <= Lg; m += blockDim.x) {
-    const int k = m % n;
-    const int kk = (n - k) % n;
+  const int kmax = min(n - 1, Lg);
+  for (int k = threadIdx.x; k <= kmax; k += blockDim.x) {
+    const int kk = k == 0 ? 0 : n - k;
     const T2 X = buf[k], Xc = cconj(buf[kk]);
-    const T2 ph = cconj(phase<T2>(m, rp.phi_num, rp.phi_den));
-    const T2 tN = CT<T2>::mk(half * (X.x + Xc.x), half * (X.y + Xc.y));
-    GN[m] = cmul(tN, ph);
-    if (south) {
-      // (X - Xc) / (2i)
-      const T2 dlt = csub(X, Xc);
-      const T2 tS = CT<T2>::mk(half * dlt.y, -half * dlt.x);
-      GS[m] = cmul(tS, ph);
+    const T2 ph = cconj(ring_phase<T2>(k, rp.phi_num, rp.phi_den, tstep, tw));
+    const T2 tN = cmul(CT<T2>::mk(half * (X.x + Xc.x), half * (X.y + Xc.y)), ph);
+    // (X - Xc) / (2i)
+    const T2 dlt = csub(X, Xc);
+    const T2 tS = cmul(CT<T2>::mk(half * dlt.y, -half * dlt.x), ph);
+    T s = (T)1;
+    for (int m = k; m <= Lg; m += n) {
+      GN[m] = CT<T2>::mk(s * tN.x, s * tN.y);
+      if (south) GS[m] = CT<T2>::mk(s * tS.x, s * tS.y);
+      s *= sgn;
     }
   }
 }

@@ -406,7 +406,9 @@ static wf_status enqueue_iteration(Plan &P, T2 *F, T2 *G, const double *data,
   if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[2 * C + slot], P.stream, cudaEventRecordExternal));
   WF_TRY(launch_legendre_synth<T2>(P, xs, F, P.state, P.lmax));
   if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[3 * C + slot], P.stream, cudaEventRecordExternal));
+  if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[4 * C + slot], P.stream, cudaEventRecordExternal));
   WF_TRY(launch_ring<T2>(P, RING_FUSED, F, G, data, nullptr, P.state, P.lmax));
+  if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[5 * C + slot], P.stream, cudaEventRecordExternal));
   ++P.nlaunch;
   k_control<<<1, CTRL_THREADS, 0, P.stream>>>(P.state, P.partials, P.lmax, P.cl_d,
                                               P.trace);
@@ -431,7 +433,7 @@ static wf_status capture_graph(Plan &P, int which, T2 *F, T2 *G, const double *d
     WF_CUDA(cudaStreamCreateWithFlags(&P.capture_stream, cudaStreamNonBlocking));
   if (P.opts.timing && P.tev_chunk < chunk) {
     for (cudaEvent_t e : P.tev) cudaEventDestroy(e);
-    P.tev.assign(4 * chunk, nullptr);
+    P.tev.assign(6 * chunk, nullptr);
     for (auto &e : P.tev) WF_CUDA(cudaEventCreate(&e));
     P.tev_chunk = chunk;
   }
@@ -500,14 +502,13 @@ static wf_status run_loop(Plan &P, int which, T2 *F, T2 *G, const double *tinit,
       const int active = std::min(P.state_h->iter - it0, P.graph_chunk[which]);
       const int C = P.tev_chunk;
       for (int i = 0; i < active; ++i) {
-        float a = 0.f, b = 0.f;
-        WF_CUDA(cudaEventElapsedTime(&a, P.tev[0 * C + i], P.tev[1 * C + i]));
-        WF_CUDA(cudaEventElapsedTime(&b, P.tev[2 * C + i], P.tev[3 * C + i]));
-        P.kern_ms[0] += a;
-        P.kern_ms[1] += b;
+        for (int k = 0; k < 3; ++k) {
+          float t = 0.f;
+          WF_CUDA(cudaEventElapsedTime(&t, P.tev[2 * k * C + i], P.tev[(2 * k + 1) * C + i]));
+          P.kern_ms[k] += t;
+        }
       }
-      P.kern_launches[0] += active;
-      P.kern_launches[1] += active;
+      for (int k = 0; k < 3; ++k) P.kern_launches[k] += active;
       it0 = P.state_h->iter;
     }
     if (P.state_h->done) break;
@@ -599,12 +600,16 @@ static wf_status account_work(Plan &P, int i0, int i1) {
   std::vector<TraceEntry> h(i1 - i0);
   WF_CUDA(cudaMemcpy(h.data(), P.trace + i0, sizeof(TraceEntry) * h.size(),
                      cudaMemcpyDeviceToHost));
+  // ring step: F read and G written for m <= lcur on every ring (T2 each),
+  // d and sigma^2 read once per pixel (FP64)
+  const double t2 = P.opts.precision == WF_PREC_FP64 ? 16.0 : 8.0;
   for (const TraceEntry &e : h) {
     if (e.lcur < 0) continue;
     double t = 0.0;
     WF_TRY(legendre_terms(P, e.lcur, &t));
     P.kern_flop[0] += 7.0 * t;
     P.kern_flop[1] += 7.0 * t;
+    P.kern_flop[2] += 2.0 * t2 * P.nring * (e.lcur + 1.0) + 16.0 * P.npix;
   }
   return WF_OK;
 }

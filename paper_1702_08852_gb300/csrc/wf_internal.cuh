@@ -163,11 +163,13 @@ struct Plan {
   // optional per-kernel timing inside the captured graphs (opts.timing):
   // events around the Legendre analysis (k = 0) and synthesis (k = 1) of
   // every iteration of a chunk; accumulated over active iterations only
-  std::vector<cudaEvent_t> tev;     // [2 kernels][2 (start, stop)][chunk]
+  // timed kernels: 0 analysis, 1 synthesis, 2 ring step (both launches)
+  std::vector<cudaEvent_t> tev;     // [3 kernels][2 (start, stop)][chunk]
   int tev_chunk = 0;
-  double kern_ms[2] = {0.0, 0.0};
-  long kern_launches[2] = {0, 0};
-  double kern_flop[2] = {0.0, 0.0};  // algorithmic flops of the timed launches
+  double kern_ms[3] = {0.0, 0.0, 0.0};
+  long kern_launches[3] = {0, 0, 0};
+  // algorithmic work of the timed launches: flops (0, 1), DRAM bytes (2)
+  double kern_flop[3] = {0.0, 0.0, 0.0};
   std::vector<double> work_cache;    // reduced (l, m, ring-pair) count per band
   std::vector<int> seed_l_h;         // host copy of seed_l
 };

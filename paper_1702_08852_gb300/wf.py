@@ -307,7 +307,8 @@ class Plan:
         ms, n, gf = ctypes.c_double(), ctypes.c_long(), ctypes.c_double()
         _check(lib().wf_kernel_stats(self.handle, int(kernel), ctypes.byref(ms),
                                      ctypes.byref(n), ctypes.byref(gf), int(reset)))
-        return {"ms": ms.value, "launches": n.value, "gflop": gf.value}
+        key = "gbytes" if int(kernel) == 2 else "gflop"
+        return {"ms": ms.value, "launches": n.value, key: gf.value}
 
     def legendre_terms(self, L=None):
         t = ctypes.c_double()
