@@ -31,11 +31,15 @@ static void free_plan(wf_plan_s *P) {
                   P->seed_u, P->tw64,  P->tw32,    P->chirp64, P->chirp32, P->bhat64,
                   P->bhat32, P->nvar,  P->F64,     P->G64,    P->F32,    P->G32,
                   P->x,      P->xtmp,  P->dmap,    P->mtmp,   P->partials, P->red,
-                  P->state,  P->trace, P->xacc,  P->src, P->xs64, P->xs32};
+                  P->state,  P->trace, P->xacc,  P->src, P->xs64, P->xs32,
+                  P->nvar32, P->dmap32};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (P->state_h) cudaFreeHost(P->state_h);
   if (P->capture_stream) cudaStreamDestroy(P->capture_stream);
+  if (P->side_stream) cudaStreamDestroy(P->side_stream);
+  if (P->fork_ev) cudaEventDestroy(P->fork_ev);
+  if (P->join_ev) cudaEventDestroy(P->join_ev);
   for (cudaEvent_t e : P->tev) cudaEventDestroy(e);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
@@ -43,6 +47,9 @@ static void free_plan(wf_plan_s *P) {
 }
 
 static wf_status alloc_work(Plan &P) {
+  WF_CUDA(cudaStreamCreateWithFlags(&P.side_stream, cudaStreamNonBlocking));
+  WF_CUDA(cudaEventCreateWithFlags(&P.fork_ev, cudaEventDisableTiming));
+  WF_CUDA(cudaEventCreateWithFlags(&P.join_ev, cudaEventDisableTiming));
   const size_t nF = (size_t)P.nring * (P.lmax + 1);
   WF_CUDA(cudaMalloc(&P.F64, sizeof(double2) * nF));
   WF_CUDA(cudaMalloc(&P.G64, sizeof(double2) * nF));
@@ -55,6 +62,7 @@ static wf_status alloc_work(Plan &P) {
   WF_CUDA(cudaMalloc(&P.xs32, sizeof(float2) * P.nalm));
   WF_CUDA(cudaMalloc(&P.src, sizeof(double2) * P.nalm));
   WF_CUDA(cudaMalloc(&P.dmap, sizeof(double) * P.npix));
+  WF_CUDA(cudaMalloc(&P.dmap32, sizeof(float) * P.npix));
   WF_CUDA(cudaMalloc(&P.mtmp, sizeof(double) * P.npix));
   WF_CUDA(cudaMalloc(&P.partials, sizeof(double) * 2 * (P.lmax + 1)));
   WF_CUDA(cudaMalloc(&P.red, sizeof(double) * 1024));

@@ -283,7 +283,8 @@ __device__ __forceinline__ void anal_chunk(T (&v)[32], int lc, int L, int m,
 #pragma unroll
   for (int jj = 0; jj < LCHUNK; ++jj) {
     const int l = lc + jj;
-    T a_re = (T)0, a_im = (T)0;
+    // two partial sums (even, odd j) halve the dependent FMA chain
+    T a_re = (T)0, a_im = (T)0, b_re = (T)0, b_im = (T)0;
     if (!TAIL || l <= L) {
       T c;
       if constexpr (VEC)
@@ -299,17 +300,19 @@ __device__ __forceinline__ void anal_chunk(T (&v)[32], int lc, int L, int m,
         }
         u2[j] = u1[j];
         u1[j] = u;
-        if ((jj & 1) == 0) {
-          a_re = fma(u, pr[j], a_re);
-          a_im = fma(u, pim[j], a_im);
+        const T pre = (jj & 1) == 0 ? pr[j] : qr[j];
+        const T pim_ = (jj & 1) == 0 ? pim[j] : qim[j];
+        if ((j & 1) == 0) {
+          a_re = fma(u, pre, a_re);
+          a_im = fma(u, pim_, a_im);
         } else {
-          a_re = fma(u, qr[j], a_re);
-          a_im = fma(u, qim[j], a_im);
+          b_re = fma(u, pre, b_re);
+          b_im = fma(u, pim_, b_im);
         }
       }
     }
-    v[2 * jj] = a_re;
-    v[2 * jj + 1] = a_im;
+    v[2 * jj] = a_re + b_re;
+    v[2 * jj + 1] = a_im + b_im;
   }
 }
 

@@ -387,6 +387,13 @@ __global__ void k_noise_copy(const double *nv, const uint8_t *mask, long npix,
   }
 }
 
+// sigma^2 / alpha in FP32 for the FP32 ring step (+inf stays +inf)
+__global__ void k_noise_f32(const double *nv, long npix, double inv_alpha, float *out) {
+  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+       p += (long)gridDim.x * blockDim.x)
+    out[p] = (float)(nv[p] * inv_alpha);
+}
+
 wf_status upload_noise(Plan &P, const double *nvar_dev, const uint8_t *mask_dev) {
   if (!P.nvar) WF_CUDA(cudaMalloc(&P.nvar, sizeof(double) * P.npix));
   const int nb = 304;
@@ -422,6 +429,9 @@ wf_status upload_noise(Plan &P, const double *nvar_dev, const uint8_t *mask_dev)
     return WF_ERR_ARG;
   }
   P.alpha = mn;
+  if (!P.nvar32) WF_CUDA(cudaMalloc(&P.nvar32, sizeof(float) * P.npix));
+  k_noise_f32<<<nb, 256, 0, P.stream>>>(P.nvar, P.npix, 1.0 / mn, P.nvar32);
+  WF_CUDA(cudaGetLastError());
   P.has_noise = true;
   return WF_OK;
 }

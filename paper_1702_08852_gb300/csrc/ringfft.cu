@@ -77,20 +77,55 @@ __device__ __forceinline__ T2 rot_q(T2 a) {
   return INV ? CT<T2>::mk(-a.y, a.x) : CT<T2>::mk(a.y, -a.x);
 }
 
+// Twiddles of one pass: pair(j) gives W_2h^j = e^{-i pi j / h} and
+// W_h^j = (W_2h^j)^2 (h a power of two, 0 <= j < h).  FP32 computes them:
+// sincospi of the exact argument j / h (1/h is exact) and one complex square
+// -- no memory access on the FFT's critical path.  FP64 reads the plan's
+// table tw[i] = e^{-2 pi i i / Mmax} (FP64 sincospi would cost more than the
+// butterfly on this part's FP64 pipe).
+template <typename T2> struct TwPass;
+template <> struct TwPass<float2> {
+  float inv;
+  __device__ __forceinline__ TwPass(int h, const float2 *, int) : inv(1.0f / (float)h) {}
+  __device__ __forceinline__ void pair(int j, float2 &w2h, float2 &wh) const {
+    float s, c;
+    sincospif((float)j * inv, &s, &c);
+    w2h = make_float2(c, -s);
+    wh = make_float2(c * c - s * s, -2.0f * c * s);
+  }
+};
+template <> struct TwPass<double2> {
+  const double2 *tw;
+  int ts;
+  __device__ __forceinline__ TwPass(int h, const double2 *t, int Mmax)
+      : tw(t), ts(Mmax / (2 * h)) {}
+  __device__ __forceinline__ void pair(int j, double2 &w2h, double2 &wh) const {
+    w2h = tw[j * ts];
+    wh = tw[2 * j * ts];
+  }
+};
+
 // natural -> bit-reversed; INV uses e^{+2 pi i jk/M}.  Two radix-2 stages
 // (spans h and h/2) per pass over shared memory ("radix-2^2"): the output
 // order stays bit-reversed, and the barriers and shared-memory round trips
 // halve.  An odd number of stages ends with one radix-2 pass of span 1.
+// Where the twiddle index j = b mod q is the same for all of a thread's
+// butterflies (q <= blockDim), the twiddles are computed once per pass.
 template <typename T2, bool INV>
 __device__ void fft_dif(T2 *buf, int M, const T2 *__restrict__ tw, int Mmax) {
   int h = M >> 1;
   for (; h >= 2; h >>= 2) {
     const int q = h >> 1;
-    const int ts = Mmax / (2 * h);
+    const TwPass<T2> tp(h, tw, Mmax);
+    const bool fixed = q <= (int)blockDim.x;
+    T2 w1f, w2f;
+    if (fixed) tp.pair((int)threadIdx.x & (q - 1), w1f, w2f);
+    #pragma unroll 4
     for (int b = threadIdx.x; b < (M >> 2); b += blockDim.x) {
       const int j = b & (q - 1);
       const int i0 = ((b - j) << 2) + j, i1 = i0 + q, i2 = i0 + h, i3 = i2 + q;
-      const T2 w1 = tw[j * ts], w2 = tw[2 * j * ts];  // W_2h^j, W_h^j
+      T2 w1 = w1f, w2 = w2f;  // W_2h^j, W_h^j
+      if (!fixed) tp.pair(j, w1, w2);
       const T2 x0 = buf[i0], x1 = buf[i1], x2 = buf[i2], x3 = buf[i3];
       const T2 a0 = cadd(x0, x2), a1 = cadd(x1, x3);
       const T2 a2 = INV ? cmulc(csub(x0, x2), w1) : cmul(csub(x0, x2), w1);
@@ -129,11 +164,16 @@ __device__ void fft_dit(T2 *buf, int M, const T2 *__restrict__ tw, int Mmax) {
     h = 2;
   }
   for (; h < M; h <<= 2) {
-    const int ta = Mmax / (2 * h), tb = Mmax / (4 * h);
+    const TwPass<T2> tp(2 * h, tw, Mmax);  // pair(j) = (W_4h^j, W_2h^j)
+    const bool fixed = h <= (int)blockDim.x;
+    T2 waf, wbf;
+    if (fixed) tp.pair((int)threadIdx.x & (h - 1), wbf, waf);
+    #pragma unroll 4
     for (int b = threadIdx.x; b < (M >> 2); b += blockDim.x) {
       const int j = b & (h - 1);
       const int i0 = ((b - j) << 2) + j, i1 = i0 + h, i2 = i0 + 2 * h, i3 = i2 + h;
-      const T2 wa = tw[j * ta], wb = tw[j * tb];  // W_2h^j, W_4h^j
+      T2 wa = waf, wb = wbf;  // W_2h^j, W_4h^j
+      if (!fixed) tp.pair(j, wb, wa);
       const T2 x0 = buf[i0], x1 = buf[i1], x2 = buf[i2], x3 = buf[i3];
       const T2 c1 = INV ? cmulc(x1, wa) : cmul(x1, wa);
       const T2 c3 = INV ? cmulc(x3, wa) : cmul(x3, wa);
@@ -157,9 +197,11 @@ __device__ void bluestein(T2 *buf, int n, int M, const T2 *__restrict__ tw,
                           int Mmax, const T2 *__restrict__ chirp,
                           const T2 *__restrict__ bhat) {
   fft_dif<T2, false>(buf, M, tw, Mmax);
+  #pragma unroll 4
   for (int q = threadIdx.x; q < M; q += blockDim.x) buf[q] = cmul(buf[q], bhat[q]);
   __syncthreads();
   fft_dit<T2, true>(buf, M, tw, Mmax);
+  #pragma unroll 4
   for (int k = threadIdx.x; k < n; k += blockDim.x) buf[k] = cmulc(buf[k], chirp[k]);
   __syncthreads();
 }
@@ -190,18 +232,29 @@ __device__ __forceinline__ T2 ring_phase(int k, int num, int den, int tstep,
 
 // c_k = sum over m = +-k mod n, |m| <= L, of F[m] e^{i m phi0}
 //     = e^{i k phi0} (sum_j sgn^j F[k + j n] + sum_{j >= 1} sgn^j conj F[j n - k])
+// When n > L each sum has at most one term (every equatorial ring, the outer
+// polar rings): the two loads are issued together, not in dependent loops.
 template <typename T2>
 __device__ __forceinline__ T2 fold(const T2 *__restrict__ Fr, int k, int n, int L,
                                    typename CT<T2>::T sgn, T2 ph) {
   typedef typename CT<T2>::T T;
   T2 acc = CT<T2>::mk((T)0, (T)0);
+  if (n > L) {
+    const T2 zero = CT<T2>::mk((T)0, (T)0);
+    const T2 a = k <= L ? Fr[k] : zero;
+    const T2 b = n - k <= L ? Fr[n - k] : zero;
+    acc = CT<T2>::mk(a.x + sgn * b.x, a.y - sgn * b.y);
+    return cmul(acc, ph);
+  }
   T s = (T)1;
+#pragma unroll 4
   for (int m = k; m <= L; m += n) {
     const T2 f = Fr[m];
     acc = CT<T2>::mk(acc.x + s * f.x, acc.y + s * f.y);
     s *= sgn;
   }
   s = sgn;
+#pragma unroll 4
   for (int m = n - k; m <= L; m += n) {  // m >= 1 since k < n
     const T2 f = Fr[m];
     acc = CT<T2>::mk(acc.x + s * f.x, acc.y - s * f.y);
@@ -210,27 +263,40 @@ __device__ __forceinline__ T2 fold(const T2 *__restrict__ Fr, int k, int n, int 
   return cmul(acc, ph);
 }
 
+// threads per ring pair: 512 for launches whose largest FFT has 8192 or more
+// points (the polar Bluestein rings at Nside >= 1024: more warps to hide the
+// latency of the table and twiddle loads at 3 CTAs per SM), else 256
 constexpr int RING_THREADS = 256;
+constexpr int RING_THREADS_BIG = 512;
 
 template <typename T2, int MODE>
-__global__ void __launch_bounds__(RING_THREADS)
+__global__ void __launch_bounds__(RING_THREADS_BIG)
     k_ring(const RingPair *__restrict__ pairs, int pair_base, int lmax,
            const T2 *__restrict__ F, T2 *__restrict__ G,
            const double *__restrict__ in_map, double *__restrict__ out_map,
            const double *__restrict__ nvar, const T2 *__restrict__ tw, int Mmax,
            const T2 *__restrict__ chirp_all, const T2 *__restrict__ bhat_all,
-           const SolverState *__restrict__ st, int lstatic) {
+           const SolverState *__restrict__ st, int lstatic, int reverse,
+           const float *__restrict__ in32, const float *__restrict__ nv32) {
   typedef typename CT<T2>::T T;
-  const RingPair rp = pairs[pair_base + blockIdx.x];
+  // reverse: the polar rings grow with the pair index; taking the largest
+  // first keeps the small ones for the tail of the launch
+  const int blk = reverse ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+  const RingPair rp = pairs[pair_base + blk];
   int Lf = lstatic, Lg = lstatic;
-  double xi = 0.0, mu = 0.0;
+  double xi = 0.0, mu = 0.0, alpha = 1.0;
   if (st) {
     if (st->done) return;
     Lf = st->lcur;
     Lg = max(st->lcur, st->lnext);
     xi = st->xi;
     mu = st->mu;
+    alpha = st->alpha;
   }
+  // FP32 step: w = (xi / alpha) / (sigma^2 / alpha + mu / alpha) -- the same
+  // weight with every operand scaled to O(1) for the FP32 range
+  constexpr bool F32STEP = MODE == RING_FUSED && sizeof(T) == 4;
+  const float xia = (float)(xi / alpha), mua = (float)(mu / alpha);
   extern __shared__ __align__(16) unsigned char smraw[];
   T2 *buf = reinterpret_cast<T2 *>(smraw);
   const int n = rp.nphi, M = rp.fftM;
@@ -248,6 +314,7 @@ __global__ void __launch_bounds__(RING_THREADS)
   if (MODE != RING_ANALYSIS) {
     const T2 *FN = F + rp.ringN * stride;
     const T2 *FS = south ? F + rp.ringS * stride : nullptr;
+    #pragma unroll 4
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       T2 cN = zero, cS = zero;
       if (Lf >= 0 && (k <= Lf || n - k <= Lf)) {
@@ -267,6 +334,7 @@ __global__ void __launch_bounds__(RING_THREADS)
       fft_dif<T2, true>(buf, M, tw, Mmax);  // bit-reversed output
     }
     // pixel step; position q holds pixel j
+    #pragma unroll 4
     for (int q = threadIdx.x; q < n; q += blockDim.x) {
       const int j = blue ? q : bitrev_n(q, bits);
       T2 zz = buf[q];
@@ -281,18 +349,28 @@ __global__ void __launch_bounds__(RING_THREADS)
           out_map[pN] = sN;
           if (south) out_map[pS] = sS;
         }
-        double tN = sN, tS = 0.0;
-        {
-          const double v = nvar[pN];
-          const double w = xi / (v + mu);  // 0 on masked pixels (v = +inf)
-          tN = sN + w * ((in_map ? in_map[pN] : 0.0) - sN);
+        T2 tt;
+        if constexpr (F32STEP) {
+          // 0 on masked pixels (sigma^2 / alpha = +inf)
+          const float sNf = zz.x, sSf = zz.y;
+          float tN = sNf + xia / (nv32[pN] + mua) * ((in32 ? in32[pN] : 0.f) - sNf);
+          float tS = 0.f;
+          if (south) tS = sSf + xia / (nv32[pS] + mua) * ((in32 ? in32[pS] : 0.f) - sSf);
+          tt = CT<T2>::mk((T)tN, (T)tS);
+        } else {
+          double tN = sN, tS = 0.0;
+          {
+            const double v = nvar[pN];
+            const double w = xi / (v + mu);  // 0 on masked pixels (v = +inf)
+            tN = sN + w * ((in_map ? in_map[pN] : 0.0) - sN);
+          }
+          if (south) {
+            const double v = nvar[pS];
+            const double w = xi / (v + mu);
+            tS = sS + w * ((in_map ? in_map[pS] : 0.0) - sS);
+          }
+          tt = CT<T2>::mk((T)tN, (T)tS);
         }
-        if (south) {
-          const double v = nvar[pS];
-          const double w = xi / (v + mu);
-          tS = sS + w * ((in_map ? in_map[pS] : 0.0) - sS);
-        }
-        const T2 tt = CT<T2>::mk((T)tN, (T)tS);
         buf[q] = blue ? cmulc(tt, chirp[q]) : tt;
       }
     }
@@ -301,6 +379,7 @@ __global__ void __launch_bounds__(RING_THREADS)
       for (int k = n + threadIdx.x; k < M; k += blockDim.x) buf[k] = zero;
     __syncthreads();
   } else {
+    #pragma unroll 4
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       const double tN = in_map[rp.ofsN + j];
       const double tS = south ? in_map[rp.ofsS + j] : 0.0;
@@ -325,6 +404,7 @@ __global__ void __launch_bounds__(RING_THREADS)
   T2 *GS = south ? G + rp.ringS * stride : nullptr;
   const T half = (T)0.5;
   const int kmax = min(n - 1, Lg);
+  #pragma unroll 4
   for (int k = threadIdx.x; k <= kmax; k += blockDim.x) {
     const int kk = k == 0 ? 0 : n - k;
     const T2 X = buf[k], Xc = cconj(buf[kk]);
@@ -357,23 +437,36 @@ template <> struct Tables<float2> {
 template <typename T2, int MODE>
 static wf_status launch_ring_mode(const Plan &P, const T2 *F, T2 *G,
                                   const double *in_map, double *out_map,
-                                  const SolverState *st, int lstatic) {
+                                  const SolverState *st, int lstatic, const float *in32) {
   auto kern = k_ring<T2, MODE>;
   // two launches: the polar rings (pairs 0 .. nside-2, Bluestein unless n is
-  // a power of two) and the equatorial belt (pairs nside-1 .. 2 nside-1)
+  // a power of two) and the equatorial belt (pairs nside-1 .. 2 nside-1);
+  // they touch disjoint rings and run concurrently on two streams
   const int npolar = P.nside - 1;
   const int groups[2][2] = {{0, npolar}, {npolar, P.npairs}};
+  const bool fork = npolar > 0 && P.side_stream;
+  if (fork) {
+    WF_CUDA(cudaEventRecord(P.fork_ev, P.stream));
+    WF_CUDA(cudaStreamWaitEvent(P.side_stream, P.fork_ev, 0));
+  }
   for (int g = 0; g < 2; ++g) {
     const int b = groups[g][0], e = groups[g][1];
     if (e <= b) continue;
     int Mg = 1;
     for (int k = b; k < e; ++k) Mg = std::max(Mg, P.pairs_h[k].fftM);
     const size_t smem = sizeof(T2) * Mg;
+    const int threads = Mg >= 8192 ? RING_THREADS_BIG : RING_THREADS;
+    cudaStream_t s = (fork && g == 1) ? P.side_stream : P.stream;
     ++P.nlaunch;
-    kern<<<e - b, RING_THREADS, smem, P.stream>>>(
+    kern<<<e - b, threads, smem, s>>>(
         P.pairs, b, P.lmax, F, G, in_map, out_map, P.nvar, Tables<T2>::tw(P),
-        P.fftMmax, Tables<T2>::ch(P), Tables<T2>::bh(P), st, lstatic);
+        P.fftMmax, Tables<T2>::ch(P), Tables<T2>::bh(P), st, lstatic, g == 0, in32,
+        P.nvar32);
     WF_CUDA(cudaGetLastError());
+  }
+  if (fork) {
+    WF_CUDA(cudaEventRecord(P.join_ev, P.side_stream));
+    WF_CUDA(cudaStreamWaitEvent(P.stream, P.join_ev, 0));
   }
   return WF_OK;
 }
@@ -381,15 +474,19 @@ static wf_status launch_ring_mode(const Plan &P, const T2 *F, T2 *G,
 template <typename T2>
 wf_status launch_ring(const Plan &P, int mode, const T2 *F, T2 *G,
                       const double *in_map, double *out_map,
-                      const SolverState *st, int lstatic) {
+                      const SolverState *st, int lstatic, const float *in32) {
   switch (mode) {
     case RING_SYNTH:
-      return launch_ring_mode<T2, RING_SYNTH>(P, F, G, in_map, out_map, st, lstatic);
+      return launch_ring_mode<T2, RING_SYNTH>(P, F, G, in_map, out_map, st, lstatic, in32);
     case RING_ANALYSIS:
-      return launch_ring_mode<T2, RING_ANALYSIS>(P, F, G, in_map, out_map, st,
-                                                 lstatic);
+      return launch_ring_mode<T2, RING_ANALYSIS>(P, F, G, in_map, out_map, st, lstatic,
+                                                 in32);
     default:
-      return launch_ring_mode<T2, RING_FUSED>(P, F, G, in_map, out_map, st, lstatic);
+      if (sizeof(T2) == sizeof(float2) && !P.nvar32) {
+        set_error("ring step: the plan has no noise variance");
+        return WF_ERR_STATE;
+      }
+      return launch_ring_mode<T2, RING_FUSED>(P, F, G, in_map, out_map, st, lstatic, in32);
   }
 }
 
@@ -412,9 +509,9 @@ wf_status init_ring_attributes() {
 
 template wf_status launch_ring<double2>(const Plan &, int, const double2 *,
                                         double2 *, const double *, double *,
-                                        const SolverState *, int);
+                                        const SolverState *, int, const float *);
 template wf_status launch_ring<float2>(const Plan &, int, const float2 *, float2 *,
                                        const double *, double *,
-                                       const SolverState *, int);
+                                       const SolverState *, int, const float *);
 
 }  // namespace wf

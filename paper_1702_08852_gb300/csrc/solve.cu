@@ -31,6 +31,13 @@ __global__ void k_mask_data(const double *d, const double *nvar, long npix,
     out[p] = isinf(nvar[p]) ? 0.0 : d[p];
 }
 
+// the masked data in FP32 for the FP32 ring step
+__global__ void k_data_f32(const double *d, long npix, float *out) {
+  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+       p += (long)gridDim.x * blockDim.x)
+    out[p] = (float)d[p];
+}
+
 // largest l with C_l - mu Omega > 0 (the band where Sbar = Theta(S - U) is
 // nonzero), -1 if none; block-wide, result valid in thread 0
 __device__ int band_of(const double *cl, int lmax, double mu, double omega,
@@ -407,7 +414,9 @@ static wf_status enqueue_iteration(Plan &P, T2 *F, T2 *G, const double *data,
   WF_TRY(launch_legendre_synth<T2>(P, xs, F, P.state, P.lmax));
   if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[3 * C + slot], P.stream, cudaEventRecordExternal));
   if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[4 * C + slot], P.stream, cudaEventRecordExternal));
-  WF_TRY(launch_ring<T2>(P, RING_FUSED, F, G, data, nullptr, P.state, P.lmax));
+  // the FP32 loops run on the plan's masked data map, read from its FP32 copy
+  const float *d32 = (sizeof(T2) == sizeof(float2) && data) ? P.dmap32 : nullptr;
+  WF_TRY(launch_ring<T2>(P, RING_FUSED, F, G, data, nullptr, P.state, P.lmax, d32));
   if (timed) WF_CUDA(cudaEventRecordWithFlags(P.tev[5 * C + slot], P.stream, cudaEventRecordExternal));
   ++P.nlaunch;
   k_control<<<1, CTRL_THREADS, 0, P.stream>>>(P.state, P.partials, P.lmax, P.cl_d,
@@ -601,15 +610,19 @@ static wf_status account_work(Plan &P, int i0, int i1) {
   WF_CUDA(cudaMemcpy(h.data(), P.trace + i0, sizeof(TraceEntry) * h.size(),
                      cudaMemcpyDeviceToHost));
   // ring step: F read and G written for m <= lcur on every ring (T2 each),
-  // d and sigma^2 read once per pixel (FP64)
-  const double t2 = P.opts.precision == WF_PREC_FP64 ? 16.0 : 8.0;
-  for (const TraceEntry &e : h) {
+  // sigma^2 read once per pixel, and d in the iterations that read it
+  // (FP64: 8 bytes each; FP32 step: 4)
+  const bool f64 = P.opts.precision == WF_PREC_FP64;
+  const double t2 = f64 ? 16.0 : 8.0, pb = f64 ? 8.0 : 4.0;
+  for (int i = i0; i < i1; ++i) {
+    const TraceEntry &e = h[i - i0];
     if (e.lcur < 0) continue;
     double t = 0.0;
     WF_TRY(legendre_terms(P, e.lcur, &t));
     P.kern_flop[0] += 7.0 * t;
     P.kern_flop[1] += 7.0 * t;
-    P.kern_flop[2] += 2.0 * t2 * P.nring * (e.lcur + 1.0) + 16.0 * P.npix;
+    P.kern_flop[2] += 2.0 * t2 * P.nring * (e.lcur + 1.0) +
+                      (i < P.data_iters ? 2.0 : 1.0) * pb * P.npix;
   }
   return WF_OK;
 }
@@ -675,6 +688,9 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
     // and when progress stalls.
     bool converged = false;
     SolverState &h = *P.state_h;
+    ++P.nlaunch;
+    k_data_f32<<<304, 256, 0, P.stream>>>(P.dmap, P.npix, P.dmap32);
+    WF_CUDA(cudaGetLastError());
     h.noise_guard = 1;
     h.anchor_eps = ANCHOR_EPS;
     if (h.eps_k < ANCHOR_EPS) h.max_iter = 1;  // one plain step from t0 = d
@@ -686,6 +702,7 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       return WF_ERR_NUMERIC;
     }
     total_iter = h.iter;
+    P.data_iters = total_iter;
     bool anchored = h.at_boundary || h.max_iter == 1;
     if (h.max_iter == 1 && !h.at_boundary) {
       // the single plain step did not advance: stay in the initial stage
@@ -796,6 +813,7 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
                             cudaMemcpyHostToDevice, P.stream));
     WF_TRY(run_loop<double2>(P, 0, P.F64, P.G64, tinit, P.dmap, nullptr));
     total_iter = P.state_h->iter;
+    P.data_iters = total_iter;
     first_stages = P.state_h->stage + 1;
   }
   if (map) WF_TRY(alm2map(P, reinterpret_cast<const double *>(P.x), map));

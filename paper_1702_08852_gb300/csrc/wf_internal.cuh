@@ -97,6 +97,10 @@ struct Plan {
   double omega = 0.0;
   cudaStream_t stream = nullptr;
   cudaStream_t capture_stream = nullptr;  // graphs are captured here
+  // the ring step's two launches (polar, equatorial rings) run side by side:
+  // forked from `stream` onto side_stream and joined back with two events
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   wf_opts opts{};
   std::vector<double> cl;
   std::vector<RingPair> pairs_h;
@@ -129,6 +133,7 @@ struct Plan {
   bool has_noise = false;
   double alpha = 0.0;
   double *nvar = nullptr;        // [npix] sigma^2, +inf on masked pixels
+  float *nvar32 = nullptr;       // [npix] sigma^2 / alpha in FP32 (FP32 ring step)
 
   // work buffers
   double2 *F64 = nullptr, *G64 = nullptr;   // [nring][lmax+1]
@@ -140,6 +145,8 @@ struct Plan {
   float2 *xs32 = nullptr;        // [nalm] g_lm x_lm, synthesis input (FP32)
   double2 *src = nullptr;        // [nalm] harmonic source of a correction solve
   double *dmap = nullptr;        // [npix] data with masked pixels zeroed
+  float *dmap32 = nullptr;       // [npix] FP32 copy of dmap (FP32 ring step)
+  int data_iters = 0;            // iterations of the last solve that read d
   double *mtmp = nullptr;        // [npix]
   double *partials = nullptr;    // [lmax+1][2]
   double *red = nullptr;         // small reduction scratch
@@ -199,10 +206,14 @@ enum RingMode {
   RING_ANALYSIS = 1,  // map (masked pixels -> 0) -> G
   RING_FUSED = 2      // F -> s -> t = s + w (d - s) -> G  (in_map NULL: d = 0)
 };
+// The FP32 fused step (T2 = float2) reads d from in32 (FP32, NULL: d = 0)
+// and sigma^2 / alpha from the plan's nvar32, and updates t in FP32; the
+// FP64 one reads in_map and nvar.
 template <typename T2>
 wf_status launch_ring(const Plan &P, int mode, const T2 *F, T2 *G,
                       const double *in_map, double *out_map,
-                      const SolverState *st, int lstatic);
+                      const SolverState *st, int lstatic,
+                      const float *in32 = nullptr);
 
 // once per plan (kernel attributes; allowed outside stream capture only)
 wf_status init_legendre_attributes();

@@ -1,0 +1,92 @@
+"""FP32 spherical-harmonic transforms of the CUDA path (the transforms the
+mixed-precision solver iterates with), through the C ABI, against the
+oracle's FP64 direct sums, element by element.
+
+Tolerance (relative to the largest output value): u (64 + 2 nside sqrt(lmax+1)),
+u = 2^-24.  The second term bounds the phase drift of the FP32 Legendre
+recurrence: rounding c_l to FP32 perturbs the step's frequency by ~u / tan(theta),
+the errors of lmax steps add like a random walk (sqrt(lmax) u / tan(theta)),
+and the ring nearest the pole has tan(theta) ~ 0.8 / nside.  The first term
+covers the FP32 FFTs and sums on coarse grids."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -24
+
+
+def tol32(nside, lmax):
+    return U * (64.0 + 2.0 * nside * np.sqrt(lmax + 1.0))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1702_08852_gb300 import build
+    build.build()
+    return torch
+
+
+def rand_alm(lmax, seed):
+    from paper_1702_08852_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    n = inputs.nalm(lmax)
+    a = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    _, ms = inputs.lm_of_slots(lmax)
+    a[ms == 0] = a[ms == 0].real
+    return a
+
+
+# power-of-two and Bluestein rings, ragged band limits, several CTAs per m
+CASES = [(1, 2), (2, 5), (4, 8), (8, 16), (8, 7), (16, 32), (32, 64), (32, 95),
+         (64, 128), (160, 320)]
+
+
+@pytest.mark.parametrize("nside,lmax", CASES)
+def test_alm2map_f32_matches_oracle(torch_cuda, osht, nside, lmax):
+    torch = torch_cuda
+    from paper_1702_08852_gb300 import wf
+    a = rand_alm(lmax, 300 + nside + lmax)
+    ref = osht.alm2map(a, nside, lmax)
+    with wf.Plan(nside, lmax, np.ones(lmax + 1)) as p:
+        got = p.alm2map_f32(torch.from_numpy(a).cuda()).cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= tol32(nside, lmax) * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("nside,lmax", CASES)
+def test_map2alm_f32_matches_oracle(torch_cuda, osht, nside, lmax):
+    torch = torch_cuda
+    from paper_1702_08852_gb300 import wf
+    m = np.random.default_rng(nside * 11 + lmax).standard_normal(12 * nside * nside)
+    ref = osht.map2alm(m, nside, lmax)
+    with wf.Plan(nside, lmax, np.ones(lmax + 1)) as p:
+        got = p.map2alm_f32(torch.from_numpy(m).cuda()).cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= tol32(nside, lmax) * np.max(np.abs(ref))
+
+
+def test_f32_full_size_sampled(torch_cuda, osht):
+    """Nside 1024, lmax 2048: sampled pixels (the polar rings included) and
+    sampled coefficients, each computed one by one by the oracle."""
+    torch = torch_cuda
+    from paper_1702_08852_gb300 import wf, inputs
+    nside, lmax = 1024, 2048
+    npix = 12 * nside * nside
+    cl = inputs.cl_spectrum(lmax, nside)
+    rng = np.random.default_rng(91)
+    a = inputs.random_alm(rng, np.maximum(cl, 1e-12))
+    with wf.Plan(nside, lmax, cl) as p:
+        mp = p.alm2map_f32(torch.from_numpy(a).cuda()).cpu().numpy()
+        pix = np.concatenate([rng.integers(0, npix, 30),
+                              [0, 3, 4, 40, npix - 1, npix // 2, 2 * nside * (nside - 1)]])
+        ref = osht.alm2map_pixels(a, nside, lmax, pix)
+        assert np.max(np.abs(mp[pix] - ref)) <= tol32(nside, lmax) * np.max(np.abs(mp))
+        m = rng.standard_normal(npix)
+        b = p.map2alm_f32(torch.from_numpy(m).cuda()).cpu().numpy()
+    ls, ms = inputs.lm_of_slots(lmax)
+    sel = np.concatenate([rng.integers(0, len(ls), 10), [0, inputs.nalm(lmax) - 1, 2048]])
+    om = 4 * np.pi / npix
+    ref = om * osht.adjoint_modes(m, nside, lmax, ls[sel], ms[sel])
+    assert np.max(np.abs(b[sel] - ref)) <= tol32(nside, lmax) * np.max(np.abs(b))
