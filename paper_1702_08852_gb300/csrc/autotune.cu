@@ -15,7 +15,7 @@ namespace wf {
 
 namespace {
 struct Choice {
-  int syn[2], ana[2];
+  int syn[2], ana[2], ana_queue;
 };
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, Choice> g_tune_cache;
@@ -55,6 +55,7 @@ wf_status autotune(Plan &P) {
         P.syn_np[k] = it->second.syn[k];
         P.ana_np[k] = it->second.ana[k];
       }
+      P.ana_queue = it->second.ana_queue;
       return WF_OK;
     }
   }
@@ -85,19 +86,26 @@ wf_status autotune(Plan &P) {
     P.syn_np[k] = pick;
     best = 1e30f;
     pick = P.ana_np[k];
+    int pick_q = 0;
     const int *cand = k ? ana_cand32 : ana_cand64;
     const int nc = k ? 4 : 3;
-    for (int i = 0; i < nc && st == WF_OK; ++i) {
-      P.ana_np[k] = cand[i];
+    // FP32 also tries the queue-scheduled analysis with 4 and 8 pairs per lane
+    const int nq = k ? 2 : 0;
+    for (int i = 0; i < nc + nq && st == WF_OK; ++i) {
+      const bool q = i >= nc;
+      P.ana_queue = q ? 1 : 0;
+      P.ana_np[k] = q ? (i == nc ? 4 : 8) : cand[i];
       float ms = 0.f;
       st = k ? time_anal<float2>(P, P.G32, e0, e1, &ms)
              : time_anal<double2>(P, P.G64, e0, e1, &ms);
       if (st == WF_OK && ms < best) {
         best = ms;
-        pick = cand[i];
+        pick = P.ana_np[k];
+        pick_q = P.ana_queue;
       }
     }
     P.ana_np[k] = pick;
+    if (k) P.ana_queue = pick_q;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -108,6 +116,7 @@ wf_status autotune(Plan &P) {
     c.syn[k] = P.syn_np[k];
     c.ana[k] = P.ana_np[k];
   }
+  c.ana_queue = P.ana_queue;
   g_tune_cache[key] = c;
   return WF_OK;
 }

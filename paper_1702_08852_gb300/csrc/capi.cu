@@ -32,7 +32,8 @@ static void free_plan(wf_plan_s *P) {
                   P->bhat32, P->nvar,  P->F64,     P->G64,    P->F32,    P->G32,
                   P->x,      P->xtmp,  P->dmap,    P->mtmp,   P->partials, P->red,
                   P->state,  P->trace, P->xacc,  P->src, P->xs64, P->xs32,
-                  P->nvar32, P->dmap32};
+                  P->nvar32, P->dmap32, P->ana_scratch, P->ana_lstart,
+                  P->ana_counter};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (P->state_h) cudaFreeHost(P->state_h);
@@ -63,6 +64,18 @@ static wf_status alloc_work(Plan &P) {
   WF_CUDA(cudaMalloc(&P.src, sizeof(double2) * P.nalm));
   WF_CUDA(cudaMalloc(&P.dmap, sizeof(double) * P.npix));
   WF_CUDA(cudaMalloc(&P.dmap32, sizeof(float) * P.npix));
+  {
+    // queue-scheduled FP32 analysis: partial sums of tiles of 128 ring pairs
+    // (the smallest tile of its variants)
+    const long tiles = (P.npairs + 127) / 128;
+    int dev = 0;
+    WF_CUDA(cudaGetDevice(&dev));
+    WF_CUDA(cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, dev));
+    WF_CUDA(cudaMalloc(&P.ana_scratch, sizeof(float2) * tiles * P.nalm));
+    WF_CUDA(cudaMalloc(&P.ana_lstart, sizeof(int) * tiles * (P.lmax + 1)));
+    WF_CUDA(cudaMalloc(&P.ana_counter, sizeof(int)));
+    WF_CUDA(cudaMemsetAsync(P.ana_counter, 0, sizeof(int), P.stream));
+  }
   WF_CUDA(cudaMalloc(&P.mtmp, sizeof(double) * P.npix));
   WF_CUDA(cudaMalloc(&P.partials, sizeof(double) * 2 * (P.lmax + 1)));
   WF_CUDA(cudaMalloc(&P.red, sizeof(double) * 1024));

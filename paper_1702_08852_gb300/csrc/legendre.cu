@@ -24,6 +24,9 @@
 // (Eq. 15, App. B) and the partial sums of the Cauchy norms.
 #include <limits.h>
 
+#include <algorithm>
+#include <atomic>
+
 #include "wf_internal.cuh"
 
 namespace wf {
@@ -316,6 +319,85 @@ __device__ __forceinline__ void anal_chunk(T (&v)[32], int lc, int L, int m,
   }
 }
 
+// Epilogue of one coefficient (l, m), index i: a = Omega g_l (sr, si) (the
+// ring sums in u-units), then in ANA_FILTER mode the source term of an
+// anchored stage, the filter f_l = Sbar / (Sbar + xi Omega) and the Cauchy
+// partial sums (weight wm = 1 for m = 0, 2 else); writes x and xs_out.
+template <typename T>
+__device__ __forceinline__ void anal_finish(long i, int l, double sr, double si,
+                                            double wm, int mode,
+                                            const double *__restrict__ rg,
+                                            const double *__restrict__ cl, double omega,
+                                            double xi, double mu,
+                                            const double2 *__restrict__ src,
+                                            double2 *__restrict__ x,
+                                            typename Vec2<T>::type *__restrict__ xs_out,
+                                            double &num, double &den) {
+  const double s = omega * rg[i];
+  double ar = s * sr, ai = s * si;
+  if (mode == ANA_FILTER) {
+    const double sbar = fmax(cl[l] - mu * omega, 0.0);
+    const double f = sbar / (sbar + xi * omega);
+    if (src) {  // harmonic source term of a correction solve
+      ar += xi * omega * src[i].x;
+      ai += xi * omega * src[i].y;
+    }
+    ar *= f;
+    ai *= f;
+    const double2 old = x[i];
+    const double dr = ar - old.x, di = ai - old.y;
+    num += wm * (dr * dr + di * di);
+    den += wm * (ar * ar + ai * ai);
+  }
+  x[i] = make_double2(ar, ai);
+  if (xs_out) xs_out[i] = Vec2<T>::make((T)(rg[i] * ar), (T)(rg[i] * ai));
+}
+
+// coefficients of this m above the band (l > L) are zero
+template <typename T>
+__device__ __forceinline__ void anal_zero_above(int m, int L, int lmax, long base,
+                                                double wm, int mode,
+                                                double2 *__restrict__ x,
+                                                typename Vec2<T>::type *__restrict__ xs_out,
+                                                double &num) {
+  const int lz = max(m, L + 1);
+  for (int l = lz + (int)threadIdx.x; l <= lmax; l += ANA_THREADS) {
+    const long i = base + (l - m);
+    if (mode == ANA_FILTER) {
+      const double2 old = x[i];
+      num += wm * (old.x * old.x + old.y * old.y);
+    }
+    x[i] = make_double2(0.0, 0.0);
+    if (xs_out) xs_out[i] = Vec2<T>::make((T)0, (T)0);
+  }
+}
+
+// block sums of the Cauchy partials -> partials[2m], partials[2m + 1]
+// (fixed order: lanes by xor-butterfly, then warps in index order)
+__device__ __forceinline__ void anal_partials(double num, double den, int m,
+                                              double *__restrict__ partials) {
+  __shared__ double wsum[2][ANA_WARPS];
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+  }
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    wsum[0][warp] = num;
+    wsum[1][warp] = den;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < ANA_WARPS; ++w) {
+      a += wsum[0][w];
+      b += wsum[1][w];
+    }
+    partials[2 * m] = a;
+    partials[2 * m + 1] = b;
+  }
+}
+
 template <typename T, int NP>
 __global__ void __launch_bounds__(ANA_THREADS)
     k_legendre_anal(const RingPair *__restrict__ pairs, int npairs, int lmax,
@@ -341,7 +423,6 @@ __global__ void __launch_bounds__(ANA_THREADS)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long base = lm_index(lmax, m, m);
   const double wm = (m == 0) ? 1.0 : 2.0;
-  __shared__ double red_num[ANA_THREADS], red_den[ANA_THREADS];
   double num = 0.0, den = 0.0;
 
   if (m <= L) {
@@ -428,55 +509,154 @@ __global__ void __launch_bounds__(ANA_THREADS)
         sr += (double)acc[w * nl + j].x;
         si += (double)acc[w * nl + j].y;
       }
-      const long i = base + j;
-      const double s = omega * rg[i];
-      double ar = s * sr, ai = s * si;
-      if (mode == ANA_FILTER) {
-        const int l = m + j;
-        const double sbar = fmax(cl[l] - mu * omega, 0.0);
-        const double f = sbar / (sbar + xi * omega);
-        if (src) {  // harmonic source term of a correction solve
-          ar += xi * omega * src[i].x;
-          ai += xi * omega * src[i].y;
-        }
-        ar *= f;
-        ai *= f;
-        const double2 old = x[i];
-        const double dr = ar - old.x, di = ai - old.y;
-        num += wm * (dr * dr + di * di);
-        den += wm * (ar * ar + ai * ai);
+      anal_finish<T>(base + j, m + j, sr, si, wm, mode, rg, cl, omega, xi, mu, src, x,
+                     xs_out, num, den);
+    }
+  }
+  anal_zero_above<T>(m, L, lmax, base, wm, mode, x, xs_out, num);
+  if (mode == ANA_FILTER) anal_partials(num, den, m, partials);
+}
+
+// ------------------------------------------------- analysis, queue-scheduled
+// The same contraction with the work split into items (m, tile of 32 NP ring
+// pairs), ordered heaviest first (m ascending).  Each warp takes items from
+// a device counter until none is left, so no warp waits for another (the
+// per-m CTA above waits at its barriers for its slowest warp, and a CTA per m
+// leaves the triangle's small-m rows to the end).  An item writes its
+// per-chunk warp sums for l in [lstart, L] to scratch[tile][i] (FP32
+// complex) and lstart to ana_lstart; k_anal_combine then adds the tiles of
+// each (l, m) in tile order (deterministic) and runs the epilogue.
+constexpr int ANA_Q_CTAS_PER_SM = 8;  // upper bound; the occupancy decides
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(ANA_THREADS)
+    k_legendre_anal_q(const RingPair *__restrict__ pairs, int npairs, int lmax, long nalm,
+                      const double *__restrict__ rc, const float *__restrict__ rc32,
+                      const int *__restrict__ seed_l, const double2 *__restrict__ seed_u,
+                      const typename Vec2<T>::type *__restrict__ G, T *__restrict__ scratch,
+                      int *__restrict__ lstart, int *__restrict__ counter,
+                      const SolverState *__restrict__ st, int lstatic) {
+  int L = lstatic;
+  if (st) {
+    if (st->done) return;
+    L = st->lcur;
+  }
+  if (L < 0) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int sc_stride = (lmax + 4) & ~3;  // 16-byte aligned rows
+  T *sc = reinterpret_cast<T *>(smraw) + (long)warp * sc_stride;
+  constexpr int TP = 32 * NP;
+  const int ntiles = (npairs + TP - 1) / TP;
+  const int nitems = (L + 1) * ntiles;
+  const long stride = lmax + 1;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(counter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= nitems) break;
+    const int m = item / ntiles, tile = item - m * ntiles;
+    const long base = lm_index(lmax, m, m);
+    const int pair0 = tile * TP;
+    T zh[NP], zl[NP], u1[NP], u2[NP], s0[NP], s1[NP];
+    T pr[NP], pim[NP], qr[NP], qim[NP];
+    int ls[NP];
+    int lmin = INT_MAX, linj = -1;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const int k = pair0 + lane + 32 * j;
+      u1[j] = u2[j] = (T)0;
+      if (k < npairs) {
+        const RingPair &rp = pairs[k];
+        split_z<T>(rp.z, zh[j], zl[j]);
+        ls[j] = seed_l[(long)m * npairs + k];
+        const double2 su = seed_u[(long)m * npairs + k];
+        s0[j] = (T)su.x;
+        s1[j] = (T)su.y;
+        const typename Vec2<T>::type gn = G[rp.ringN * stride + m];
+        typename Vec2<T>::type gs = Vec2<T>::make((T)0, (T)0);
+        if (rp.ringS >= 0) gs = G[rp.ringS * stride + m];
+        pr[j] = gn.x + gs.x;
+        pim[j] = gn.y + gs.y;
+        qr[j] = gn.x - gs.x;
+        qim[j] = gn.y - gs.y;
+      } else {
+        zh[j] = zl[j] = s0[j] = s1[j] = pr[j] = pim[j] = qr[j] = qim[j] = (T)0;
+        ls[j] = INT_MAX - 2;
       }
-      x[i] = make_double2(ar, ai);
-      if (xs_out) xs_out[i] = Vec2<T>::make((T)(rg[i] * ar), (T)(rg[i] * ai));
-    }
-  }
-  // coefficients of this m above the band are zero
-  const int lz = max(m, L + 1);
-  for (int l = lz + tid; l <= lmax; l += ANA_THREADS) {
-    const long i = base + (l - m);
-    if (mode == ANA_FILTER) {
-      const double2 old = x[i];
-      num += wm * (old.x * old.x + old.y * old.y);
-    }
-    x[i] = make_double2(0.0, 0.0);
-    if (xs_out) xs_out[i] = Vec2<T>::make((T)0, (T)0);
-  }
-  if (mode == ANA_FILTER) {
-    red_num[tid] = num;
-    red_den[tid] = den;
-    __syncthreads();
-    for (int s = ANA_THREADS / 2; s > 0; s >>= 1) {
-      if (tid < s) {
-        red_num[tid] += red_num[tid + s];
-        red_den[tid] += red_den[tid + s];
+      if (ls[j] <= L) {
+        lmin = min(lmin, ls[j]);
+        linj = max(linj, ls[j] + 1);
       }
-      __syncthreads();
     }
-    if (tid == 0) {
-      partials[2 * m] = red_num[0];
-      partials[2 * m + 1] = red_den[0];
+    lmin = warp_min(lmin);
+    linj = warp_max(linj);
+    const int lc0 = lmin <= L ? m + ((lmin - m) / LCHUNK) * LCHUNK : L + 1;
+    if (lane == 0) lstart[(long)m * ntiles + tile] = lc0;
+    if (lmin > L) continue;
+    __syncwarp();  // the previous item's reads of sc are done
+    for (int j = lane; j <= L - m; j += 32) sc[j] = coef<T>(rc, rc32, base + j);
+    __syncwarp();
+    T *out = scratch + 2 * ((long)tile * nalm + base - m);  // out[2 l + re/im]
+    for (int lc = lc0; lc <= L; lc += LCHUNK) {
+      T v[32];
+      if (lc + LCHUNK - 1 > L)
+        anal_chunk<T, NP, true, true>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls, pr,
+                                      pim, qr, qim);
+      else if (lc <= linj)
+        anal_chunk<T, NP, true, false>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls, pr,
+                                       pim, qr, qim);
+      else
+        anal_chunk<T, NP, false, false>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls, pr,
+                                        pim, qr, qim);
+      const T tot = transpose_reduce32<T>(v, lane);
+      const int l = lc + (lane >> 1);
+      if (l <= L) out[2 * l + (lane & 1)] = tot;
     }
   }
+}
+
+// Sum the tiles of every (l, m) of one m in tile order and finish as the
+// per-m kernel does.  Block 0 resets the queue counter for the next launch
+// (the analysis kernel has finished: same stream).
+template <typename T>
+__global__ void __launch_bounds__(ANA_THREADS)
+    k_anal_combine(int lmax, long nalm, int ntiles, const T *__restrict__ scratch,
+                   const int *__restrict__ lstart, int *__restrict__ counter,
+                   const double *__restrict__ rg, const double *__restrict__ cl,
+                   double omega, double2 *__restrict__ x, double *__restrict__ partials,
+                   const double2 *__restrict__ src,
+                   typename Vec2<T>::type *__restrict__ xs_out,
+                   const SolverState *__restrict__ st, int mode, int lstatic) {
+  const int m = blockIdx.x;
+  int L = lstatic;
+  double xi = 0.0, mu = 0.0;
+  if (st) {
+    if (st->done) return;
+    L = st->lcur;
+    xi = st->xi;
+    mu = st->mu;
+  }
+  if (m == 0 && threadIdx.x == 0) *counter = 0;
+  const long base = lm_index(lmax, m, m);
+  const double wm = (m == 0) ? 1.0 : 2.0;
+  double num = 0.0, den = 0.0;
+  if (m <= L) {
+    for (int j = threadIdx.x; j <= L - m; j += ANA_THREADS) {
+      const int l = m + j;
+      double sr = 0.0, si = 0.0;
+      for (int t = 0; t < ntiles; ++t) {
+        if (l < __ldg(lstart + (long)m * ntiles + t)) continue;
+        const T *p = scratch + 2 * ((long)t * nalm + base + j);
+        sr += (double)p[0];
+        si += (double)p[1];
+      }
+      anal_finish<T>(base + j, l, sr, si, wm, mode, rg, cl, omega, xi, mu, src, x, xs_out,
+                     num, den);
+    }
+  }
+  anal_zero_above<T>(m, L, lmax, base, wm, mode, x, xs_out, num);
+  if (mode == ANA_FILTER) anal_partials(num, den, m, partials);
 }
 
 // ------------------------------------------------------------------ launch
@@ -516,6 +696,38 @@ static void anal_variant(const Plan &P, const typename Vec2<T>::type *G, double2
       G, x, P.partials, src, xs_out, st, mode, lstatic);
 }
 
+// queue-scheduled FP32 analysis: persistent grid of ANA_Q_CTAS_PER_SM CTAs
+// per SM, then the per-m combine
+template <int NP>
+static wf_status anal_queue_variant(const Plan &P, const float2 *G, double2 *x,
+                                    const SolverState *st, int mode, int lstatic,
+                                    const double2 *src, float2 *xs_out) {
+  const int sc_stride = (P.lmax + 4) & ~3;
+  const size_t smem = sizeof(float) * sc_stride * ANA_WARPS;
+  const int ntiles = (P.npairs + 32 * NP - 1) / (32 * NP);
+  // one resident wave: CTAs per SM from the occupancy calculator (queried
+  // once; the first call comes from the autotuner, outside graph capture)
+  static std::atomic<int> per_sm_cache[2] = {0, 0};
+  int per_sm = per_sm_cache[NP == 8].load();
+  if (per_sm == 0) {
+    int n = 0;
+    WF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_legendre_anal_q<float, NP>,
+                                                          ANA_THREADS, smem));
+    per_sm = std::max(1, std::min(n, ANA_Q_CTAS_PER_SM));
+    per_sm_cache[NP == 8].store(per_sm);
+  }
+  k_legendre_anal_q<float, NP><<<P.num_sms * per_sm, ANA_THREADS, smem, P.stream>>>(
+      P.pairs, P.npairs, P.lmax, P.nalm, P.rc, P.rc32, P.seed_l, P.seed_u, G,
+      P.ana_scratch, P.ana_lstart, P.ana_counter, st, lstatic);
+  WF_CUDA(cudaGetLastError());
+  ++P.nlaunch;
+  k_anal_combine<float><<<P.lmax + 1, ANA_THREADS, 0, P.stream>>>(
+      P.lmax, P.nalm, ntiles, P.ana_scratch, P.ana_lstart, P.ana_counter, P.rg, P.cl_d,
+      P.omega, x, P.partials, src, xs_out, st, mode, lstatic);
+  WF_CUDA(cudaGetLastError());
+  return WF_OK;
+}
+
 // ring pairs per thread: the autotuner's choice for this plan and precision
 template <typename T2>
 wf_status launch_legendre_synth(const Plan &P, const T2 *xs, T2 *F,
@@ -539,6 +751,14 @@ wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
   typedef typename Kernels<T2>::T T;
   const int np = P.ana_np[sizeof(T) == 4];
   ++P.nlaunch;
+  if constexpr (sizeof(T) == 4) {
+    if (P.ana_queue) {
+      const float2 *g = reinterpret_cast<const float2 *>(G);
+      float2 *xo = reinterpret_cast<float2 *>(xs_out);
+      return np == 4 ? anal_queue_variant<4>(P, g, x, st, mode, lstatic, src, xo)
+                     : anal_queue_variant<8>(P, g, x, st, mode, lstatic, src, xo);
+    }
+  }
   switch (np) {
     case 2: anal_variant<T, 2>(P, G, x, st, mode, lstatic, src, xs_out); break;
     case 4: anal_variant<T, 4>(P, G, x, st, mode, lstatic, src, xs_out); break;
@@ -576,6 +796,10 @@ wf_status init_legendre_attributes() {
   WF_CUDA((set_big_smem_anal<float, 4>(big)));
   WF_CUDA((set_big_smem_anal<float, 8>(big)));
   WF_CUDA((set_big_smem_anal<float, 16>(big)));
+  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_q<float, 4>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_q<float, 8>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return WF_OK;
 }
 

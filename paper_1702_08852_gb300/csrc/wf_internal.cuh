@@ -118,6 +118,13 @@ struct Plan {
   // the autotuner (opts.autotune) or the defaults below
   int syn_np[2] = {2, 2};
   int ana_np[2] = {4, 8};
+  // FP32 analysis scheduling: 0 = one CTA per m, 1 = warps take (m, tile)
+  // items from a queue and a combine kernel sums the tiles (ana_scratch)
+  int ana_queue = 0;
+  float *ana_scratch = nullptr;  // [tiles of 128 pairs][nalm] float2
+  int *ana_lstart = nullptr;     // [lmax+1][tiles] first l written per item
+  int *ana_counter = nullptr;    // the queue's next item (reset by the combine)
+  int num_sms = 0;
 
   // FFT tables
   int fftMmax = 1;
