@@ -228,6 +228,30 @@ wf_status wf_trace(wf_plan_t plan, int *count, int *stage, double *xi,
 wf_status wf_kernel_stats(wf_plan_t plan, int kernel, double *ms, long *launches,
                           double *gflop, int reset);
 
+/* Launch variants of the Legendre kernels in use by a plan, and the times
+ * the autotuner measured for each candidate (opts.autotune = 1; -1 where a
+ * candidate was not timed, e.g. a cached choice or autotune = 0).
+ * Index [0] = FP64 kernels, [1] = FP32 kernels.
+ *  syn_np     ring pairs per thread of the synthesis.
+ *  ana_np     ring pairs per lane of the analysis.
+ *  ana_queue  FP32 analysis scheduling: 0 = one CTA per m, 1 = warps take
+ *             (m, tile) items from a queue, then a per-m combine kernel.
+ *  syn_ms     candidates 1, 2, 4 pairs per thread: ms for two launches.
+ *  ana_ms     candidates (per-m CTA) 2, 4, 8, 16 pairs per lane, then (FP32
+ *             only) queue with 4 and 8: ms for two launches. */
+typedef struct {
+  int syn_np[2], ana_np[2], ana_queue;
+  float syn_ms[2][3], ana_ms[2][6];
+} wf_tuning;
+wf_status wf_get_tuning(wf_plan_t plan, wf_tuning *out);
+/* Set the launch variants (syn_np, ana_np, ana_queue of *in; the ms fields
+ * are ignored).  syn_np in {1, 2, 4}; ana_np in {2, 4, 8, 16} (FP64 {2, 4,
+ * 8}); ana_queue 0 or 1, and with 1 ana_np[1] in {4, 8}.  The plan's
+ * captured iteration graphs are dropped and re-captured on the next solve.
+ * Errors: WF_ERR_ARG for NULL or a value outside these sets (the plan is
+ * unchanged). */
+wf_status wf_set_tuning(wf_plan_t plan, const wf_tuning *in);
+
 /* Algorithmic work of one Legendre transform at band limit L (<= lmax): the
  * number of (l, m, ring pair) terms with l <= L and |lambda_lm| >= 2^-100. */
 wf_status wf_legendre_terms(wf_plan_t plan, int L, double *terms);

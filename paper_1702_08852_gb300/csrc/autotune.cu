@@ -72,12 +72,14 @@ wf_status autotune(Plan &P) {
   for (int k = 0; k < 2 && st == WF_OK; ++k) {  // 0 = FP64, 1 = FP32
     float best = 1e30f;
     int pick = P.syn_np[k];
-    for (int c : syn_cand) {
+    for (int ci = 0; ci < 3; ++ci) {
+      const int c = syn_cand[ci];
       P.syn_np[k] = c;
       float ms = 0.f;
       st = k ? time_synth<float2>(P, P.xs32, P.F32, e0, e1, &ms)
              : time_synth<double2>(P, P.xs64, P.F64, e0, e1, &ms);
       if (st != WF_OK) break;
+      P.tune_syn_ms[k][ci] = ms;
       if (ms < best) {
         best = ms;
         pick = c;
@@ -98,6 +100,7 @@ wf_status autotune(Plan &P) {
       float ms = 0.f;
       st = k ? time_anal<float2>(P, P.G32, e0, e1, &ms)
              : time_anal<double2>(P, P.G64, e0, e1, &ms);
+      if (st == WF_OK) P.tune_ana_ms[k][q ? 4 + (i - nc) : i] = ms;
       if (st == WF_OK && ms < best) {
         best = ms;
         pick = P.ana_np[k];

@@ -1,5 +1,6 @@
 // capi.cu -- the extern "C" entry points declared in include/wf.h:
 // argument checking, plan lifetime, error strings.
+#include <initializer_list>
 #include <math.h>
 #include <string.h>
 
@@ -365,6 +366,47 @@ wf_status wf_kernel_stats(wf_plan_t plan, int kernel, double *ms, long *launches
     plan->kern_ms[kernel] = 0.0;
     plan->kern_launches[kernel] = 0;
     plan->kern_flop[kernel] = 0.0;
+  }
+  return WF_OK;
+}
+
+wf_status wf_get_tuning(wf_plan_t plan, wf_tuning *out) {
+  if (!plan || !out) return arg_error("wf_get_tuning: NULL argument");
+  for (int k = 0; k < 2; ++k) {
+    out->syn_np[k] = plan->syn_np[k];
+    out->ana_np[k] = plan->ana_np[k];
+    for (int c = 0; c < 3; ++c) out->syn_ms[k][c] = plan->tune_syn_ms[k][c];
+    for (int c = 0; c < 6; ++c) out->ana_ms[k][c] = plan->tune_ana_ms[k][c];
+  }
+  out->ana_queue = plan->ana_queue;
+  return WF_OK;
+}
+
+wf_status wf_set_tuning(wf_plan_t plan, const wf_tuning *in) {
+  if (!plan || !in) return arg_error("wf_set_tuning: NULL argument");
+  auto one_of = [](int v, std::initializer_list<int> set) {
+    for (int s : set)
+      if (v == s) return true;
+    return false;
+  };
+  for (int k = 0; k < 2; ++k) {
+    if (!one_of(in->syn_np[k], {1, 2, 4}))
+      return arg_error("wf_set_tuning: syn_np must be 1, 2 or 4");
+  }
+  if (!one_of(in->ana_np[0], {2, 4, 8}))
+    return arg_error("wf_set_tuning: FP64 ana_np must be 2, 4 or 8");
+  if (!one_of(in->ana_queue, {0, 1}))
+    return arg_error("wf_set_tuning: ana_queue must be 0 or 1");
+  if (in->ana_queue ? !one_of(in->ana_np[1], {4, 8}) : !one_of(in->ana_np[1], {2, 4, 8, 16}))
+    return arg_error("wf_set_tuning: FP32 ana_np must be 2, 4, 8 or 16 (queue: 4 or 8)");
+  for (int k = 0; k < 2; ++k) {
+    plan->syn_np[k] = in->syn_np[k];
+    plan->ana_np[k] = in->ana_np[k];
+  }
+  plan->ana_queue = in->ana_queue;
+  for (int i = 0; i < 3; ++i) {
+    if (plan->graph[i]) cudaGraphExecDestroy(plan->graph[i]);
+    plan->graph[i] = nullptr;
   }
   return WF_OK;
 }

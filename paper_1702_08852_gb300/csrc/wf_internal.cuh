@@ -125,6 +125,8 @@ struct Plan {
   int *ana_lstart = nullptr;     // [lmax+1][tiles] first l written per item
   int *ana_counter = nullptr;    // the queue's next item (reset by the combine)
   int num_sms = 0;
+  float tune_syn_ms[2][3] = {{-1, -1, -1}, {-1, -1, -1}};
+  float tune_ana_ms[2][6] = {{-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}};
 
   // FFT tables
   int fftMmax = 1;

@@ -49,6 +49,12 @@ class wf_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class _Tuning(ctypes.Structure):
+    _fields_ = [("syn_np", ctypes.c_int * 2), ("ana_np", ctypes.c_int * 2),
+                ("ana_queue", ctypes.c_int), ("syn_ms", (ctypes.c_float * 3) * 2),
+                ("ana_ms", (ctypes.c_float * 6) * 2)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 
@@ -87,6 +93,8 @@ def lib():
             "wf_kernel_stats": (I, [_P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long),
                                     ctypes.POINTER(D), I]),
             "wf_legendre_terms": (I, [_P, I, ctypes.POINTER(D)]),
+            "wf_get_tuning": (I, [_P, ctypes.POINTER(_Tuning)]),
+            "wf_set_tuning": (I, [_P, ctypes.POINTER(_Tuning)]),
             "wf_net_create": (I, [ctypes.POINTER(_P), _P, I, I, I, I]),
             "wf_net_num_params": (ctypes.c_long, [_P]),
             "wf_net_set_params": (I, [_P, _P, ctypes.c_long]),
@@ -310,6 +318,26 @@ class Plan:
         key = "gbytes" if int(kernel) == 2 else "gflop"
         return {"ms": ms.value, "launches": n.value, key: gf.value}
 
+    def tuning(self):
+        """Launch variants in use and the autotuner's timings (wf_get_tuning)."""
+        t = _Tuning()
+        _check(lib().wf_get_tuning(self.handle, ctypes.byref(t)))
+        return {"syn_np": list(t.syn_np), "ana_np": list(t.ana_np),
+                "ana_queue": t.ana_queue,
+                "syn_ms": [list(r) for r in t.syn_ms], "ana_ms": [list(r) for r in t.ana_ms]}
+
+    def set_tuning(self, syn_np=None, ana_np=None, ana_queue=None):
+        """Force launch variants (wf_set_tuning); None keeps the current one."""
+        t = _Tuning()
+        _check(lib().wf_get_tuning(self.handle, ctypes.byref(t)))
+        if syn_np is not None:
+            t.syn_np[0], t.syn_np[1] = syn_np
+        if ana_np is not None:
+            t.ana_np[0], t.ana_np[1] = ana_np
+        if ana_queue is not None:
+            t.ana_queue = int(ana_queue)
+        _check(lib().wf_set_tuning(self.handle, ctypes.byref(t)))
+
     def legendre_terms(self, L=None):
         t = ctypes.c_double()
         _check(lib().wf_legendre_terms(self.handle, self.lmax if L is None else int(L),
@@ -462,6 +490,14 @@ def wf_kernel_stats(plan, kernel=0, reset=False):
 
 def wf_legendre_terms(plan, L=None):
     return plan.legendre_terms(L)
+
+
+def wf_get_tuning(plan):
+    return plan.tuning()
+
+
+def wf_set_tuning(plan, syn_np=None, ana_np=None, ana_queue=None):
+    return plan.set_tuning(syn_np, ana_np, ana_queue)
 
 
 def wf_destroy(plan):

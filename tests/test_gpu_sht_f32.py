@@ -90,3 +90,45 @@ def test_f32_full_size_sampled(torch_cuda, osht):
     om = 4 * np.pi / npix
     ref = om * osht.adjoint_modes(m, nside, lmax, ls[sel], ms[sel])
     assert np.max(np.abs(b[sel] - ref)) <= tol32(nside, lmax) * np.max(np.abs(b))
+
+
+VARIANTS = [dict(ana_np=(4, 2), ana_queue=0), dict(ana_np=(4, 4), ana_queue=0),
+            dict(ana_np=(4, 8), ana_queue=0), dict(ana_np=(4, 16), ana_queue=0),
+            dict(ana_np=(4, 4), ana_queue=1), dict(ana_np=(4, 8), ana_queue=1),
+            dict(syn_np=(2, 1)), dict(syn_np=(2, 4))]
+
+
+@pytest.mark.parametrize("tuning", VARIANTS)
+@pytest.mark.parametrize("nside,lmax", [(32, 95), (64, 128)])
+def test_f32_launch_variants_match_oracle(torch_cuda, osht, tuning, nside, lmax):
+    """Every launch variant of the FP32 Legendre kernels (forced through
+    wf_set_tuning) against the oracle, both directions."""
+    torch = torch_cuda
+    from paper_1702_08852_gb300 import wf
+    a = rand_alm(lmax, 7 * nside + lmax)
+    ref = osht.alm2map(a, nside, lmax)
+    m = np.random.default_rng(lmax).standard_normal(12 * nside * nside)
+    refb = osht.map2alm(m, nside, lmax)
+    with wf.Plan(nside, lmax, np.ones(lmax + 1)) as p:
+        p.set_tuning(**tuning)
+        got = p.alm2map_f32(torch.from_numpy(a).cuda()).cpu().numpy()
+        gotb = p.map2alm_f32(torch.from_numpy(m).cuda()).cpu().numpy()
+        gotb2 = p.map2alm_f32(torch.from_numpy(m).cuda()).cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= tol32(nside, lmax) * np.max(np.abs(ref))
+    assert np.max(np.abs(gotb - refb)) <= tol32(nside, lmax) * np.max(np.abs(refb))
+    assert np.array_equal(gotb, gotb2)  # deterministic, queue included
+
+
+def test_tuning_report_and_bad_values(torch_cuda):
+    torch = torch_cuda
+    from paper_1702_08852_gb300 import wf
+    with wf.Plan(16, 32, np.ones(33), autotune=1) as p:
+        t = p.tuning()
+        assert all(ms > 0 for ms in t["syn_ms"][1]) and all(ms > 0 for ms in t["ana_ms"][1])
+        assert t["ana_ms"][0][3] == -1.0  # FP64 has no 16-pair candidate
+        assert t["ana_np"][1] in (2, 4, 8, 16) and t["ana_queue"] in (0, 1)
+        for bad in (dict(syn_np=(3, 2)), dict(ana_np=(16, 8)), dict(ana_queue=2),
+                    dict(ana_np=(4, 2), ana_queue=1)):
+            with pytest.raises(wf.WFError):
+                p.set_tuning(**bad)
+        assert p.tuning()["ana_np"] == t["ana_np"]

@@ -29,11 +29,13 @@ def problem(osht, kind, nside, seed, **kw):
     return p, d
 
 
-def gpu_solve(torch, p, d, **opts):
+def gpu_solve(torch, p, d, tuning=None, **opts):
     from paper_1702_08852_gb300 import wf
     nv = torch.from_numpy(p.noise_var).cuda()
     mk = torch.from_numpy(p.mask.astype(np.uint8)).cuda()
     with wf.Plan(p.nside, p.lmax, p.cl, nv, mk, **opts) as plan:
+        if tuning:
+            plan.set_tuning(**tuning)
         alm, mp, st = plan.solve(torch.from_numpy(d).cuda())
         tr = plan.trace()
         return alm.cpu().numpy(), mp.cpu().numpy(), st, tr
@@ -209,3 +211,21 @@ def test_mixed_precision_reaches_fp64_fixed_point(torch_cuda, osht, odm, nside, 
     err = np.linalg.norm(mp - sref) / np.linalg.norm(sref)
     assert err < 1e-6, (err, st)
     assert st["fp_residual"] < 1e-6
+
+
+@pytest.mark.parametrize("ana_np,ana_queue", [(4, 1), (8, 1), (16, 0), (2, 0)])
+def test_mixed_precision_variants_reach_fp64_fixed_point(torch_cuda, osht, odm, ana_np,
+                                                         ana_queue):
+    """The same check with the FP32 analysis forced to each launch variant
+    (the queue-scheduled one included: its combine kernel carries the filter,
+    the anchored-stage source and the Cauchy partial sums)."""
+    torch = torch_cuda
+    p, d = problem(osht, "lognormal", 16, 8)
+    alm, mp, st, tr = gpu_solve(torch, p, d, tuning={"ana_np": (4, ana_np),
+                                                     "ana_queue": ana_queue},
+                                precision=1, eps_final=1e-7, stop_rule=1)
+    assert st["converged"] == 1
+    Y = osht.ymatrix(p.nside, p.lmax)
+    ref = odm.dm_fixed_point_dense(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d, 0.0, Y=Y)
+    sref = Y @ osht.alm_to_real(ref, p.lmax)
+    assert np.linalg.norm(mp - sref) / np.linalg.norm(sref) < 1e-6
