@@ -229,8 +229,9 @@ wf_status wf_kernel_stats(wf_plan_t plan, int kernel, double *ms, long *launches
                           double *gflop, int reset);
 
 /* Launch variants of the Legendre kernels in use by a plan, and the times
- * the autotuner measured for each candidate (opts.autotune = 1; -1 where a
- * candidate was not timed, e.g. a cached choice or autotune = 0).
+ * the autotuner measured for each candidate (opts.autotune = 1; a choice
+ * cached for the geometry reports the timings it was made from; -1 where a
+ * candidate was not timed, and everywhere with autotune = 0).
  * Index [0] = FP64 kernels, [1] = FP32 kernels.
  *  syn_np     ring pairs per thread of the synthesis.
  *  ana_np     ring pairs per lane of the analysis.

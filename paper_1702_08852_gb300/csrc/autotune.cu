@@ -5,6 +5,8 @@
 // more pairs per thread give more independent recurrences (latency hiding)
 // and amortise the analysis' warp reduction, but cost registers and
 // occupancy.  Results are cached per (nside, lmax) for the process.
+#include <string.h>
+
 #include <map>
 #include <mutex>
 #include <utility>
@@ -16,6 +18,7 @@ namespace wf {
 namespace {
 struct Choice {
   int syn[2], ana[2], ana_queue;
+  float syn_ms[2][3], ana_ms[2][6];  // the timings the choice was made from
 };
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, Choice> g_tune_cache;
@@ -56,6 +59,8 @@ wf_status autotune(Plan &P) {
         P.ana_np[k] = it->second.ana[k];
       }
       P.ana_queue = it->second.ana_queue;
+      memcpy(P.tune_syn_ms, it->second.syn_ms, sizeof(P.tune_syn_ms));
+      memcpy(P.tune_ana_ms, it->second.ana_ms, sizeof(P.tune_ana_ms));
       return WF_OK;
     }
   }
@@ -120,6 +125,8 @@ wf_status autotune(Plan &P) {
     c.ana[k] = P.ana_np[k];
   }
   c.ana_queue = P.ana_queue;
+  memcpy(c.syn_ms, P.tune_syn_ms, sizeof(c.syn_ms));
+  memcpy(c.ana_ms, P.tune_ana_ms, sizeof(c.ana_ms));
   g_tune_cache[key] = c;
   return WF_OK;
 }
