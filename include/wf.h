@@ -233,24 +233,28 @@ wf_status wf_kernel_stats(wf_plan_t plan, int kernel, double *ms, long *launches
  * cached for the geometry reports the timings it was made from; -1 where a
  * candidate was not timed, and everywhere with autotune = 0).
  * Index [0] = FP64 kernels, [1] = FP32 kernels.
- *  syn_np     ring pairs per thread of the synthesis.
- *  ana_np     ring pairs per lane of the analysis.
- *  ana_queue  FP32 analysis scheduling: 0 = one CTA per m, 1 = warps take
- *             (m, tile) items from a queue, then a per-m combine kernel.
- *  syn_ms     candidates 1, 2, 4 pairs per thread: ms for two launches.
- *  ana_ms     candidates (per-m CTA) 2, 4, 8, 16 pairs per lane, then (FP32
- *             only) queue with 4 and 8: ms for two launches. */
+ *  syn_np      ring pairs per thread of the synthesis.
+ *  syn_packed  FP32 synthesis on packed f32x2 pairs of rings (syn_np 2, 4).
+ *  ana_np      ring pairs per lane of the analysis.
+ *  ana_queue   FP32 analysis scheduling: 0 = one CTA per m, 1 = warps take
+ *              (m, tile) items from a queue, then a per-m combine kernel.
+ *  ana_packed  FP32 per-m analysis on packed f32x2 pairs (ana_np 4, 8).
+ *  syn_ms      candidates 1, 2, 4 pairs per thread, then (FP32) packed 2, 4:
+ *              ms for two launches.
+ *  ana_ms      candidates 2, 4, 8, 16 pairs per lane, then (FP32 only) queue
+ *              4, 8 and packed 4, 8: ms for two launches. */
 typedef struct {
-  int syn_np[2], ana_np[2], ana_queue;
-  float syn_ms[2][3], ana_ms[2][6];
+  int syn_np[2], syn_packed, ana_np[2], ana_queue, ana_packed;
+  float syn_ms[2][5], ana_ms[2][8];
 } wf_tuning;
 wf_status wf_get_tuning(wf_plan_t plan, wf_tuning *out);
-/* Set the launch variants (syn_np, ana_np, ana_queue of *in; the ms fields
- * are ignored).  syn_np in {1, 2, 4}; ana_np in {2, 4, 8, 16} (FP64 {2, 4,
- * 8}); ana_queue 0 or 1, and with 1 ana_np[1] in {4, 8}.  The plan's
- * captured iteration graphs are dropped and re-captured on the next solve.
- * Errors: WF_ERR_ARG for NULL or a value outside these sets (the plan is
- * unchanged). */
+/* Set the launch variants (the int fields of *in; the ms fields are
+ * ignored).  syn_np in {1, 2, 4}; ana_np in {2, 4, 8, 16} (FP64 {2, 4, 8});
+ * ana_queue and the packed flags 0 or 1; ana_queue and ana_packed not both;
+ * syn_packed needs syn_np[1] in {2, 4}; ana_queue or ana_packed need
+ * ana_np[1] in {4, 8}.  The plan's captured iteration graphs are dropped and
+ * re-captured on the next solve.  Errors: WF_ERR_ARG for NULL or a value
+ * outside these sets (the plan is unchanged). */
 wf_status wf_set_tuning(wf_plan_t plan, const wf_tuning *in);
 
 /* Algorithmic work of one Legendre transform at band limit L (<= lmax): the

@@ -17,8 +17,8 @@ namespace wf {
 
 namespace {
 struct Choice {
-  int syn[2], ana[2], ana_queue;
-  float syn_ms[2][3], ana_ms[2][6];  // the timings the choice was made from
+  int syn[2], ana[2], ana_queue, syn_x2, ana_x2;
+  float syn_ms[2][5], ana_ms[2][8];  // the timings the choice was made from
 };
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, Choice> g_tune_cache;
@@ -59,6 +59,8 @@ wf_status autotune(Plan &P) {
         P.ana_np[k] = it->second.ana[k];
       }
       P.ana_queue = it->second.ana_queue;
+      P.syn_x2 = it->second.syn_x2;
+      P.ana_x2 = it->second.ana_x2;
       memcpy(P.tune_syn_ms, it->second.syn_ms, sizeof(P.tune_syn_ms));
       memcpy(P.tune_ana_ms, it->second.ana_ms, sizeof(P.tune_ana_ms));
       return WF_OK;
@@ -77,9 +79,14 @@ wf_status autotune(Plan &P) {
   for (int k = 0; k < 2 && st == WF_OK; ++k) {  // 0 = FP64, 1 = FP32
     float best = 1e30f;
     int pick = P.syn_np[k];
-    for (int ci = 0; ci < 3; ++ci) {
-      const int c = syn_cand[ci];
+    int pick_x2 = 0;
+    // FP32 also tries the packed f32x2 synthesis with 2 and 4 pairs
+    const int nsyn = k ? 5 : 3;
+    for (int ci = 0; ci < nsyn; ++ci) {
+      const bool x2 = ci >= 3;
+      const int c = x2 ? (ci == 3 ? 2 : 4) : syn_cand[ci];
       P.syn_np[k] = c;
+      if (k) P.syn_x2 = x2 ? 1 : 0;
       float ms = 0.f;
       st = k ? time_synth<float2>(P, P.xs32, P.F32, e0, e1, &ms)
              : time_synth<double2>(P, P.xs64, P.F64, e0, e1, &ms);
@@ -88,32 +95,38 @@ wf_status autotune(Plan &P) {
       if (ms < best) {
         best = ms;
         pick = c;
+        pick_x2 = x2 ? 1 : 0;
       }
     }
+    if (k) P.syn_x2 = pick_x2;
     P.syn_np[k] = pick;
     best = 1e30f;
     pick = P.ana_np[k];
-    int pick_q = 0;
+    int pick_q = 0, pick_ax2 = 0;
     const int *cand = k ? ana_cand32 : ana_cand64;
     const int nc = k ? 4 : 3;
-    // FP32 also tries the queue-scheduled analysis with 4 and 8 pairs per lane
-    const int nq = k ? 2 : 0;
-    for (int i = 0; i < nc + nq && st == WF_OK; ++i) {
-      const bool q = i >= nc;
+    // FP32 also tries the queue-scheduled analysis (slots 4, 5) and the
+    // packed f32x2 one (slots 6, 7), each with 4 and 8 pairs per lane
+    const int ntot = k ? 8 : 3;
+    for (int i = 0; i < ntot && st == WF_OK; ++i) {
+      const bool q = k && i >= 4 && i < 6, x2 = k && i >= 6;
       P.ana_queue = q ? 1 : 0;
-      P.ana_np[k] = q ? (i == nc ? 4 : 8) : cand[i];
+      P.ana_x2 = x2 ? 1 : 0;
+      P.ana_np[k] = (q || x2) ? ((i & 1) ? 8 : 4) : cand[i];
       float ms = 0.f;
       st = k ? time_anal<float2>(P, P.G32, e0, e1, &ms)
              : time_anal<double2>(P, P.G64, e0, e1, &ms);
-      if (st == WF_OK) P.tune_ana_ms[k][q ? 4 + (i - nc) : i] = ms;
+      if (st == WF_OK) P.tune_ana_ms[k][i] = ms;
       if (st == WF_OK && ms < best) {
         best = ms;
         pick = P.ana_np[k];
         pick_q = P.ana_queue;
+        pick_ax2 = P.ana_x2;
       }
     }
     P.ana_np[k] = pick;
-    if (k) P.ana_queue = pick_q;
+    P.ana_queue = k ? pick_q : P.ana_queue;
+    P.ana_x2 = k ? pick_ax2 : P.ana_x2;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -125,6 +138,8 @@ wf_status autotune(Plan &P) {
     c.ana[k] = P.ana_np[k];
   }
   c.ana_queue = P.ana_queue;
+  c.syn_x2 = P.syn_x2;
+  c.ana_x2 = P.ana_x2;
   memcpy(c.syn_ms, P.tune_syn_ms, sizeof(c.syn_ms));
   memcpy(c.ana_ms, P.tune_ana_ms, sizeof(c.ana_ms));
   g_tune_cache[key] = c;

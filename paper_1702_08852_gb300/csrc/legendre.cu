@@ -74,9 +74,14 @@ __device__ __forceinline__ int warp_max(int v) {
   return v;
 }
 
-// One step of u_l = c_l z u_{l-1} - u_{l-2}.  In FP32, z = cos(theta) is
-// carried as zh + zl (two floats): rounding z alone to FP32 displaces a ring
-// near the pole by ~6e-8 / sin(theta) rad, a phase error of l times that.
+// One step of the recurrence.  FP64: u_l = c_l z u_{l-1} - u_{l-2}.  FP32
+// runs the sign-folded s_l = eps_l u_l, eps_l = (-1)^floor(l/2), which obeys
+// s_l = c'_l z s_{l-1} + s_{l-2} with the table c'_l = +-c_l (plan.cu): the
+// same roundings, no negated operand.  The FP32 kernels therefore take seeds
+// times eps, give ring sums in s-units (the epilogue multiplies by eps_l)
+// and read a synthesis input pre-multiplied by eps_l.  In FP32, z = cos(theta)
+// is carried as zh + zl (two floats): rounding z alone to FP32 displaces a
+// ring near the pole by ~6e-8 / sin(theta) rad, a phase error of l times that.
 __device__ __forceinline__ double rec_step(double c, double zh, double, double u1,
                                            double u2) {
   return fma(c * zh, u1, -u2);
@@ -84,7 +89,38 @@ __device__ __forceinline__ double rec_step(double c, double zh, double, double u
 __device__ __forceinline__ float rec_step(float c, float zh, float zl, float u1,
                                           float u2) {
   const float a = c * u1;
-  return fmaf(a, zh, fmaf(a, zl, -u2));
+  return fmaf(a, zh, fmaf(a, zl, u2));
+}
+// eps_l of the FP32 sign folding (1 in FP64)
+template <typename T>
+__device__ __forceinline__ double fold_sign(int l) {
+  return (sizeof(T) == 4 && ((l >> 1) & 1)) ? -1.0 : 1.0;
+}
+
+// Packed FP32 pairs (sm_100 family f32x2 arithmetic): one instruction does
+// the operation for two rings, each half rounded as the scalar instruction.
+__device__ __forceinline__ void fma2(float &dx, float &dy, float ax, float ay, float bx,
+                                     float by, float cx, float cy) {
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(dx), "=f"(dy)
+      : "f"(ax), "f"(ay), "f"(bx), "f"(by), "f"(cx), "f"(cy));
+}
+__device__ __forceinline__ void mul2(float &dx, float &dy, float ax, float ay, float bx,
+                                     float by) {
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " mul.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(dx), "=f"(dy)
+      : "f"(ax), "f"(ay), "f"(bx), "f"(by));
+}
+// the FP32 recurrence step for rings j, j' at once (same roundings as rec_step)
+__device__ __forceinline__ void rec_step2(float c, float zh0, float zh1, float zl0,
+                                          float zl1, float u10, float u11, float u20,
+                                          float u21, float &s0, float &s1) {
+  float a0, a1, t0, t1;
+  mul2(a0, a1, c, c, u10, u11);
+  fma2(t0, t1, a0, a1, zl0, zl1, u20, u21);
+  fma2(s0, s1, a0, a1, zh0, zh1, t0, t1);
 }
 template <typename T>
 __device__ __forceinline__ void split_z(double z, T &zh, T &zl) {
@@ -98,7 +134,7 @@ __device__ __forceinline__ size_t align16d(size_t b) { return (b + 15) & ~(size_
 // ------------------------------------------------------------------ synthesis
 constexpr int SYN_THREADS = 128;
 
-template <typename T, int NP>
+template <typename T, int NP, bool X2 = false>
 __global__ void __launch_bounds__(SYN_THREADS)
     k_legendre_synth(const RingPair *__restrict__ pairs, int npairs, int lmax,
                      const double *__restrict__ rc, const float *__restrict__ rc32,
@@ -142,8 +178,8 @@ __global__ void __launch_bounds__(SYN_THREADS)
       split_z<T>(pairs[k].z, zh[j], zl[j]);
       ls[j] = seed_l[(long)m * npairs + k];
       const double2 su = seed_u[(long)m * npairs + k];
-      s0[j] = (T)su.x;
-      s1[j] = (T)su.y;
+      s0[j] = (T)(fold_sign<T>(ls[j]) * su.x);
+      s1[j] = (T)(fold_sign<T>(ls[j] + 1) * su.y);
     } else {
       zh[j] = zl[j] = (T)0;
       ls[j] = INT_MAX - 2;
@@ -201,16 +237,37 @@ __global__ void __launch_bounds__(SYN_THREADS)
         x0 = sx[l - m];
         x1 = sx[l + 1 - m];
       }
+      if constexpr (X2) {
+        // rings (2 jp, 2 jp + 1) in packed f32x2 pairs
+        static_assert(sizeof(T) == 4 && NP % 2 == 0, "packed pairs are FP32, NP even");
 #pragma unroll
-      for (int j = 0; j < NP; ++j) {
-        T u = rec_step(c0, zh[j], zl[j], u1[j], u2[j]);
-        er[j] = fma(u, x0.x, er[j]);
-        ei[j] = fma(u, x0.y, ei[j]);
-        T v = rec_step(c1, zh[j], zl[j], u, u1[j]);
-        orr[j] = fma(v, x1.x, orr[j]);
-        oi[j] = fma(v, x1.y, oi[j]);
-        u2[j] = u;
-        u1[j] = v;
+        for (int jp = 0; jp < NP / 2; ++jp) {
+          const int j0 = 2 * jp, j1 = 2 * jp + 1;
+          float w0, w1, v0, v1;
+          rec_step2(c0, zh[j0], zh[j1], zl[j0], zl[j1], u1[j0], u1[j1], u2[j0], u2[j1], w0,
+                    w1);
+          fma2(er[j0], er[j1], w0, w1, x0.x, x0.x, er[j0], er[j1]);
+          fma2(ei[j0], ei[j1], w0, w1, x0.y, x0.y, ei[j0], ei[j1]);
+          rec_step2(c1, zh[j0], zh[j1], zl[j0], zl[j1], w0, w1, u1[j0], u1[j1], v0, v1);
+          fma2(orr[j0], orr[j1], v0, v1, x1.x, x1.x, orr[j0], orr[j1]);
+          fma2(oi[j0], oi[j1], v0, v1, x1.y, x1.y, oi[j0], oi[j1]);
+          u2[j0] = w0;
+          u2[j1] = w1;
+          u1[j0] = v0;
+          u1[j1] = v1;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          T u = rec_step(c0, zh[j], zl[j], u1[j], u2[j]);
+          er[j] = fma(u, x0.x, er[j]);
+          ei[j] = fma(u, x0.y, ei[j]);
+          T v = rec_step(c1, zh[j], zl[j], u, u1[j]);
+          orr[j] = fma(v, x1.x, orr[j]);
+          oi[j] = fma(v, x1.y, oi[j]);
+          u2[j] = u;
+          u1[j] = v;
+        }
       }
     }
     if (l <= L) {
@@ -264,7 +321,7 @@ __device__ __forceinline__ T transpose_reduce32(T (&v)[32], int lane) {
 // chunk.  TAIL: the chunk runs past L (l > L contributes 0).  In FP32 full
 // chunks the coefficients c_l come from shared memory in 16-byte loads
 // (lc - m is a multiple of LCHUNK and the table starts 16-byte aligned).
-template <typename T, int NP, bool INJ, bool TAIL>
+template <typename T, int NP, bool INJ, bool TAIL, bool X2 = false>
 __device__ __forceinline__ void anal_chunk(T (&v)[32], int lc, int L, int m,
                                            const T *__restrict__ sc, const T (&zh)[NP],
                                            const T (&zl)[NP], T (&u1)[NP], T (&u2)[NP],
@@ -294,6 +351,40 @@ __device__ __forceinline__ void anal_chunk(T (&v)[32], int lc, int L, int m,
         c = cc[jj];
       else
         c = sc[l - m];
+      if constexpr (X2) {
+        // rings (2 jp, 2 jp + 1) in packed pairs; the partial sums a, b hold
+        // the even / odd pair of each chunk of four rings
+        static_assert(sizeof(T) == 4 && NP % 2 == 0, "packed pairs are FP32, NP even");
+        float ar0 = 0.f, ar1 = 0.f, ai0 = 0.f, ai1 = 0.f;
+        float br0 = 0.f, br1 = 0.f, bi0 = 0.f, bi1 = 0.f;
+#pragma unroll
+        for (int jp = 0; jp < NP / 2; ++jp) {
+          const int j0 = 2 * jp, j1 = 2 * jp + 1;
+          float w0, w1;
+          rec_step2(c, zh[j0], zh[j1], zl[j0], zl[j1], u1[j0], u1[j1], u2[j0], u2[j1], w0,
+                    w1);
+          if (INJ) {
+            w0 = (l == ls[j0]) ? s0[j0] : w0;
+            w0 = (l == ls[j0] + 1) ? s1[j0] : w0;
+            w1 = (l == ls[j1]) ? s0[j1] : w1;
+            w1 = (l == ls[j1] + 1) ? s1[j1] : w1;
+          }
+          u2[j0] = u1[j0];
+          u2[j1] = u1[j1];
+          u1[j0] = w0;
+          u1[j1] = w1;
+          const bool ev = (jj & 1) == 0;
+          if ((jp & 1) == 0) {
+            fma2(ar0, ar1, w0, w1, ev ? pr[j0] : qr[j0], ev ? pr[j1] : qr[j1], ar0, ar1);
+            fma2(ai0, ai1, w0, w1, ev ? pim[j0] : qim[j0], ev ? pim[j1] : qim[j1], ai0, ai1);
+          } else {
+            fma2(br0, br1, w0, w1, ev ? pr[j0] : qr[j0], ev ? pr[j1] : qr[j1], br0, br1);
+            fma2(bi0, bi1, w0, w1, ev ? pim[j0] : qim[j0], ev ? pim[j1] : qim[j1], bi0, bi1);
+          }
+        }
+        a_re = (ar0 + ar1) + (br0 + br1);
+        a_im = (ai0 + ai1) + (bi0 + bi1);
+      } else {
 #pragma unroll
       for (int j = 0; j < NP; ++j) {
         T u = rec_step(c, zh[j], zl[j], u1[j], u2[j]);
@@ -313,6 +404,7 @@ __device__ __forceinline__ void anal_chunk(T (&v)[32], int lc, int L, int m,
           b_im = fma(u, pim_, b_im);
         }
       }
+      }
     }
     v[2 * jj] = a_re + b_re;
     v[2 * jj + 1] = a_im + b_im;
@@ -320,7 +412,7 @@ __device__ __forceinline__ void anal_chunk(T (&v)[32], int lc, int L, int m,
 }
 
 // Epilogue of one coefficient (l, m), index i: a = Omega g_l (sr, si) (the
-// ring sums in u-units), then in ANA_FILTER mode the source term of an
+// ring sums in u-units; FP32: s-units, times eps_l here), then in ANA_FILTER mode the source term of an
 // anchored stage, the filter f_l = Sbar / (Sbar + xi Omega) and the Cauchy
 // partial sums (weight wm = 1 for m = 0, 2 else); writes x and xs_out.
 template <typename T>
@@ -333,7 +425,7 @@ __device__ __forceinline__ void anal_finish(long i, int l, double sr, double si,
                                             double2 *__restrict__ x,
                                             typename Vec2<T>::type *__restrict__ xs_out,
                                             double &num, double &den) {
-  const double s = omega * rg[i];
+  const double s = omega * rg[i] * fold_sign<T>(l);  // ring sums are in s-units
   double ar = s * sr, ai = s * si;
   if (mode == ANA_FILTER) {
     const double sbar = fmax(cl[l] - mu * omega, 0.0);
@@ -350,7 +442,10 @@ __device__ __forceinline__ void anal_finish(long i, int l, double sr, double si,
     den += wm * (ar * ar + ai * ai);
   }
   x[i] = make_double2(ar, ai);
-  if (xs_out) xs_out[i] = Vec2<T>::make((T)(rg[i] * ar), (T)(rg[i] * ai));
+  if (xs_out) {  // the synthesis input g a (times eps_l in FP32)
+    const double gs = rg[i] * fold_sign<T>(l);
+    xs_out[i] = Vec2<T>::make((T)(gs * ar), (T)(gs * ai));
+  }
 }
 
 // coefficients of this m above the band (l > L) are zero
@@ -398,7 +493,7 @@ __device__ __forceinline__ void anal_partials(double num, double den, int m,
   }
 }
 
-template <typename T, int NP>
+template <typename T, int NP, bool X2 = false>
 __global__ void __launch_bounds__(ANA_THREADS)
     k_legendre_anal(const RingPair *__restrict__ pairs, int npairs, int lmax,
                     const double *__restrict__ rc, const float *__restrict__ rc32,
@@ -453,8 +548,8 @@ __global__ void __launch_bounds__(ANA_THREADS)
           split_z<T>(rp.z, zh[j], zl[j]);
           ls[j] = seed_l[(long)m * npairs + k];
           const double2 su = seed_u[(long)m * npairs + k];
-          s0[j] = (T)su.x;
-          s1[j] = (T)su.y;
+          s0[j] = (T)(fold_sign<T>(ls[j]) * su.x);
+          s1[j] = (T)(fold_sign<T>(ls[j] + 1) * su.y);
           const T2 gn = G[rp.ringN * stride + m];
           T2 gs = Vec2<T>::make((T)0, (T)0);
           if (rp.ringS >= 0) gs = G[rp.ringS * stride + m];
@@ -482,13 +577,13 @@ __global__ void __launch_bounds__(ANA_THREADS)
         // the warp already in (the plain recurrence: 5 FP instructions per
         // term), and the last, partial chunk
         if (lc + LCHUNK - 1 > L)
-          anal_chunk<T, NP, true, true>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
+          anal_chunk<T, NP, true, true, X2>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
                                         pr, pim, qr, qim);
         else if (lc <= linj)
-          anal_chunk<T, NP, true, false>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
+          anal_chunk<T, NP, true, false, X2>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
                                          pr, pim, qr, qim);
         else
-          anal_chunk<T, NP, false, false>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
+          anal_chunk<T, NP, false, false, X2>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
                                           pr, pim, qr, qim);
         const T tot = transpose_reduce32<T>(v, lane);
         const int l = lc + (lane >> 1);
@@ -571,8 +666,8 @@ __global__ void __launch_bounds__(ANA_THREADS)
         split_z<T>(rp.z, zh[j], zl[j]);
         ls[j] = seed_l[(long)m * npairs + k];
         const double2 su = seed_u[(long)m * npairs + k];
-        s0[j] = (T)su.x;
-        s1[j] = (T)su.y;
+        s0[j] = (T)(fold_sign<T>(ls[j]) * su.x);
+        s1[j] = (T)(fold_sign<T>(ls[j] + 1) * su.y);
         const typename Vec2<T>::type gn = G[rp.ringN * stride + m];
         typename Vec2<T>::type gs = Vec2<T>::make((T)0, (T)0);
         if (rp.ringS >= 0) gs = G[rp.ringS * stride + m];
@@ -672,26 +767,26 @@ struct Kernels<float2> {
   typedef float T;
 };
 
-template <typename T, int NP>
+template <typename T, int NP, bool X2 = false>
 static void synth_variant(const Plan &P, const typename Vec2<T>::type *xs,
                           typename Vec2<T>::type *F, const SolverState *st, int lstatic) {
   typedef typename Vec2<T>::type T2;
   const size_t smem = align16(sizeof(T2) * (P.lmax + 1)) + sizeof(T) * (P.lmax + 1);
   const int pairs_per_cta = SYN_THREADS * NP;
   dim3 grid((P.npairs + pairs_per_cta - 1) / pairs_per_cta, P.lmax + 1);
-  k_legendre_synth<T, NP><<<grid, SYN_THREADS, smem, P.stream>>>(
+  k_legendre_synth<T, NP, X2><<<grid, SYN_THREADS, smem, P.stream>>>(
       P.pairs, P.npairs, P.lmax, P.rc, P.rc32, P.rg, P.seed_l, P.seed_u, xs, F, st,
       lstatic);
 }
 
-template <typename T, int NP>
+template <typename T, int NP, bool X2 = false>
 static void anal_variant(const Plan &P, const typename Vec2<T>::type *G, double2 *x,
                          const SolverState *st, int mode, int lstatic, const double2 *src,
                          typename Vec2<T>::type *xs_out) {
   typedef typename Vec2<T>::type T2;
   const size_t smem =
       align16(sizeof(T2) * (P.lmax + 1) * ANA_WARPS) + sizeof(T) * (P.lmax + 1);
-  k_legendre_anal<T, NP><<<P.lmax + 1, ANA_THREADS, smem, P.stream>>>(
+  k_legendre_anal<T, NP, X2><<<P.lmax + 1, ANA_THREADS, smem, P.stream>>>(
       P.pairs, P.npairs, P.lmax, P.rc, P.rc32, P.rg, P.seed_l, P.seed_u, P.cl_d, P.omega,
       G, x, P.partials, src, xs_out, st, mode, lstatic);
 }
@@ -735,6 +830,16 @@ wf_status launch_legendre_synth(const Plan &P, const T2 *xs, T2 *F,
   typedef typename Kernels<T2>::T T;
   const int np = P.syn_np[sizeof(T) == 4];
   ++P.nlaunch;
+  if constexpr (sizeof(T) == 4) {
+    if (P.syn_x2) {
+      if (np == 4)
+        synth_variant<T, 4, true>(P, xs, F, st, lstatic);
+      else
+        synth_variant<T, 2, true>(P, xs, F, st, lstatic);
+      WF_CUDA(cudaGetLastError());
+      return WF_OK;
+    }
+  }
   switch (np) {
     case 1: synth_variant<T, 1>(P, xs, F, st, lstatic); break;
     case 4: synth_variant<T, 4>(P, xs, F, st, lstatic); break;
@@ -758,6 +863,14 @@ wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
       return np == 4 ? anal_queue_variant<4>(P, g, x, st, mode, lstatic, src, xo)
                      : anal_queue_variant<8>(P, g, x, st, mode, lstatic, src, xo);
     }
+    if (P.ana_x2) {
+      if (np == 4)
+        anal_variant<T, 4, true>(P, G, x, st, mode, lstatic, src, xs_out);
+      else
+        anal_variant<T, 8, true>(P, G, x, st, mode, lstatic, src, xs_out);
+      WF_CUDA(cudaGetLastError());
+      return WF_OK;
+    }
   }
   switch (np) {
     case 2: anal_variant<T, 2>(P, G, x, st, mode, lstatic, src, xs_out); break;
@@ -769,14 +882,14 @@ wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
   return WF_OK;
 }
 
-template <typename T, int NP>
+template <typename T, int NP, bool X2 = false>
 static cudaError_t set_big_smem_synth(int big) {
-  return cudaFuncSetAttribute(k_legendre_synth<T, NP>,
+  return cudaFuncSetAttribute(k_legendre_synth<T, NP, X2>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
-template <typename T, int NP>
+template <typename T, int NP, bool X2 = false>
 static cudaError_t set_big_smem_anal(int big) {
-  return cudaFuncSetAttribute(k_legendre_anal<T, NP>,
+  return cudaFuncSetAttribute(k_legendre_anal<T, NP, X2>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
@@ -796,6 +909,10 @@ wf_status init_legendre_attributes() {
   WF_CUDA((set_big_smem_anal<float, 4>(big)));
   WF_CUDA((set_big_smem_anal<float, 8>(big)));
   WF_CUDA((set_big_smem_anal<float, 16>(big)));
+  WF_CUDA((set_big_smem_synth<float, 2, true>(big)));
+  WF_CUDA((set_big_smem_synth<float, 4, true>(big)));
+  WF_CUDA((set_big_smem_anal<float, 4, true>(big)));
+  WF_CUDA((set_big_smem_anal<float, 8, true>(big)));
   WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_q<float, 4>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_q<float, 8>,
@@ -803,20 +920,25 @@ wf_status init_legendre_attributes() {
   return WF_OK;
 }
 
-// xs = g_lm x_lm in the transform precision (the synthesis input)
+// xs = g_lm x_lm in the transform precision (the synthesis input; FP32
+// also times eps_l); one block per m
 template <typename T2>
 __global__ void k_prescale(const double2 *__restrict__ x, const double *__restrict__ rg,
-                           long n, T2 *__restrict__ xs) {
+                           int lmax, T2 *__restrict__ xs) {
   typedef typename Scalar<T2>::type T;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long)gridDim.x * blockDim.x)
-    xs[i] = Vec2<T>::make((T)(rg[i] * x[i].x), (T)(rg[i] * x[i].y));
+  const int m = blockIdx.x;
+  const long base = lm_index(lmax, m, m) - m;
+  for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
+    const long i = base + l;
+    const double gs = rg[i] * fold_sign<T>(l);
+    xs[i] = Vec2<T>::make((T)(gs * x[i].x), (T)(gs * x[i].y));
+  }
 }
 
 template <typename T2>
 wf_status launch_prescale(const Plan &P, const double2 *x, T2 *xs) {
   ++P.nlaunch;
-  k_prescale<T2><<<304, 256, 0, P.stream>>>(x, P.rg, P.nalm, xs);
+  k_prescale<T2><<<P.lmax + 1, 128, 0, P.stream>>>(x, P.rg, P.lmax, xs);
   WF_CUDA(cudaGetLastError());
   return WF_OK;
 }

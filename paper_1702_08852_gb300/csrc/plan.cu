@@ -216,12 +216,16 @@ static wf_status make_recurrence_tables(Plan &P) {
       }
       g[i] = gl;
       c[i] = a * g1 / gl;
+      // FP32 kernels run s_l = eps_l u_l, eps_l = (-1)^floor(l/2): then
+      // s_l = c'_l z s_{l-1} + s_{l-2} with c'_l = eps_{l-1} eps_l c_l =
+      // -c_l for even l, +c_l for odd l (no negated operand, so two rings
+      // fit one packed f32x2 FMA)
+      c32[i] = (float)((l % 2 == 0) ? -c[i] : c[i]);
       a_prev = a;
       g2 = g1;
       g1 = gl;
     }
   }
-  for (long i = 0; i < P.nalm; ++i) c32[i] = (float)c[i];
   WF_CUDA(cudaMalloc(&P.rc, sizeof(double) * P.nalm));
   WF_CUDA(cudaMalloc(&P.rg, sizeof(double) * P.nalm));
   WF_CUDA(cudaMalloc(&P.rc32, sizeof(float) * P.nalm));

@@ -121,12 +121,15 @@ struct Plan {
   // FP32 analysis scheduling: 0 = one CTA per m, 1 = warps take (m, tile)
   // items from a queue and a combine kernel sums the tiles (ana_scratch)
   int ana_queue = 0;
+  // FP32 kernels on packed f32x2 pairs of rings (NP even): 0 / 1
+  int syn_x2 = 0, ana_x2 = 0;
   float *ana_scratch = nullptr;  // [tiles of 128 pairs][nalm] float2
   int *ana_lstart = nullptr;     // [lmax+1][tiles] first l written per item
   int *ana_counter = nullptr;    // the queue's next item (reset by the combine)
   int num_sms = 0;
-  float tune_syn_ms[2][3] = {{-1, -1, -1}, {-1, -1, -1}};
-  float tune_ana_ms[2][6] = {{-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}};
+  float tune_syn_ms[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};
+  float tune_ana_ms[2][8] = {{-1, -1, -1, -1, -1, -1, -1, -1},
+                             {-1, -1, -1, -1, -1, -1, -1, -1}};
 
   // FFT tables
   int fftMmax = 1;

@@ -50,9 +50,10 @@ class wf_stats(ctypes.Structure):
 
 
 class _Tuning(ctypes.Structure):
-    _fields_ = [("syn_np", ctypes.c_int * 2), ("ana_np", ctypes.c_int * 2),
-                ("ana_queue", ctypes.c_int), ("syn_ms", (ctypes.c_float * 3) * 2),
-                ("ana_ms", (ctypes.c_float * 6) * 2)]
+    _fields_ = [("syn_np", ctypes.c_int * 2), ("syn_packed", ctypes.c_int),
+                ("ana_np", ctypes.c_int * 2), ("ana_queue", ctypes.c_int),
+                ("ana_packed", ctypes.c_int), ("syn_ms", (ctypes.c_float * 5) * 2),
+                ("ana_ms", (ctypes.c_float * 8) * 2)]
 
 
 _lib = None
@@ -322,11 +323,13 @@ class Plan:
         """Launch variants in use and the autotuner's timings (wf_get_tuning)."""
         t = _Tuning()
         _check(lib().wf_get_tuning(self.handle, ctypes.byref(t)))
-        return {"syn_np": list(t.syn_np), "ana_np": list(t.ana_np),
-                "ana_queue": t.ana_queue,
+        return {"syn_np": list(t.syn_np), "syn_packed": t.syn_packed,
+                "ana_np": list(t.ana_np), "ana_queue": t.ana_queue,
+                "ana_packed": t.ana_packed,
                 "syn_ms": [list(r) for r in t.syn_ms], "ana_ms": [list(r) for r in t.ana_ms]}
 
-    def set_tuning(self, syn_np=None, ana_np=None, ana_queue=None):
+    def set_tuning(self, syn_np=None, ana_np=None, ana_queue=None, syn_packed=None,
+                   ana_packed=None):
         """Force launch variants (wf_set_tuning); None keeps the current one."""
         t = _Tuning()
         _check(lib().wf_get_tuning(self.handle, ctypes.byref(t)))
@@ -336,6 +339,10 @@ class Plan:
             t.ana_np[0], t.ana_np[1] = ana_np
         if ana_queue is not None:
             t.ana_queue = int(ana_queue)
+        if syn_packed is not None:
+            t.syn_packed = int(syn_packed)
+        if ana_packed is not None:
+            t.ana_packed = int(ana_packed)
         _check(lib().wf_set_tuning(self.handle, ctypes.byref(t)))
 
     def legendre_terms(self, L=None):
@@ -496,8 +503,9 @@ def wf_get_tuning(plan):
     return plan.tuning()
 
 
-def wf_set_tuning(plan, syn_np=None, ana_np=None, ana_queue=None):
-    return plan.set_tuning(syn_np, ana_np, ana_queue)
+def wf_set_tuning(plan, syn_np=None, ana_np=None, ana_queue=None, syn_packed=None,
+                  ana_packed=None):
+    return plan.set_tuning(syn_np, ana_np, ana_queue, syn_packed, ana_packed)
 
 
 def wf_destroy(plan):

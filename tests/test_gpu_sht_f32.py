@@ -95,7 +95,10 @@ def test_f32_full_size_sampled(torch_cuda, osht):
 VARIANTS = [dict(ana_np=(4, 2), ana_queue=0), dict(ana_np=(4, 4), ana_queue=0),
             dict(ana_np=(4, 8), ana_queue=0), dict(ana_np=(4, 16), ana_queue=0),
             dict(ana_np=(4, 4), ana_queue=1), dict(ana_np=(4, 8), ana_queue=1),
-            dict(syn_np=(2, 1)), dict(syn_np=(2, 4))]
+            dict(ana_np=(4, 4), ana_queue=0, ana_packed=1),
+            dict(ana_np=(4, 8), ana_queue=0, ana_packed=1),
+            dict(syn_np=(2, 1)), dict(syn_np=(2, 4)),
+            dict(syn_np=(2, 2), syn_packed=1), dict(syn_np=(2, 4), syn_packed=1)]
 
 
 @pytest.mark.parametrize("tuning", VARIANTS)
@@ -125,10 +128,14 @@ def test_tuning_report_and_bad_values(torch_cuda):
     with wf.Plan(16, 32, np.ones(33), autotune=1) as p:
         t = p.tuning()
         assert all(ms > 0 for ms in t["syn_ms"][1]) and all(ms > 0 for ms in t["ana_ms"][1])
-        assert t["ana_ms"][0][3] == -1.0  # FP64 has no 16-pair candidate
+        # FP64 has no 16-pair, queue or packed candidates
+        assert all(ms == -1.0 for ms in t["ana_ms"][0][3:])
+        assert all(ms == -1.0 for ms in t["syn_ms"][0][3:])
         assert t["ana_np"][1] in (2, 4, 8, 16) and t["ana_queue"] in (0, 1)
         for bad in (dict(syn_np=(3, 2)), dict(ana_np=(16, 8)), dict(ana_queue=2),
-                    dict(ana_np=(4, 2), ana_queue=1)):
+                    dict(ana_np=(4, 2), ana_queue=1),
+                    dict(ana_np=(4, 8), ana_queue=1, ana_packed=1),
+                    dict(syn_np=(2, 1), syn_packed=1)):
             with pytest.raises(wf.WFError):
                 p.set_tuning(**bad)
         assert p.tuning()["ana_np"] == t["ana_np"]

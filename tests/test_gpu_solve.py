@@ -213,16 +213,19 @@ def test_mixed_precision_reaches_fp64_fixed_point(torch_cuda, osht, odm, nside, 
     assert st["fp_residual"] < 1e-6
 
 
-@pytest.mark.parametrize("ana_np,ana_queue", [(4, 1), (8, 1), (16, 0), (2, 0)])
+@pytest.mark.parametrize("ana_np,ana_queue,packed", [(4, 1, 0), (8, 1, 0), (16, 0, 0),
+                                                     (2, 0, 0), (8, 0, 1), (4, 0, 1)])
 def test_mixed_precision_variants_reach_fp64_fixed_point(torch_cuda, osht, odm, ana_np,
-                                                         ana_queue):
+                                                         ana_queue, packed):
     """The same check with the FP32 analysis forced to each launch variant
     (the queue-scheduled one included: its combine kernel carries the filter,
     the anchored-stage source and the Cauchy partial sums)."""
     torch = torch_cuda
     p, d = problem(osht, "lognormal", 16, 8)
-    alm, mp, st, tr = gpu_solve(torch, p, d, tuning={"ana_np": (4, ana_np),
-                                                     "ana_queue": ana_queue},
+    tuning = {"ana_np": (4, ana_np), "ana_queue": ana_queue, "ana_packed": packed}
+    if packed:
+        tuning.update(syn_np=(2, 2), syn_packed=1)
+    alm, mp, st, tr = gpu_solve(torch, p, d, tuning=tuning,
                                 precision=1, eps_final=1e-7, stop_rule=1)
     assert st["converged"] == 1
     Y = osht.ymatrix(p.nside, p.lmax)
