@@ -552,13 +552,16 @@ def run_kernel_case(args):
     a = torch.from_numpy(inputs.random_alm(np.random.default_rng(5),
                                            np.maximum(cl, 1e-30))).cuda()
     out = {}
-    with wf.Plan(ns, lm, cl) as p:
+    with wf.Plan(ns, lm, cl, autotune=1) as p:
         f32 = args.kernel_case == "legendre32"
         syn = p.alm2map_f32 if f32 else p.alm2map
         ana = p.map2alm_f32 if f32 else p.map2alm
         m = syn(a)
         b = ana(m)
         torch.cuda.synchronize()
+        # the timed launches sit in an NVTX range (profilers can select them
+        # with --nvtx-include "kernel_case/")
+        torch.cuda.nvtx.range_push("kernel_case")
         for name, fn, arg, o in (("synthesis", syn, a, m), ("analysis", ana, m, b)):
             ts = []
             for _ in range(args.reps):
@@ -570,7 +573,11 @@ def run_kernel_case(args):
                 torch.cuda.synchronize()
                 ts.append(e0.elapsed_time(e1))
             out[name + "_ms"] = min(ts)
+        torch.cuda.nvtx.range_pop()
         out["terms"] = p.legendre_terms()
+        t = p.tuning()
+        out["variants"] = {k: t[k] for k in ("syn_np", "syn_packed", "ana_np", "ana_queue",
+                                              "ana_packed")}
     print(json.dumps({"kernel_case": args.kernel_case, "nside": ns, **out}))
 
 
