@@ -83,6 +83,12 @@ typedef struct {
   int autotune;      /* 1: at plan creation, time the launch variants of the
                         Legendre kernels for this geometry and keep the
                         fastest (cached per nside, lmax; default 0) */
+  int anchor;        /* WF_PREC_MIXED: arithmetic of the anchor steps
+                        r = G(x_a) - x_a.  1 (default): the Legendre
+                        transforms in double-float (pairs of FP32, ~48-bit
+                        significand) on the FP32 pipe, ring FFTs in FP64;
+                        0: plain FP64.  The last stage's acceptance test
+                        and fp_residual always use plain FP64. */
 } wf_opts;
 
 /* Per-solve statistics. */
@@ -197,6 +203,13 @@ wf_status wf_map2alm(wf_plan_t plan, const double *map_dev, double *alm_dev);
  * error the mixed-precision solve works with. */
 wf_status wf_alm2map_f32(wf_plan_t plan, const double *alm_dev, double *map_dev);
 wf_status wf_map2alm_f32(wf_plan_t plan, const double *map_dev, double *alm_dev);
+
+/* The same transforms with the Legendre step in double-float (each value an
+ * unevaluated sum of two FP32 numbers, ~48-bit significand, run on the FP32
+ * pipe) and FP64 ring FFTs: the arithmetic of the mixed solver's anchor
+ * steps (opts.anchor = 1).  FP64 in and out; errors as wf_alm2map_f32. */
+wf_status wf_alm2map_df64(wf_plan_t plan, const double *alm_dev, double *map_dev);
+wf_status wf_map2alm_df64(wf_plan_t plan, const double *map_dev, double *alm_dev);
 
 /* Sizes of a plan. */
 long wf_npix(int nside);

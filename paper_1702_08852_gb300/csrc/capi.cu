@@ -72,7 +72,9 @@ static wf_status alloc_work(Plan &P) {
     int dev = 0;
     WF_CUDA(cudaGetDevice(&dev));
     WF_CUDA(cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, dev));
-    WF_CUDA(cudaMalloc(&P.ana_scratch, sizeof(float2) * tiles * P.nalm));
+    // 16 bytes per entry: FP32 complex for the FP32 kernels, FP64 complex
+    // for the double-float anchor analysis
+    WF_CUDA(cudaMalloc(&P.ana_scratch, sizeof(double2) * tiles * P.nalm));
     WF_CUDA(cudaMalloc(&P.ana_lstart, sizeof(int) * tiles * (P.lmax + 1)));
     WF_CUDA(cudaMalloc(&P.ana_counter, sizeof(int)));
     WF_CUDA(cudaMemsetAsync(P.ana_counter, 0, sizeof(int), P.stream));
@@ -104,6 +106,7 @@ static wf_status check_opts(const wf_opts &o) {
     return arg_error("wf: unknown precision");
   if (o.graph_chunk < 0 || o.graph_chunk > 4096)
     return arg_error("wf: graph_chunk out of range");
+  if (o.anchor != 0 && o.anchor != 1) return arg_error("wf: anchor must be 0 or 1");
   return WF_OK;
 }
 
@@ -126,6 +129,7 @@ void wf_opts_default(wf_opts *o) {
   o->band_limit = 1;
   o->graph_chunk = 0;
   o->refine_max = 8;
+  o->anchor = 1;
 }
 
 long wf_npix(int nside) { return 12L * nside * nside; }
@@ -333,6 +337,22 @@ wf_status wf_map2alm_f32(wf_plan_t plan, const double *map_dev, double *alm_dev)
   if (!plan) return arg_error("wf_map2alm_f32: plan is NULL");
   if (!alm_dev || !map_dev) return arg_error("wf_map2alm_f32: NULL buffer");
   WF_TRY(map2alm_f32(*plan, map_dev, alm_dev));
+  WF_CUDA(cudaStreamSynchronize(plan->stream));
+  return WF_OK;
+}
+
+wf_status wf_alm2map_df64(wf_plan_t plan, const double *alm_dev, double *map_dev) {
+  if (!plan) return arg_error("wf_alm2map_df64: plan is NULL");
+  if (!alm_dev || !map_dev) return arg_error("wf_alm2map_df64: NULL buffer");
+  WF_TRY(alm2map_df64(*plan, alm_dev, map_dev));
+  WF_CUDA(cudaStreamSynchronize(plan->stream));
+  return WF_OK;
+}
+
+wf_status wf_map2alm_df64(wf_plan_t plan, const double *map_dev, double *alm_dev) {
+  if (!plan) return arg_error("wf_map2alm_df64: plan is NULL");
+  if (!alm_dev || !map_dev) return arg_error("wf_map2alm_df64: NULL buffer");
+  WF_TRY(map2alm_df64(*plan, map_dev, alm_dev));
   WF_CUDA(cudaStreamSynchronize(plan->stream));
   return WF_OK;
 }

@@ -352,8 +352,10 @@ __device__ __forceinline__ void anal_chunk(T (&v)[32], int lc, int L, int m,
       else
         c = sc[l - m];
       if constexpr (X2) {
-        // rings (2 jp, 2 jp + 1) in packed pairs; the partial sums a, b hold
-        // the even / odd pair of each chunk of four rings
+        // rings (2 jp, 2 jp + 1) in packed pairs; with more than two pairs
+        // the partial sums a, b hold the even / odd pair of each group of
+        // four rings (shorter dependent chains), with two pairs one packed
+        // sum (fewer adds to merge)
         static_assert(sizeof(T) == 4 && NP % 2 == 0, "packed pairs are FP32, NP even");
         float ar0 = 0.f, ar1 = 0.f, ai0 = 0.f, ai1 = 0.f;
         float br0 = 0.f, br1 = 0.f, bi0 = 0.f, bi1 = 0.f;
@@ -374,7 +376,7 @@ __device__ __forceinline__ void anal_chunk(T (&v)[32], int lc, int L, int m,
           u1[j0] = w0;
           u1[j1] = w1;
           const bool ev = (jj & 1) == 0;
-          if ((jp & 1) == 0) {
+          if (NP <= 4 || (jp & 1) == 0) {
             fma2(ar0, ar1, w0, w1, ev ? pr[j0] : qr[j0], ev ? pr[j1] : qr[j1], ar0, ar1);
             fma2(ai0, ai1, w0, w1, ev ? pim[j0] : qim[j0], ev ? pim[j1] : qim[j1], ai0, ai1);
           } else {
@@ -382,8 +384,13 @@ __device__ __forceinline__ void anal_chunk(T (&v)[32], int lc, int L, int m,
             fma2(bi0, bi1, w0, w1, ev ? pim[j0] : qim[j0], ev ? pim[j1] : qim[j1], bi0, bi1);
           }
         }
-        a_re = (ar0 + ar1) + (br0 + br1);
-        a_im = (ai0 + ai1) + (bi0 + bi1);
+        if constexpr (NP <= 4) {
+          a_re = ar0 + ar1;
+          a_im = ai0 + ai1;
+        } else {
+          a_re = (ar0 + ar1) + (br0 + br1);
+          a_im = (ai0 + ai1) + (bi0 + bi1);
+        }
       } else {
 #pragma unroll
       for (int j = 0; j < NP; ++j) {
@@ -396,7 +403,9 @@ __device__ __forceinline__ void anal_chunk(T (&v)[32], int lc, int L, int m,
         u1[j] = u;
         const T pre = (jj & 1) == 0 ? pr[j] : qr[j];
         const T pim_ = (jj & 1) == 0 ? pim[j] : qim[j];
-        if ((j & 1) == 0) {
+        // FP32: two partial sums (shorter dependent chains); FP64 is bound
+        // by its pipe's throughput, so one sum saves the merging adds
+        if (sizeof(T) == 8 || (j & 1) == 0) {
           a_re = fma(u, pre, a_re);
           a_im = fma(u, pim_, a_im);
         } else {
@@ -406,8 +415,13 @@ __device__ __forceinline__ void anal_chunk(T (&v)[32], int lc, int L, int m,
       }
       }
     }
-    v[2 * jj] = a_re + b_re;
-    v[2 * jj + 1] = a_im + b_im;
+    if constexpr (sizeof(T) == 8) {
+      v[2 * jj] = a_re;
+      v[2 * jj + 1] = a_im;
+    } else {
+      v[2 * jj] = a_re + b_re;
+      v[2 * jj + 1] = a_im + b_im;
+    }
   }
 }
 
@@ -754,6 +768,255 @@ __global__ void __launch_bounds__(ANA_THREADS)
   if (mode == ANA_FILTER) anal_partials(num, den, m, partials);
 }
 
+// ------------------------------------------- double-float (df64) kernels
+// The anchors of the mixed solver need the FP64 iteration map to ~1e-10, not
+// to FP64's last bit, and this part's FP64 pipe is ~1/64 of its FP32 pipe.
+// These kernels carry every value as an unevaluated sum hi + lo of two
+// floats (~48-bit significand: products by FMA two-product, sums by
+// two-sum, Dekker/Knuth), so the same transforms run on the FP32 pipe.
+// Inputs and outputs are FP64 (double2), the recurrence is the FP64 one
+// (u-convention, table rc), the analysis writes per-tile FP64 partial sums
+// that k_anal_combine<double> adds in tile order.  Every operation is an
+// explicit _rn intrinsic or fmaf, so nothing is contracted or reassociated.
+struct dd {
+  float hi, lo;
+};
+__device__ __forceinline__ dd dd_of(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double dd_val(dd a) { return (double)a.hi + (double)a.lo; }
+// (s, e) with |s| >= |e| -> normalised pair
+__device__ __forceinline__ dd dd_quick(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return dd_quick(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dd dd_sub(dd a, dd b) { return dd_add(a, {-b.hi, -b.lo}); }
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return dd_quick(p, e);
+}
+// acc += u x with acc kept unnormalised (hi carries the running sum, lo the
+// accumulated rounding errors); read it with dd_val
+__device__ __forceinline__ void dd_acc(dd &acc, dd u, dd x) {
+  const float p = __fmul_rn(u.hi, x.hi);
+  float e = fmaf(u.hi, x.hi, -p);
+  e = fmaf(u.hi, x.lo, fmaf(u.lo, x.hi, e));
+  const float s = __fadd_rn(acc.hi, p);
+  const float bb = __fsub_rn(s, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  acc.hi = s;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+}
+// u_l = c_l z u_{l-1} - u_{l-2}
+__device__ __forceinline__ dd dd_rec(dd c, dd z, dd u1, dd u2) {
+  return dd_sub(dd_mul(dd_mul(c, u1), z), u2);
+}
+
+constexpr int DD_NP_SYN = 2, DD_NP_ANA = 4;
+
+// synthesis: as k_legendre_synth (one CTA row per m, one thread per
+// DD_NP_SYN ring pairs), E/O parity sums in df64
+__global__ void __launch_bounds__(SYN_THREADS)
+    k_legendre_synth_dd(const RingPair *__restrict__ pairs, int npairs, int lmax,
+                        const double *__restrict__ rc, const int *__restrict__ seed_l,
+                        const double2 *__restrict__ seed_u, const double2 *__restrict__ xs,
+                        double2 *__restrict__ F, const SolverState *__restrict__ st,
+                        int lstatic) {
+  constexpr int NP = DD_NP_SYN;
+  const int m = blockIdx.y;
+  int L = lstatic;
+  if (st) {
+    if (st->done) return;
+    L = st->lcur;
+  }
+  if (m > L) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nl = L - m + 1;
+  dd *sxr = reinterpret_cast<dd *>(smraw);
+  dd *sxi = sxr + nl;
+  dd *sc = sxi + nl;
+  const long base = lm_index(lmax, m, m);
+  for (int j = threadIdx.x; j < nl; j += blockDim.x) {
+    const double2 xv = xs[base + j];
+    sxr[j] = dd_of(xv.x);
+    sxi[j] = dd_of(xv.y);
+    sc[j] = dd_of(rc[base + j]);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pair0 = (blockIdx.x * (SYN_THREADS / 32) + warp) * 32 * NP;
+  if (pair0 >= npairs) return;
+  const dd zero = {0.f, 0.f};
+  dd z[NP], u1[NP], u2[NP], s0[NP], s1[NP], er[NP], ei[NP], orr[NP], oi[NP];
+  int ls[NP];
+  int lmin = INT_MAX, linj = -1;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    const int k = pair0 + lane + 32 * j;
+    u1[j] = u2[j] = er[j] = ei[j] = orr[j] = oi[j] = zero;
+    z[j] = s0[j] = s1[j] = zero;
+    ls[j] = INT_MAX - 2;
+    if (k < npairs) {
+      z[j] = dd_of(pairs[k].z);
+      ls[j] = seed_l[(long)m * npairs + k];
+      const double2 su = seed_u[(long)m * npairs + k];
+      s0[j] = dd_of(su.x);
+      s1[j] = dd_of(su.y);
+    }
+    if (ls[j] <= L) {
+      lmin = min(lmin, ls[j]);
+      linj = max(linj, ls[j] + 1);
+    }
+  }
+  lmin = warp_min(lmin);
+  linj = warp_max(linj);
+  for (int l = lmin; l <= L; ++l) {
+    const dd c = sc[l - m], xr = sxr[l - m], xi = sxi[l - m];
+    const bool even = ((l - m) & 1) == 0;
+    const bool inj = l <= linj;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      dd u = dd_rec(c, z[j], u1[j], u2[j]);
+      if (inj) {
+        u = (l == ls[j]) ? s0[j] : u;
+        u = (l == ls[j] + 1) ? s1[j] : u;
+      }
+      u2[j] = u1[j];
+      u1[j] = u;
+      if (even) {
+        dd_acc(er[j], u, xr);
+        dd_acc(ei[j], u, xi);
+      } else {
+        dd_acc(orr[j], u, xr);
+        dd_acc(oi[j], u, xi);
+      }
+    }
+  }
+  const long stride = lmax + 1;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    const int k = pair0 + lane + 32 * j;
+    if (k >= npairs) continue;
+    const RingPair &rp = pairs[k];
+    const double e_r = dd_val(er[j]), e_i = dd_val(ei[j]);
+    const double o_r = dd_val(orr[j]), o_i = dd_val(oi[j]);
+    F[rp.ringN * stride + m] = make_double2(e_r + o_r, e_i + o_i);
+    if (rp.ringS >= 0) F[rp.ringS * stride + m] = make_double2(e_r - o_r, e_i - o_i);
+  }
+}
+
+// analysis: queue-scheduled like k_legendre_anal_q; per (m, tile of 32
+// DD_NP_ANA ring pairs) item, per chunk of LCHUNK l the lane's df64 sums are
+// rounded to FP64 and reduced across the warp in FP64
+__global__ void __launch_bounds__(ANA_THREADS)
+    k_legendre_anal_dd(const RingPair *__restrict__ pairs, int npairs, int lmax, long nalm,
+                       const double *__restrict__ rc, const int *__restrict__ seed_l,
+                       const double2 *__restrict__ seed_u, const double2 *__restrict__ G,
+                       double *__restrict__ scratch, int *__restrict__ lstart,
+                       int *__restrict__ counter, const SolverState *__restrict__ st,
+                       int lstatic) {
+  constexpr int NP = DD_NP_ANA;
+  int L = lstatic;
+  if (st) {
+    if (st->done) return;
+    L = st->lcur;
+  }
+  if (L < 0) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  dd *sc = reinterpret_cast<dd *>(smraw) + (long)warp * (lmax + 1);
+  constexpr int TP = 32 * NP;
+  const int ntiles = (npairs + TP - 1) / TP;
+  const int nitems = (L + 1) * ntiles;
+  const long stride = lmax + 1;
+  const dd zero = {0.f, 0.f};
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(counter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= nitems) break;
+    const int m = item / ntiles, tile = item - m * ntiles;
+    const long base = lm_index(lmax, m, m);
+    const int pair0 = tile * TP;
+    dd z[NP], u1[NP], u2[NP], s0[NP], s1[NP], pr[NP], pim[NP], qr[NP], qim[NP];
+    int ls[NP];
+    int lmin = INT_MAX, linj = -1;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const int k = pair0 + lane + 32 * j;
+      u1[j] = u2[j] = z[j] = s0[j] = s1[j] = pr[j] = pim[j] = qr[j] = qim[j] = zero;
+      ls[j] = INT_MAX - 2;
+      if (k < npairs) {
+        const RingPair &rp = pairs[k];
+        z[j] = dd_of(rp.z);
+        ls[j] = seed_l[(long)m * npairs + k];
+        const double2 su = seed_u[(long)m * npairs + k];
+        s0[j] = dd_of(su.x);
+        s1[j] = dd_of(su.y);
+        const double2 gn = G[rp.ringN * stride + m];
+        double2 gs = make_double2(0.0, 0.0);
+        if (rp.ringS >= 0) gs = G[rp.ringS * stride + m];
+        pr[j] = dd_of(gn.x + gs.x);
+        pim[j] = dd_of(gn.y + gs.y);
+        qr[j] = dd_of(gn.x - gs.x);
+        qim[j] = dd_of(gn.y - gs.y);
+      }
+      if (ls[j] <= L) {
+        lmin = min(lmin, ls[j]);
+        linj = max(linj, ls[j] + 1);
+      }
+    }
+    lmin = warp_min(lmin);
+    linj = warp_max(linj);
+    const int lc0 = lmin <= L ? m + ((lmin - m) / LCHUNK) * LCHUNK : L + 1;
+    if (lane == 0) lstart[(long)m * ntiles + tile] = lc0;
+    if (lmin > L) continue;
+    __syncwarp();
+    for (int j = lane; j <= L - m; j += 32) sc[j] = dd_of(rc[base + j]);
+    __syncwarp();
+    double *out = scratch + 2 * ((long)tile * nalm + base - m);  // out[2 l + re/im]
+    for (int lc = lc0; lc <= L; lc += LCHUNK) {
+      double v[32];
+      const bool inj = lc <= linj;
+#pragma unroll
+      for (int jj = 0; jj < LCHUNK; ++jj) {
+        const int l = lc + jj;
+        dd ar = zero, ai = zero;
+        if (l <= L) {
+          const dd c = sc[l - m];
+          const bool even = (jj & 1) == 0;  // lc - m is a multiple of LCHUNK
+#pragma unroll
+          for (int j = 0; j < NP; ++j) {
+            dd u = dd_rec(c, z[j], u1[j], u2[j]);
+            if (inj) {
+              u = (l == ls[j]) ? s0[j] : u;
+              u = (l == ls[j] + 1) ? s1[j] : u;
+            }
+            u2[j] = u1[j];
+            u1[j] = u;
+            dd_acc(ar, u, even ? pr[j] : qr[j]);
+            dd_acc(ai, u, even ? pim[j] : qim[j]);
+          }
+        }
+        v[2 * jj] = dd_val(ar);
+        v[2 * jj + 1] = dd_val(ai);
+      }
+      const double tot = transpose_reduce32<double>(v, lane);
+      const int l = lc + (lane >> 1);
+      if (l <= L) out[2 * l + (lane & 1)] = tot;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ launch
 template <typename T2>
 struct Kernels;
@@ -882,6 +1145,50 @@ wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
   return WF_OK;
 }
 
+// double-float transforms for the anchors of the mixed solver (FP64 in and
+// out; see the kernels above)
+wf_status launch_legendre_synth_dd(const Plan &P, const double2 *xs, double2 *F,
+                                   const SolverState *st, int lstatic) {
+  const size_t smem = 3 * sizeof(dd) * (P.lmax + 1);
+  const int pairs_per_cta = SYN_THREADS * DD_NP_SYN;
+  dim3 grid((P.npairs + pairs_per_cta - 1) / pairs_per_cta, P.lmax + 1);
+  ++P.nlaunch;
+  k_legendre_synth_dd<<<grid, SYN_THREADS, smem, P.stream>>>(
+      P.pairs, P.npairs, P.lmax, P.rc, P.seed_l, P.seed_u, xs, F, st, lstatic);
+  WF_CUDA(cudaGetLastError());
+  return WF_OK;
+}
+
+wf_status launch_legendre_anal_dd(const Plan &P, const double2 *G, double2 *x,
+                                  const SolverState *st, int mode, int lstatic,
+                                  const double2 *src, double2 *xs_out) {
+  const size_t smem = sizeof(dd) * (P.lmax + 1) * ANA_WARPS;
+  const int ntiles = (P.npairs + 32 * DD_NP_ANA - 1) / (32 * DD_NP_ANA);
+  // one resident wave (occupancy queried once; the anchor steps that call
+  // this are plain launches, never captured)
+  static std::atomic<int> per_sm_cache{0};
+  int per_sm = per_sm_cache.load();
+  if (per_sm == 0) {
+    int n = 0;
+    WF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_legendre_anal_dd,
+                                                          ANA_THREADS, smem));
+    per_sm = std::max(1, std::min(n, ANA_Q_CTAS_PER_SM));
+    per_sm_cache.store(per_sm);
+  }
+  double *scratch = reinterpret_cast<double *>(P.ana_scratch);
+  ++P.nlaunch;
+  k_legendre_anal_dd<<<P.num_sms * per_sm, ANA_THREADS, smem, P.stream>>>(
+      P.pairs, P.npairs, P.lmax, P.nalm, P.rc, P.seed_l, P.seed_u, G, scratch,
+      P.ana_lstart, P.ana_counter, st, lstatic);
+  WF_CUDA(cudaGetLastError());
+  ++P.nlaunch;
+  k_anal_combine<double><<<P.lmax + 1, ANA_THREADS, 0, P.stream>>>(
+      P.lmax, P.nalm, ntiles, scratch, P.ana_lstart, P.ana_counter, P.rg, P.cl_d, P.omega,
+      x, P.partials, src, xs_out, st, mode, lstatic);
+  WF_CUDA(cudaGetLastError());
+  return WF_OK;
+}
+
 template <typename T, int NP, bool X2 = false>
 static cudaError_t set_big_smem_synth(int big) {
   return cudaFuncSetAttribute(k_legendre_synth<T, NP, X2>,
@@ -913,6 +1220,10 @@ wf_status init_legendre_attributes() {
   WF_CUDA((set_big_smem_synth<float, 4, true>(big)));
   WF_CUDA((set_big_smem_anal<float, 4, true>(big)));
   WF_CUDA((set_big_smem_anal<float, 8, true>(big)));
+  WF_CUDA(cudaFuncSetAttribute(k_legendre_synth_dd,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_dd,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_q<float, 4>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_q<float, 8>,

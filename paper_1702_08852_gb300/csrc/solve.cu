@@ -329,6 +329,23 @@ wf_status map2alm_f32(Plan &P, const double *map, double *alm) {
   return WF_OK;
 }
 
+wf_status alm2map_df64(Plan &P, const double *alm, double *map) {
+  const double2 *a = reinterpret_cast<const double2 *>(alm);
+  WF_TRY(launch_prescale<double2>(P, a, P.xs64));
+  WF_TRY(launch_legendre_synth_dd(P, P.xs64, P.F64, nullptr, P.lmax));
+  WF_TRY(launch_ring<double2>(P, RING_SYNTH, P.F64, nullptr, nullptr, map, nullptr,
+                              P.lmax));
+  return WF_OK;
+}
+
+wf_status map2alm_df64(Plan &P, const double *map, double *alm) {
+  WF_TRY(launch_ring<double2>(P, RING_ANALYSIS, nullptr, P.G64, map, nullptr, nullptr,
+                              P.lmax));
+  WF_TRY(launch_legendre_anal_dd(P, P.G64, reinterpret_cast<double2 *>(alm), nullptr,
+                                 ANA_PLAIN, P.lmax));
+  return WF_OK;
+}
+
 // ---------------------------------------------------------------- solve
 static int band_host(const std::vector<double> &cl, double mu, double omega) {
   int b = -1;
@@ -551,8 +568,11 @@ __global__ void k_alm_add(double2 *x, const double2 *y, long n) {
 
 // One FP64 iteration map of stage (xi, mu) with band L: gx = G(x); returns
 // ||G(x) - x||^2 in *num.  (Defaults: the last stage, full band.)
+// One iteration map of stage (xi, mu, band L) from x into gx, and the
+// squared step norm.  dd: the Legendre transforms in double-float (the
+// anchors of a mixed solve with opts.anchor = 1); else plain FP64.
 static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
-                           double xi, double mu, int L) {
+                           double xi, double mu, int L, bool dd = false) {
   SolverState s = initial_state(P);
   s.xi = xi;
   s.mu = mu;
@@ -564,10 +584,16 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
   WF_CUDA(cudaMemcpyAsync(gx, x, sizeof(double2) * P.nalm, cudaMemcpyDeviceToDevice,
                           P.stream));
   WF_TRY(launch_prescale<double2>(P, x, P.xs64));
-  WF_TRY(launch_legendre_synth<double2>(P, P.xs64, P.F64, nullptr, std::max(L, 0)));
+  if (dd)
+    WF_TRY(launch_legendre_synth_dd(P, P.xs64, P.F64, nullptr, std::max(L, 0)));
+  else
+    WF_TRY(launch_legendre_synth<double2>(P, P.xs64, P.F64, nullptr, std::max(L, 0)));
   WF_TRY(launch_ring<double2>(P, RING_FUSED, P.F64, P.G64, P.dmap, nullptr, P.state,
                               P.lmax));
-  WF_TRY(launch_legendre_anal<double2>(P, P.G64, gx, P.state, ANA_FILTER, P.lmax));
+  if (dd)
+    WF_TRY(launch_legendre_anal_dd(P, P.G64, gx, P.state, ANA_FILTER, P.lmax));
+  else
+    WF_TRY(launch_legendre_anal<double2>(P, P.G64, gx, P.state, ANA_FILTER, P.lmax));
   std::vector<double> part(2 * (P.lmax + 1));
   WF_CUDA(cudaMemcpyAsync(part.data(), P.partials, sizeof(double) * part.size(),
                           cudaMemcpyDeviceToHost, P.stream));
@@ -717,7 +743,8 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
     while (anchored && reanchors <= MAX_REANCHORS && cycles <= P.opts.refine_max) {
       const SolverState stage = h;  // stage parameters of this anchor
       double num = 0.0, xn = 0.0;
-      WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num, stage.xi, stage.mu, stage.lcur));
+      WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num, stage.xi, stage.mu, stage.lcur,
+                       P.opts.anchor == 1));
       WF_TRY(alm_dot(P, P.xacc, P.xacc, nullptr, &xn));
       ++P.nlaunch;
       k_make_source<<<P.lmax + 1, 128, 0, P.stream>>>(P.xtmp, P.xacc, P.cl_d, stage.xi,

@@ -212,6 +212,15 @@ wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
                                const SolverState *st, int mode, int lstatic,
                                const double2 *src = nullptr, T2 *xs_out = nullptr);
 
+// Double-float (pairs of FP32) Legendre transforms with FP64 inputs and
+// outputs, for the anchor steps of the mixed solver (legendre.cu): the same
+// contracts as launch_legendre_synth<double2> / launch_legendre_anal<double2>.
+wf_status launch_legendre_synth_dd(const Plan &P, const double2 *xs, double2 *F,
+                                   const SolverState *st, int lstatic);
+wf_status launch_legendre_anal_dd(const Plan &P, const double2 *G, double2 *x,
+                                  const SolverState *st, int mode, int lstatic,
+                                  const double2 *src = nullptr, double2 *xs_out = nullptr);
+
 // Ring transforms (ringfft.cu).  Modes:
 enum RingMode {
   RING_SYNTH = 0,     // F -> map (write s)
@@ -251,6 +260,8 @@ wf_status alm2map(Plan &P, const double *alm, double *map);
 wf_status map2alm(Plan &P, const double *map, double *alm);
 wf_status alm2map_f32(Plan &P, const double *alm, double *map);
 wf_status map2alm_f32(Plan &P, const double *map, double *alm);
+wf_status alm2map_df64(Plan &P, const double *alm, double *map);
+wf_status map2alm_df64(Plan &P, const double *map, double *alm);
 wf_status legendre_terms(Plan &P, int L, double *terms);
 SolverState initial_state(const Plan &P);
 wf_status residual_static(Plan &P, const double *d, const double *alm, double *res_wf,

@@ -35,7 +35,8 @@ class wf_opts(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("stop_rule", ctypes.c_int),
                 ("precision", ctypes.c_int), ("band_limit", ctypes.c_int),
                 ("graph_chunk", ctypes.c_int), ("refine_max", ctypes.c_int),
-                ("timing", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("anchor", ctypes.c_int)]
 
 
 class wf_stats(ctypes.Structure):
@@ -88,6 +89,8 @@ def lib():
             "wf_map2alm": (I, [_P, _P, _P]),
             "wf_alm2map_f32": (I, [_P, _P, _P]),
             "wf_map2alm_f32": (I, [_P, _P, _P]),
+            "wf_alm2map_df64": (I, [_P, _P, _P]),
+            "wf_map2alm_df64": (I, [_P, _P, _P]),
             "wf_npix": (ctypes.c_long, [I]),
             "wf_nalm": (ctypes.c_long, [I]),
             "wf_trace": (I, [_P, ctypes.POINTER(I), _P, _P, _P, _P]),
@@ -300,6 +303,24 @@ class Plan:
                                     _dev_ptr(out, torch.complex128, self.nalm, "alm")))
         return out
 
+    def alm2map_df64(self, alm, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.npix, dtype=torch.float64, device=alm.device)
+        _check(lib().wf_alm2map_df64(self.handle,
+                                     _dev_ptr(alm, torch.complex128, self.nalm, "alm"),
+                                     _dev_ptr(out, torch.float64, self.npix, "map")))
+        return out
+
+    def map2alm_df64(self, m, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.nalm, dtype=torch.complex128, device=m.device)
+        _check(lib().wf_map2alm_df64(self.handle,
+                                     _dev_ptr(m, torch.float64, self.npix, "map"),
+                                     _dev_ptr(out, torch.complex128, self.nalm, "alm")))
+        return out
+
     def trace(self, cap=1 << 20):
         n = ctypes.c_int(cap)
         st = np.empty(cap, dtype=np.int32)
@@ -477,6 +498,22 @@ def wf_alm2map(plan, alm, out=None):
 
 def wf_map2alm(plan, m, out=None):
     return plan.map2alm(m, out)
+
+
+def wf_alm2map_f32(plan, alm, out=None):
+    return plan.alm2map_f32(alm, out)
+
+
+def wf_map2alm_f32(plan, m, out=None):
+    return plan.map2alm_f32(m, out)
+
+
+def wf_alm2map_df64(plan, alm, out=None):
+    return plan.alm2map_df64(alm, out)
+
+
+def wf_map2alm_df64(plan, m, out=None):
+    return plan.map2alm_df64(m, out)
 
 
 def wf_set_noise(plan, noise_var, mask=None):

@@ -97,3 +97,55 @@ def test_full_size_sampled(torch_cuda, osht, nside):
     ref = om * osht.adjoint_modes(m, nside, lmax, ls[sel], ms[sel])
     scale = np.sqrt(np.mean(np.abs(b) ** 2))
     assert np.max(np.abs(b[sel] - ref)) <= 1e-11 * scale
+
+
+def tol_df64(nside, lmax):
+    """Double-float Legendre step: the bound of the FP32 kernels' random-walk
+    phase model with the double-float unit roundoff 2^-44 (its sums carry the
+    rounding of one FP32 addition in the low part), relative to the largest
+    output, floored at the FP64 tolerance."""
+    return max(TOL, 2.0 ** -44 * (64.0 + 2.0 * nside * np.sqrt(lmax + 1.0)))
+
+
+@pytest.mark.parametrize("nside,lmax", [(1, 2), (4, 11), (8, 16), (32, 95), (64, 128),
+                                        (160, 320)])
+def test_df64_transforms_match_oracle(torch_cuda, osht, nside, lmax):
+    """The double-float transforms of the anchor steps against the oracle."""
+    torch = torch_cuda
+    from paper_1702_08852_gb300 import wf
+    a = rand_alm(lmax, 500 + nside + lmax)
+    ref = osht.alm2map(a, nside, lmax)
+    m = np.random.default_rng(3 * nside + lmax).standard_normal(12 * nside * nside)
+    refb = osht.map2alm(m, nside, lmax)
+    with wf.Plan(nside, lmax, np.ones(lmax + 1)) as p:
+        got = p.alm2map_df64(torch.from_numpy(a).cuda()).cpu().numpy()
+        gotb = p.map2alm_df64(torch.from_numpy(m).cuda()).cpu().numpy()
+        gotb2 = p.map2alm_df64(torch.from_numpy(m).cuda()).cpu().numpy()
+    t = tol_df64(nside, lmax)
+    assert np.max(np.abs(got - ref)) <= t * np.max(np.abs(ref))
+    assert np.max(np.abs(gotb - refb)) <= t * np.max(np.abs(refb))
+    assert np.array_equal(gotb, gotb2)
+
+
+def test_df64_full_size_sampled(torch_cuda, osht):
+    """Nside 1024, lmax 2048: sampled pixels (polar rings included) and
+    coefficients of the double-float transforms, one by one by the oracle."""
+    torch = torch_cuda
+    from paper_1702_08852_gb300 import wf, inputs
+    nside, lmax = 1024, 2048
+    npix = 12 * nside * nside
+    cl = inputs.cl_spectrum(lmax, nside)
+    rng = np.random.default_rng(93)
+    a = inputs.random_alm(rng, np.maximum(cl, 1e-12))
+    with wf.Plan(nside, lmax, cl) as p:
+        mp = p.alm2map_df64(torch.from_numpy(a).cuda()).cpu().numpy()
+        pix = np.concatenate([rng.integers(0, npix, 30), [0, 3, 40, npix - 1, npix // 2]])
+        ref = osht.alm2map_pixels(a, nside, lmax, pix)
+        assert np.max(np.abs(mp[pix] - ref)) <= tol_df64(nside, lmax) * np.max(np.abs(mp))
+        m = rng.standard_normal(npix)
+        b = p.map2alm_df64(torch.from_numpy(m).cuda()).cpu().numpy()
+    ls, ms = inputs.lm_of_slots(lmax)
+    sel = np.concatenate([rng.integers(0, len(ls), 10), [0, inputs.nalm(lmax) - 1, 2048]])
+    om = 4 * np.pi / npix
+    ref = om * osht.adjoint_modes(m, nside, lmax, ls[sel], ms[sel])
+    assert np.max(np.abs(b[sel] - ref)) <= tol_df64(nside, lmax) * np.max(np.abs(b))

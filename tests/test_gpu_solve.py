@@ -194,15 +194,20 @@ def test_plan_rejects_bad_noise(torch_cuda):
     wf.Plan(nside, lmax, np.ones(lmax + 1), nv, mk).close()
 
 
-@pytest.mark.parametrize("nside,kind,seed", [(16, "lognormal", 8), (32, "lognormal", 1000),
-                                             (32, "scan", 9)])
-def test_mixed_precision_reaches_fp64_fixed_point(torch_cuda, osht, odm, nside, kind, seed):
-    """FP32 transforms for the cooling stages, FP64-anchored last stage: the
-    result matches the FP64 fixed point (dense solve) to 1e-6 relative L2."""
+@pytest.mark.parametrize("nside,kind,seed,anchor", [(16, "lognormal", 8, 1),
+                                                    (16, "lognormal", 8, 0),
+                                                    (32, "lognormal", 1000, 1),
+                                                    (32, "scan", 9, 1)])
+def test_mixed_precision_reaches_fp64_fixed_point(torch_cuda, osht, odm, nside, kind, seed,
+                                                  anchor):
+    """FP32 transforms for the cooling stages, anchored later stages (anchor
+    steps in double-float or plain FP64): the result matches the FP64 fixed
+    point (dense solve) to 1e-6 relative L2."""
     torch = torch_cuda
     kw = {"discs": 40} if kind == "scan" else {}
     p, d = problem(osht, kind, nside, seed, **kw)
-    alm, mp, st, tr = gpu_solve(torch, p, d, precision=1, eps_final=1e-7, stop_rule=1)
+    alm, mp, st, tr = gpu_solve(torch, p, d, precision=1, eps_final=1e-7, stop_rule=1,
+                                anchor=anchor)
     assert st["converged"] == 1
     assert st["refinements"] >= 1
     Y = osht.ymatrix(p.nside, p.lmax)
