@@ -23,6 +23,8 @@
 // X_k = conj(w_k) sum_j (x_j conj(w_j)) w_{k-j}, w_j = e^{i pi j^2 / n}, as a
 // length-M circular convolution (M = 2^p >= 2n - 1) by DIF -> pointwise
 // product with the kernel spectrum (stored bit-reversed) -> inverse DIT.
+#include <limits.h>
+
 #include "wf_internal.cuh"
 
 namespace wf {
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
            const double *__restrict__ nvar, const T2 *__restrict__ tw, int Mmax,
            const T2 *__restrict__ chirp_all, const T2 *__restrict__ bhat_all,
            const SolverState *__restrict__ st, int lstatic, int reverse,
-           const float *__restrict__ in32, const float *__restrict__ nv32) {
+           const float *__restrict__ in32, const float *__restrict__ nv32, int red_ofs) {
   typedef typename CT<T2>::T T;
   // reverse: the polar rings grow with the pair index; taking the largest
   // first keeps the small ones for the tail of the launch
@@ -314,16 +316,62 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
   if (MODE != RING_ANALYSIS) {
     const T2 *FN = F + rp.ringN * stride;
     const T2 *FS = south ? F + rp.ringS * stride : nullptr;
-    #pragma unroll 4
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      T2 cN = zero, cS = zero;
-      if (Lf >= 0 && (k <= Lf || n - k <= Lf)) {
-        const T2 ph = ring_phase<T2>(k, rp.phi_num, rp.phi_den, tstep, tw);
-        cN = fold(FN, k, n, Lf, sgn, ph);
-        if (south) cS = fold(FS, k, n, Lf, sgn, ph);
+    if (n < (int)blockDim.x) {
+      // small rings (n < threads): each k's sums over j are split across
+      // P = threads / n threads (j = part mod P), whose partials are added
+      // in part order -- all threads load, none walks (L+1)/n terms alone
+      T2 *red = buf + red_ofs;  // [2][blockDim]: north, south partials
+      const int P = blockDim.x / n, k = threadIdx.x % n, part = threadIdx.x / n;
+      if (part < P) {
+        T2 pN = zero, pS = zero;
+        if (Lf >= 0) {
+          for (int j = part; k + j * n <= Lf; j += P) {  // m = k + j n
+            const T s = (sgn < (T)0 && (j & 1)) ? (T)-1 : (T)1;
+            const T2 f = FN[k + j * n];
+            pN = CT<T2>::mk(pN.x + s * f.x, pN.y + s * f.y);
+            if (south) {
+              const T2 g = FS[k + j * n];
+              pS = CT<T2>::mk(pS.x + s * g.x, pS.y + s * g.y);
+            }
+          }
+          for (int j = 1 + part; j * n - k <= Lf; j += P) {  // m = j n - k, conj
+            const T s = (sgn < (T)0 && (j & 1)) ? (T)-1 : (T)1;
+            const T2 f = FN[j * n - k];
+            pN = CT<T2>::mk(pN.x + s * f.x, pN.y - s * f.y);
+            if (south) {
+              const T2 g = FS[j * n - k];
+              pS = CT<T2>::mk(pS.x + s * g.x, pS.y - s * g.y);
+            }
+          }
+        }
+        red[threadIdx.x] = pN;
+        red[blockDim.x + threadIdx.x] = pS;
       }
-      const T2 Zk = CT<T2>::mk(cN.x - cS.y, cN.y + cS.x);  // cN + i cS
-      buf[k] = blue ? cmulc(cconj(Zk), chirp[k]) : Zk;
+      __syncthreads();
+      if ((int)threadIdx.x < n) {
+        T2 cN = zero, cS = zero;
+        for (int q = 0; q < P; ++q) {
+          cN = cadd(cN, red[q * n + k]);
+          cS = cadd(cS, red[blockDim.x + q * n + k]);
+        }
+        const T2 ph = ring_phase<T2>(k, rp.phi_num, rp.phi_den, tstep, tw);
+        cN = cmul(cN, ph);
+        cS = cmul(cS, ph);
+        const T2 Zk = CT<T2>::mk(cN.x - cS.y, cN.y + cS.x);  // cN + i cS
+        buf[k] = blue ? cmulc(cconj(Zk), chirp[k]) : Zk;
+      }
+    } else {
+      #pragma unroll 4
+      for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        T2 cN = zero, cS = zero;
+        if (Lf >= 0 && (k <= Lf || n - k <= Lf)) {
+          const T2 ph = ring_phase<T2>(k, rp.phi_num, rp.phi_den, tstep, tw);
+          cN = fold(FN, k, n, Lf, sgn, ph);
+          if (south) cS = fold(FS, k, n, Lf, sgn, ph);
+        }
+        const T2 Zk = CT<T2>::mk(cN.x - cS.y, cN.y + cS.x);  // cN + i cS
+        buf[k] = blue ? cmulc(cconj(Zk), chirp[k]) : Zk;
+      }
     }
     if (blue)
       for (int k = n + threadIdx.x; k < M; k += blockDim.x) buf[k] = zero;
@@ -404,20 +452,28 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
   T2 *GS = south ? G + rp.ringS * stride : nullptr;
   const T half = (T)0.5;
   const int kmax = min(n - 1, Lg);
-  #pragma unroll 4
-  for (int k = threadIdx.x; k <= kmax; k += blockDim.x) {
-    const int kk = k == 0 ? 0 : n - k;
-    const T2 X = buf[k], Xc = cconj(buf[kk]);
-    const T2 ph = cconj(ring_phase<T2>(k, rp.phi_num, rp.phi_den, tstep, tw));
-    const T2 tN = cmul(CT<T2>::mk(half * (X.x + Xc.x), half * (X.y + Xc.y)), ph);
-    // (X - Xc) / (2i)
-    const T2 dlt = csub(X, Xc);
-    const T2 tS = cmul(CT<T2>::mk(half * dlt.y, -half * dlt.x), ph);
-    T s = (T)1;
-    for (int m = k; m <= Lg; m += n) {
-      GN[m] = CT<T2>::mk(s * tN.x, s * tN.y);
-      if (south) GS[m] = CT<T2>::mk(s * tS.x, s * tS.y);
-      s *= sgn;
+  // small rings: the copies m = k + j n of each k are split across
+  // P = threads / n threads, as in the fold
+  const int P = n < (int)blockDim.x ? (int)blockDim.x / n : 1;
+  const int kstep = n < (int)blockDim.x ? n : (int)blockDim.x;
+  const int part = n < (int)blockDim.x ? (int)threadIdx.x / n : 0;
+  if (part < P) {
+    #pragma unroll 4
+    for (int k = (n < (int)blockDim.x ? (int)threadIdx.x % n : (int)threadIdx.x);
+         k <= kmax; k += kstep) {
+      const int kk = k == 0 ? 0 : n - k;
+      const T2 X = buf[k], Xc = cconj(buf[kk]);
+      const T2 ph = cconj(ring_phase<T2>(k, rp.phi_num, rp.phi_den, tstep, tw));
+      const T2 tN = cmul(CT<T2>::mk(half * (X.x + Xc.x), half * (X.y + Xc.y)), ph);
+      // (X - Xc) / (2i)
+      const T2 dlt = csub(X, Xc);
+      const T2 tS = cmul(CT<T2>::mk(half * dlt.y, -half * dlt.x), ph);
+      for (int j = part; k + j * n <= Lg; j += P) {
+        const int m = k + j * n;
+        const T s = (sgn < (T)0 && (j & 1)) ? (T)-1 : (T)1;
+        GN[m] = CT<T2>::mk(s * tN.x, s * tN.y);
+        if (south) GS[m] = CT<T2>::mk(s * tS.x, s * tS.y);
+      }
     }
   }
 }
@@ -452,16 +508,22 @@ static wf_status launch_ring_mode(const Plan &P, const T2 *F, T2 *G,
   for (int g = 0; g < 2; ++g) {
     const int b = groups[g][0], e = groups[g][1];
     if (e <= b) continue;
-    int Mg = 1;
-    for (int k = b; k < e; ++k) Mg = std::max(Mg, P.pairs_h[k].fftM);
-    const size_t smem = sizeof(T2) * Mg;
+    int Mg = 1, nmin = INT_MAX;
+    for (int k = b; k < e; ++k) {
+      Mg = std::max(Mg, P.pairs_h[k].fftM);
+      nmin = std::min(nmin, P.pairs_h[k].nphi);
+    }
     const int threads = Mg >= 8192 ? RING_THREADS_BIG : RING_THREADS;
+    // rings with fewer pixels than threads fold through a partial-sum area
+    // of 2 x threads entries placed after the FFT buffer
+    const int red_ofs = nmin < threads ? Mg : 0;
+    const size_t smem = sizeof(T2) * (Mg + (nmin < threads ? 2 * threads : 0));
     cudaStream_t s = (fork && g == 1) ? P.side_stream : P.stream;
     ++P.nlaunch;
     kern<<<e - b, threads, smem, s>>>(
         P.pairs, b, P.lmax, F, G, in_map, out_map, P.nvar, Tables<T2>::tw(P),
         P.fftMmax, Tables<T2>::ch(P), Tables<T2>::bh(P), st, lstatic, g == 0, in32,
-        P.nvar32);
+        P.nvar32, red_ofs);
     WF_CUDA(cudaGetLastError());
   }
   if (fork) {
