@@ -18,7 +18,7 @@ namespace wf {
 namespace {
 struct Choice {
   int syn[2], ana[2], ana_queue, syn_x2, ana_x2;
-  float syn_ms[2][5], ana_ms[2][8];  // the timings the choice was made from
+  float syn_ms[2][5], ana_ms[2][9];  // the timings the choice was made from
 };
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, Choice> g_tune_cache;
@@ -105,14 +105,15 @@ wf_status autotune(Plan &P) {
     int pick_q = 0, pick_ax2 = 0;
     const int *cand = k ? ana_cand32 : ana_cand64;
     const int nc = k ? 4 : 3;
-    // FP32 also tries the queue-scheduled analysis (slots 4, 5) and the
-    // packed f32x2 one (slots 6, 7), each with 4 and 8 pairs per lane
-    const int ntot = k ? 8 : 3;
+    // FP32 also tries the queue-scheduled analysis (slots 4, 5: 4 and 8
+    // pairs per lane) and the packed f32x2 one (slots 6, 7, 8: 4, 8, 6)
+    const int ntot = k ? 9 : 3;
+    static const int x2_np[3] = {4, 8, 6};
     for (int i = 0; i < ntot && st == WF_OK; ++i) {
       const bool q = k && i >= 4 && i < 6, x2 = k && i >= 6;
       P.ana_queue = q ? 1 : 0;
       P.ana_x2 = x2 ? 1 : 0;
-      P.ana_np[k] = (q || x2) ? ((i & 1) ? 8 : 4) : cand[i];
+      P.ana_np[k] = q ? ((i & 1) ? 8 : 4) : x2 ? x2_np[i - 6] : cand[i];
       float ms = 0.f;
       st = k ? time_anal<float2>(P, P.G32, e0, e1, &ms)
              : time_anal<double2>(P, P.G64, e0, e1, &ms);

@@ -396,7 +396,7 @@ wf_status wf_get_tuning(wf_plan_t plan, wf_tuning *out) {
     out->syn_np[k] = plan->syn_np[k];
     out->ana_np[k] = plan->ana_np[k];
     for (int c = 0; c < 5; ++c) out->syn_ms[k][c] = plan->tune_syn_ms[k][c];
-    for (int c = 0; c < 8; ++c) out->ana_ms[k][c] = plan->tune_ana_ms[k][c];
+    for (int c = 0; c < 9; ++c) out->ana_ms[k][c] = plan->tune_ana_ms[k][c];
   }
   out->syn_packed = plan->syn_x2;
   out->ana_queue = plan->ana_queue;
@@ -422,9 +422,11 @@ wf_status wf_set_tuning(wf_plan_t plan, const wf_tuning *in) {
     return arg_error("wf_set_tuning: ana_queue, ana_packed, syn_packed must be 0 or 1");
   if (in->ana_queue && in->ana_packed)
     return arg_error("wf_set_tuning: ana_queue and ana_packed exclude each other");
-  if ((in->ana_queue || in->ana_packed) ? !one_of(in->ana_np[1], {4, 8})
-                                        : !one_of(in->ana_np[1], {2, 4, 8, 16}))
-    return arg_error("wf_set_tuning: FP32 ana_np must be 2, 4, 8 or 16 (queue, packed: 4 or 8)");
+  if (in->ana_queue ? !one_of(in->ana_np[1], {4, 8})
+                    : in->ana_packed ? !one_of(in->ana_np[1], {4, 6, 8})
+                                     : !one_of(in->ana_np[1], {2, 4, 8, 16}))
+    return arg_error("wf_set_tuning: FP32 ana_np must be 2, 4, 8 or 16 (queue: 4, 8; "
+                     "packed: 4, 6, 8)");
   if (in->syn_packed && !one_of(in->syn_np[1], {2, 4}))
     return arg_error("wf_set_tuning: packed FP32 synthesis needs syn_np 2 or 4");
   for (int k = 0; k < 2; ++k) {

@@ -1129,6 +1129,8 @@ wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
     if (P.ana_x2) {
       if (np == 4)
         anal_variant<T, 4, true>(P, G, x, st, mode, lstatic, src, xs_out);
+      else if (np == 6)
+        anal_variant<T, 6, true>(P, G, x, st, mode, lstatic, src, xs_out);
       else
         anal_variant<T, 8, true>(P, G, x, st, mode, lstatic, src, xs_out);
       WF_CUDA(cudaGetLastError());
@@ -1220,6 +1222,7 @@ wf_status init_legendre_attributes() {
   WF_CUDA((set_big_smem_synth<float, 4, true>(big)));
   WF_CUDA((set_big_smem_anal<float, 4, true>(big)));
   WF_CUDA((set_big_smem_anal<float, 8, true>(big)));
+  WF_CUDA((set_big_smem_anal<float, 6, true>(big)));
   WF_CUDA(cudaFuncSetAttribute(k_legendre_synth_dd,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_dd,

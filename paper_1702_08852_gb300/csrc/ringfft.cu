@@ -199,11 +199,11 @@ __device__ void bluestein(T2 *buf, int n, int M, const T2 *__restrict__ tw,
                           int Mmax, const T2 *__restrict__ chirp,
                           const T2 *__restrict__ bhat) {
   fft_dif<T2, false>(buf, M, tw, Mmax);
-  #pragma unroll 4
+  #pragma unroll 8
   for (int q = threadIdx.x; q < M; q += blockDim.x) buf[q] = cmul(buf[q], bhat[q]);
   __syncthreads();
   fft_dit<T2, true>(buf, M, tw, Mmax);
-  #pragma unroll 4
+  #pragma unroll 8
   for (int k = threadIdx.x; k < n; k += blockDim.x) buf[k] = cmulc(buf[k], chirp[k]);
   __syncthreads();
 }

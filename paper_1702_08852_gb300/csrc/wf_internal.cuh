@@ -128,8 +128,8 @@ struct Plan {
   int *ana_counter = nullptr;    // the queue's next item (reset by the combine)
   int num_sms = 0;
   float tune_syn_ms[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};
-  float tune_ana_ms[2][8] = {{-1, -1, -1, -1, -1, -1, -1, -1},
-                             {-1, -1, -1, -1, -1, -1, -1, -1}};
+  float tune_ana_ms[2][9] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1},
+                             {-1, -1, -1, -1, -1, -1, -1, -1, -1}};
 
   // FFT tables
   int fftMmax = 1;

@@ -97,6 +97,7 @@ VARIANTS = [dict(ana_np=(4, 2), ana_queue=0), dict(ana_np=(4, 4), ana_queue=0),
             dict(ana_np=(4, 4), ana_queue=1), dict(ana_np=(4, 8), ana_queue=1),
             dict(ana_np=(4, 4), ana_queue=0, ana_packed=1),
             dict(ana_np=(4, 8), ana_queue=0, ana_packed=1),
+            dict(ana_np=(4, 6), ana_queue=0, ana_packed=1),
             dict(syn_np=(2, 1)), dict(syn_np=(2, 4)),
             dict(syn_np=(2, 2), syn_packed=1), dict(syn_np=(2, 4), syn_packed=1)]
 
