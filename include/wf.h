@@ -252,20 +252,24 @@ wf_status wf_kernel_stats(wf_plan_t plan, int kernel, double *ms, long *launches
  *  ana_queue   FP32 analysis scheduling: 0 = one CTA per m, 1 = warps take
  *              (m, tile) items from a queue, then a per-m combine kernel.
  *  ana_packed  FP32 per-m analysis on packed f32x2 pairs (ana_np 4, 6, 8).
+ *  ana_global_acc  with ana_packed (ana_np 4, 6): the per-warp accumulators
+ *              in global scratch instead of shared memory (more CTAs/SM).
  *  syn_ms      candidates 1, 2, 4 pairs per thread, then (FP32) packed 2, 4:
  *              ms for two launches.
  *  ana_ms      candidates 2, 4, 8, 16 pairs per lane, then (FP32 only) queue
- *              4, 8 and packed 4, 8, 6: ms for two launches. */
+ *              4, 8, packed 4, 8, 6 and packed with global accumulators 4,
+ *              6: ms for two launches. */
 typedef struct {
-  int syn_np[2], syn_packed, ana_np[2], ana_queue, ana_packed;
-  float syn_ms[2][5], ana_ms[2][9];
+  int syn_np[2], syn_packed, ana_np[2], ana_queue, ana_packed, ana_global_acc;
+  float syn_ms[2][5], ana_ms[2][11];
 } wf_tuning;
 wf_status wf_get_tuning(wf_plan_t plan, wf_tuning *out);
 /* Set the launch variants (the int fields of *in; the ms fields are
  * ignored).  syn_np in {1, 2, 4}; ana_np in {2, 4, 8, 16} (FP64 {2, 4, 8});
  * ana_queue and the packed flags 0 or 1; ana_queue and ana_packed not both;
  * syn_packed needs syn_np[1] in {2, 4}; ana_queue needs ana_np[1] in {4, 8},
- * ana_packed in {4, 6, 8}.  The plan's captured iteration graphs are dropped and
+ * ana_packed in {4, 6, 8}; ana_global_acc needs ana_packed and ana_np[1] in
+ * {4, 6}.  The plan's captured iteration graphs are dropped and
  * re-captured on the next solve.  Errors: WF_ERR_ARG for NULL or a value
  * outside these sets (the plan is unchanged). */
 wf_status wf_set_tuning(wf_plan_t plan, const wf_tuning *in);

@@ -17,8 +17,8 @@ namespace wf {
 
 namespace {
 struct Choice {
-  int syn[2], ana[2], ana_queue, syn_x2, ana_x2;
-  float syn_ms[2][5], ana_ms[2][9];  // the timings the choice was made from
+  int syn[2], ana[2], ana_queue, syn_x2, ana_x2, ana_gacc;
+  float syn_ms[2][5], ana_ms[2][11];  // the timings the choice was made from
 };
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, Choice> g_tune_cache;
@@ -61,6 +61,7 @@ wf_status autotune(Plan &P) {
       P.ana_queue = it->second.ana_queue;
       P.syn_x2 = it->second.syn_x2;
       P.ana_x2 = it->second.ana_x2;
+      P.ana_gacc = it->second.ana_gacc;
       memcpy(P.tune_syn_ms, it->second.syn_ms, sizeof(P.tune_syn_ms));
       memcpy(P.tune_ana_ms, it->second.ana_ms, sizeof(P.tune_ana_ms));
       return WF_OK;
@@ -102,17 +103,19 @@ wf_status autotune(Plan &P) {
     P.syn_np[k] = pick;
     best = 1e30f;
     pick = P.ana_np[k];
-    int pick_q = 0, pick_ax2 = 0;
+    int pick_q = 0, pick_ax2 = 0, pick_ga = 0;
     const int *cand = k ? ana_cand32 : ana_cand64;
     const int nc = k ? 4 : 3;
     // FP32 also tries the queue-scheduled analysis (slots 4, 5: 4 and 8
-    // pairs per lane) and the packed f32x2 one (slots 6, 7, 8: 4, 8, 6)
-    const int ntot = k ? 9 : 3;
-    static const int x2_np[3] = {4, 8, 6};
+    // pairs per lane), the packed f32x2 one (slots 6, 7, 8: 4, 8, 6) and the
+    // packed one with global accumulators (slots 9, 10: 4, 6)
+    const int ntot = k ? 11 : 3;
+    static const int x2_np[5] = {4, 8, 6, 4, 6};
     for (int i = 0; i < ntot && st == WF_OK; ++i) {
-      const bool q = k && i >= 4 && i < 6, x2 = k && i >= 6;
+      const bool q = k && i >= 4 && i < 6, x2 = k && i >= 6, ga = k && i >= 9;
       P.ana_queue = q ? 1 : 0;
       P.ana_x2 = x2 ? 1 : 0;
+      P.ana_gacc = ga ? 1 : 0;
       P.ana_np[k] = q ? ((i & 1) ? 8 : 4) : x2 ? x2_np[i - 6] : cand[i];
       float ms = 0.f;
       st = k ? time_anal<float2>(P, P.G32, e0, e1, &ms)
@@ -123,11 +126,13 @@ wf_status autotune(Plan &P) {
         pick = P.ana_np[k];
         pick_q = P.ana_queue;
         pick_ax2 = P.ana_x2;
+        pick_ga = P.ana_gacc;
       }
     }
     P.ana_np[k] = pick;
     P.ana_queue = k ? pick_q : P.ana_queue;
     P.ana_x2 = k ? pick_ax2 : P.ana_x2;
+    P.ana_gacc = k ? pick_ga : P.ana_gacc;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -141,6 +146,7 @@ wf_status autotune(Plan &P) {
   c.ana_queue = P.ana_queue;
   c.syn_x2 = P.syn_x2;
   c.ana_x2 = P.ana_x2;
+  c.ana_gacc = P.ana_gacc;
   memcpy(c.syn_ms, P.tune_syn_ms, sizeof(c.syn_ms));
   memcpy(c.ana_ms, P.tune_ana_ms, sizeof(c.ana_ms));
   g_tune_cache[key] = c;

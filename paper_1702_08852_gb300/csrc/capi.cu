@@ -1,5 +1,6 @@
 // capi.cu -- the extern "C" entry points declared in include/wf.h:
 // argument checking, plan lifetime, error strings.
+#include <algorithm>
 #include <initializer_list>
 #include <math.h>
 #include <string.h>
@@ -74,7 +75,8 @@ static wf_status alloc_work(Plan &P) {
     WF_CUDA(cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, dev));
     // 16 bytes per entry: FP32 complex for the FP32 kernels, FP64 complex
     // for the double-float anchor analysis
-    WF_CUDA(cudaMalloc(&P.ana_scratch, sizeof(double2) * tiles * P.nalm));
+    // (and the packed analysis' global accumulators: 4 warps x FP32 complex)
+    WF_CUDA(cudaMalloc(&P.ana_scratch, sizeof(double2) * std::max(tiles, 2L) * P.nalm));
     WF_CUDA(cudaMalloc(&P.ana_lstart, sizeof(int) * tiles * (P.lmax + 1)));
     WF_CUDA(cudaMalloc(&P.ana_counter, sizeof(int)));
     WF_CUDA(cudaMemsetAsync(P.ana_counter, 0, sizeof(int), P.stream));
@@ -396,11 +398,12 @@ wf_status wf_get_tuning(wf_plan_t plan, wf_tuning *out) {
     out->syn_np[k] = plan->syn_np[k];
     out->ana_np[k] = plan->ana_np[k];
     for (int c = 0; c < 5; ++c) out->syn_ms[k][c] = plan->tune_syn_ms[k][c];
-    for (int c = 0; c < 9; ++c) out->ana_ms[k][c] = plan->tune_ana_ms[k][c];
+    for (int c = 0; c < 11; ++c) out->ana_ms[k][c] = plan->tune_ana_ms[k][c];
   }
   out->syn_packed = plan->syn_x2;
   out->ana_queue = plan->ana_queue;
   out->ana_packed = plan->ana_x2;
+  out->ana_global_acc = plan->ana_gacc;
   return WF_OK;
 }
 
@@ -422,6 +425,10 @@ wf_status wf_set_tuning(wf_plan_t plan, const wf_tuning *in) {
     return arg_error("wf_set_tuning: ana_queue, ana_packed, syn_packed must be 0 or 1");
   if (in->ana_queue && in->ana_packed)
     return arg_error("wf_set_tuning: ana_queue and ana_packed exclude each other");
+  if (!one_of(in->ana_global_acc, {0, 1}))
+    return arg_error("wf_set_tuning: ana_global_acc must be 0 or 1");
+  if (in->ana_global_acc && !(in->ana_packed && one_of(in->ana_np[1], {4, 6})))
+    return arg_error("wf_set_tuning: ana_global_acc needs ana_packed with ana_np 4 or 6");
   if (in->ana_queue ? !one_of(in->ana_np[1], {4, 8})
                     : in->ana_packed ? !one_of(in->ana_np[1], {4, 6, 8})
                                      : !one_of(in->ana_np[1], {2, 4, 8, 16}))
@@ -436,6 +443,7 @@ wf_status wf_set_tuning(wf_plan_t plan, const wf_tuning *in) {
   plan->syn_x2 = in->syn_packed;
   plan->ana_queue = in->ana_queue;
   plan->ana_x2 = in->ana_packed;
+  plan->ana_gacc = in->ana_global_acc;
   for (int i = 0; i < 3; ++i) {
     if (plan->graph[i]) cudaGraphExecDestroy(plan->graph[i]);
     plan->graph[i] = nullptr;

@@ -507,7 +507,11 @@ __device__ __forceinline__ void anal_partials(double num, double den, int m,
   }
 }
 
-template <typename T, int NP, bool X2 = false>
+// GACC: the per-warp accumulators live in global memory (scratch rows
+// [warp][alm], L2-resident) instead of shared memory, so shared memory no
+// longer caps the CTAs per SM; each chunk's old value is loaded before the
+// chunk's arithmetic and written back after its reduction.
+template <typename T, int NP, bool X2 = false, bool GACC = false>
 __global__ void __launch_bounds__(ANA_THREADS)
     k_legendre_anal(const RingPair *__restrict__ pairs, int npairs, int lmax,
                     const double *__restrict__ rc, const float *__restrict__ rc32,
@@ -518,7 +522,8 @@ __global__ void __launch_bounds__(ANA_THREADS)
                     double2 *__restrict__ x, double *__restrict__ partials,
                     const double2 *__restrict__ src,
                     typename Vec2<T>::type *__restrict__ xs_out,
-                    const SolverState *__restrict__ st, int mode, int lstatic) {
+                    const SolverState *__restrict__ st, int mode, int lstatic,
+                    T *__restrict__ gacc, long nalm) {
   typedef typename Vec2<T>::type T2;
   const int m = blockIdx.x;
   int L = lstatic;
@@ -538,12 +543,19 @@ __global__ void __launch_bounds__(ANA_THREADS)
     extern __shared__ __align__(16) unsigned char smraw[];
     const int nl = L - m + 1;
     T2 *acc = reinterpret_cast<T2 *>(smraw);  // [ANA_WARPS][nl]
-    T *sc = reinterpret_cast<T *>(smraw + align16d(sizeof(T2) * nl * ANA_WARPS));
+    T *sc = reinterpret_cast<T *>(smraw + (GACC ? 0 : align16d(sizeof(T2) * nl * ANA_WARPS)));
     for (int j = tid; j < nl; j += ANA_THREADS) sc[j] = coef<T>(rc, rc32, base + j);
-    for (int j = tid; j < nl * ANA_WARPS; j += ANA_THREADS)
-      acc[j] = Vec2<T>::make((T)0, (T)0);
+    if constexpr (GACC) {
+      for (int w = 0; w < ANA_WARPS; ++w)
+        for (int j = tid; j < nl; j += ANA_THREADS)
+          reinterpret_cast<T2 *>(gacc)[(long)w * nalm + base + j] = Vec2<T>::make((T)0, (T)0);
+    } else {
+      for (int j = tid; j < nl * ANA_WARPS; j += ANA_THREADS)
+        acc[j] = Vec2<T>::make((T)0, (T)0);
+    }
     __syncthreads();
-    T2 *myacc = acc + (long)warp * nl;
+    T2 *myacc = GACC ? reinterpret_cast<T2 *>(gacc) + (long)warp * nalm + base
+                     : acc + (long)warp * nl;
     const long stride = lmax + 1;
 
     for (int tile = 0; tile < npairs; tile += ANA_THREADS * NP) {
@@ -590,6 +602,10 @@ __global__ void __launch_bounds__(ANA_THREADS)
         // this warp (selects on every step), a full chunk with every seed of
         // the warp already in (the plain recurrence: 5 FP instructions per
         // term), and the last, partial chunk
+        const int lmine = lc + (lane >> 1);  // this lane's l after the reduction
+        T *mine = reinterpret_cast<T *>(myacc + (lmine - m)) + (lane & 1);
+        T old = (T)0;
+        if (GACC && lmine <= L) old = *mine;  // in flight during the chunk
         if (lc + LCHUNK - 1 > L)
           anal_chunk<T, NP, true, true, X2>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
                                         pr, pim, qr, qim);
@@ -600,23 +616,23 @@ __global__ void __launch_bounds__(ANA_THREADS)
           anal_chunk<T, NP, false, false, X2>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
                                           pr, pim, qr, qim);
         const T tot = transpose_reduce32<T>(v, lane);
-        const int l = lc + (lane >> 1);
-        if (l <= L) {
-          T2 &dst = myacc[l - m];
-          if (lane & 1)
-            dst.y += tot;
+        if (lmine <= L) {
+          if constexpr (GACC)
+            *mine = old + tot;
           else
-            dst.x += tot;
+            *mine += tot;
         }
       }
     }
     __syncthreads();
+    const T2 *accr = GACC ? reinterpret_cast<const T2 *>(gacc) + base : acc;
+    const long wstride = GACC ? nalm : nl;
     for (int j = tid; j < nl; j += ANA_THREADS) {
       double sr = 0.0, si = 0.0;
 #pragma unroll
       for (int w = 0; w < ANA_WARPS; ++w) {
-        sr += (double)acc[w * nl + j].x;
-        si += (double)acc[w * nl + j].y;
+        sr += (double)accr[w * wstride + j].x;
+        si += (double)accr[w * wstride + j].y;
       }
       anal_finish<T>(base + j, m + j, sr, si, wm, mode, rg, cl, omega, xi, mu, src, x,
                      xs_out, num, den);
@@ -1042,16 +1058,17 @@ static void synth_variant(const Plan &P, const typename Vec2<T>::type *xs,
       lstatic);
 }
 
-template <typename T, int NP, bool X2 = false>
+template <typename T, int NP, bool X2 = false, bool GACC = false>
 static void anal_variant(const Plan &P, const typename Vec2<T>::type *G, double2 *x,
                          const SolverState *st, int mode, int lstatic, const double2 *src,
                          typename Vec2<T>::type *xs_out) {
   typedef typename Vec2<T>::type T2;
-  const size_t smem =
-      align16(sizeof(T2) * (P.lmax + 1) * ANA_WARPS) + sizeof(T) * (P.lmax + 1);
-  k_legendre_anal<T, NP, X2><<<P.lmax + 1, ANA_THREADS, smem, P.stream>>>(
+  const size_t smem = (GACC ? 0 : align16(sizeof(T2) * (P.lmax + 1) * ANA_WARPS)) +
+                      sizeof(T) * (P.lmax + 1);
+  k_legendre_anal<T, NP, X2, GACC><<<P.lmax + 1, ANA_THREADS, smem, P.stream>>>(
       P.pairs, P.npairs, P.lmax, P.rc, P.rc32, P.rg, P.seed_l, P.seed_u, P.cl_d, P.omega,
-      G, x, P.partials, src, xs_out, st, mode, lstatic);
+      G, x, P.partials, src, xs_out, st, mode, lstatic,
+      GACC ? reinterpret_cast<T *>(P.ana_scratch) : nullptr, P.nalm);
 }
 
 // queue-scheduled FP32 analysis: persistent grid of ANA_Q_CTAS_PER_SM CTAs
@@ -1126,6 +1143,14 @@ wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
       return np == 4 ? anal_queue_variant<4>(P, g, x, st, mode, lstatic, src, xo)
                      : anal_queue_variant<8>(P, g, x, st, mode, lstatic, src, xo);
     }
+    if (P.ana_x2 && P.ana_gacc) {
+      if (np == 6)
+        anal_variant<T, 6, true, true>(P, G, x, st, mode, lstatic, src, xs_out);
+      else
+        anal_variant<T, 4, true, true>(P, G, x, st, mode, lstatic, src, xs_out);
+      WF_CUDA(cudaGetLastError());
+      return WF_OK;
+    }
     if (P.ana_x2) {
       if (np == 4)
         anal_variant<T, 4, true>(P, G, x, st, mode, lstatic, src, xs_out);
@@ -1196,9 +1221,9 @@ static cudaError_t set_big_smem_synth(int big) {
   return cudaFuncSetAttribute(k_legendre_synth<T, NP, X2>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
-template <typename T, int NP, bool X2 = false>
+template <typename T, int NP, bool X2 = false, bool GACC = false>
 static cudaError_t set_big_smem_anal(int big) {
-  return cudaFuncSetAttribute(k_legendre_anal<T, NP, X2>,
+  return cudaFuncSetAttribute(k_legendre_anal<T, NP, X2, GACC>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
@@ -1223,6 +1248,8 @@ wf_status init_legendre_attributes() {
   WF_CUDA((set_big_smem_anal<float, 4, true>(big)));
   WF_CUDA((set_big_smem_anal<float, 8, true>(big)));
   WF_CUDA((set_big_smem_anal<float, 6, true>(big)));
+  WF_CUDA((set_big_smem_anal<float, 4, true, true>(big)));
+  WF_CUDA((set_big_smem_anal<float, 6, true, true>(big)));
   WF_CUDA(cudaFuncSetAttribute(k_legendre_synth_dd,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_dd,

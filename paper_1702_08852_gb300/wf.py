@@ -53,8 +53,9 @@ class wf_stats(ctypes.Structure):
 class _Tuning(ctypes.Structure):
     _fields_ = [("syn_np", ctypes.c_int * 2), ("syn_packed", ctypes.c_int),
                 ("ana_np", ctypes.c_int * 2), ("ana_queue", ctypes.c_int),
-                ("ana_packed", ctypes.c_int), ("syn_ms", (ctypes.c_float * 5) * 2),
-                ("ana_ms", (ctypes.c_float * 9) * 2)]
+                ("ana_packed", ctypes.c_int), ("ana_global_acc", ctypes.c_int),
+                ("syn_ms", (ctypes.c_float * 5) * 2),
+                ("ana_ms", (ctypes.c_float * 11) * 2)]
 
 
 _lib = None
@@ -346,11 +347,11 @@ class Plan:
         _check(lib().wf_get_tuning(self.handle, ctypes.byref(t)))
         return {"syn_np": list(t.syn_np), "syn_packed": t.syn_packed,
                 "ana_np": list(t.ana_np), "ana_queue": t.ana_queue,
-                "ana_packed": t.ana_packed,
+                "ana_packed": t.ana_packed, "ana_global_acc": t.ana_global_acc,
                 "syn_ms": [list(r) for r in t.syn_ms], "ana_ms": [list(r) for r in t.ana_ms]}
 
     def set_tuning(self, syn_np=None, ana_np=None, ana_queue=None, syn_packed=None,
-                   ana_packed=None):
+                   ana_packed=None, ana_global_acc=None):
         """Force launch variants (wf_set_tuning); None keeps the current one."""
         t = _Tuning()
         _check(lib().wf_get_tuning(self.handle, ctypes.byref(t)))
@@ -364,6 +365,8 @@ class Plan:
             t.syn_packed = int(syn_packed)
         if ana_packed is not None:
             t.ana_packed = int(ana_packed)
+        if ana_global_acc is not None:
+            t.ana_global_acc = int(ana_global_acc)
         _check(lib().wf_set_tuning(self.handle, ctypes.byref(t)))
 
     def legendre_terms(self, L=None):
@@ -541,8 +544,8 @@ def wf_get_tuning(plan):
 
 
 def wf_set_tuning(plan, syn_np=None, ana_np=None, ana_queue=None, syn_packed=None,
-                  ana_packed=None):
-    return plan.set_tuning(syn_np, ana_np, ana_queue, syn_packed, ana_packed)
+                  ana_packed=None, ana_global_acc=None):
+    return plan.set_tuning(syn_np, ana_np, ana_queue, syn_packed, ana_packed, ana_global_acc)
 
 
 def wf_destroy(plan):

@@ -218,17 +218,19 @@ def test_mixed_precision_reaches_fp64_fixed_point(torch_cuda, osht, odm, nside, 
     assert st["fp_residual"] < 1e-6
 
 
-@pytest.mark.parametrize("ana_np,ana_queue,packed", [(4, 1, 0), (8, 1, 0), (16, 0, 0),
-                                                     (2, 0, 0), (8, 0, 1), (4, 0, 1),
-                                                     (6, 0, 1)])
+@pytest.mark.parametrize("ana_np,ana_queue,packed,gacc", [(4, 1, 0, 0), (8, 1, 0, 0),
+                                                          (16, 0, 0, 0), (2, 0, 0, 0),
+                                                          (8, 0, 1, 0), (4, 0, 1, 0),
+                                                          (6, 0, 1, 0), (4, 0, 1, 1)])
 def test_mixed_precision_variants_reach_fp64_fixed_point(torch_cuda, osht, odm, ana_np,
-                                                         ana_queue, packed):
+                                                         ana_queue, packed, gacc):
     """The same check with the FP32 analysis forced to each launch variant
     (the queue-scheduled one included: its combine kernel carries the filter,
     the anchored-stage source and the Cauchy partial sums)."""
     torch = torch_cuda
     p, d = problem(osht, "lognormal", 16, 8)
-    tuning = {"ana_np": (4, ana_np), "ana_queue": ana_queue, "ana_packed": packed}
+    tuning = {"ana_np": (4, ana_np), "ana_queue": ana_queue, "ana_packed": packed,
+              "ana_global_acc": gacc}
     if packed:
         tuning.update(syn_np=(2, 2), syn_packed=1)
     alm, mp, st, tr = gpu_solve(torch, p, d, tuning=tuning,
