@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true",
                     help="skip the plain FP64 solve used for the comparison")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
-    ap.add_argument("--kernel-case", choices=["legendre32", "legendre64"], default=None,
+    ap.add_argument("--kernel-case", choices=["legendre32", "legendre64", "legendre_df64"],
+                    default=None,
                     help="run only the Legendre kernels of one transform pair "
                          "(small case for profiling) and exit")
     ap.add_argument("--reps", type=int, default=3)
@@ -265,7 +266,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 transforms + f64 anchor", "data": "synthetic",
+        "dtype": "f32 transforms; anchors: double-float Legendre, f64 ring", "data": "synthetic",
         "config": {"workload": f"Nside {args.nside} lmax {2 * args.nside} scan-noise "
                                f"25% mask, 1 map per GPU",
                    "global_batch": world, "nside": args.nside, "lmax": 2 * args.nside,
@@ -423,7 +424,7 @@ def run_batch(args, rank, world):
             "value": world * nmaps * args.steps / (total_ms / 1e3), "unit": "maps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 transforms + f64 anchor",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 transforms; anchors: double-float Legendre, f64 ring",
             "data": "synthetic",
             "config": {"workload": "64 maps, Nside in {64,128,256}, lmax = 2 Nside, "
                                    "scan noise, mask 5-40 %",
@@ -553,9 +554,9 @@ def run_kernel_case(args):
                                            np.maximum(cl, 1e-30))).cuda()
     out = {}
     with wf.Plan(ns, lm, cl, autotune=1) as p:
-        f32 = args.kernel_case == "legendre32"
-        syn = p.alm2map_f32 if f32 else p.alm2map
-        ana = p.map2alm_f32 if f32 else p.map2alm
+        kc = args.kernel_case
+        syn = {"legendre32": p.alm2map_f32, "legendre_df64": p.alm2map_df64}.get(kc, p.alm2map)
+        ana = {"legendre32": p.map2alm_f32, "legendre_df64": p.map2alm_df64}.get(kc, p.map2alm)
         m = syn(a)
         b = ana(m)
         torch.cuda.synchronize()
