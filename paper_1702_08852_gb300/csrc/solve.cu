@@ -442,9 +442,12 @@ static wf_status enqueue_iteration(Plan &P, T2 *F, T2 *G, const double *data,
   return WF_OK;
 }
 
+// Iterations per graph launch: ~2^24 / Npix (fewer host polls for small
+// maps), at least 8 (at Nside 1024 a poll every ~11 ms of work instead of
+// every 2 iterations; iterations past `done` return at once).
 static int auto_chunk(const Plan &P) {
   long k = (1L << 24) / std::max(1L, P.npix);
-  return (int)std::max(2L, std::min(128L, k));
+  return (int)std::max(8L, std::min(128L, k));
 }
 
 template <typename T2>
