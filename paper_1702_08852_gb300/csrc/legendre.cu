@@ -839,26 +839,6 @@ __device__ __forceinline__ dd dd_rec(dd c, dd z, dd u1, dd u2) {
 
 constexpr int DD_NP_SYN = 2, DD_NP_ANA = 4;
 
-// v[0..31] per lane -> lane i returns the sum over lanes of v[i], in
-// double-float: the reduction stays on the FP32 pipe (a conversion to FP64
-// per value would load this part's slow FP64 pipe more than the recurrence
-// loads the FP32 one)
-__device__ __forceinline__ dd dd_transpose_reduce32(dd (&v)[32], int lane) {
-#pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
-    const bool upper = (lane & s) != 0;
-#pragma unroll
-    for (int j = 0; j < s; ++j) {
-      const dd send = upper ? v[j] : v[j + s];
-      const dd keep = upper ? v[j + s] : v[j];
-      dd recv;
-      recv.hi = __shfl_xor_sync(0xffffffffu, send.hi, s);
-      recv.lo = __shfl_xor_sync(0xffffffffu, send.lo, s);
-      v[j] = dd_add(keep, recv);
-    }
-  }
-  return v[0];
-}
 
 // synthesis: as k_legendre_synth (one CTA row per m, one thread per
 // DD_NP_SYN ring pairs), E/O parity sums in df64
@@ -953,7 +933,8 @@ __global__ void __launch_bounds__(SYN_THREADS)
 
 // analysis: queue-scheduled like k_legendre_anal_q; per (m, tile of 32
 // DD_NP_ANA ring pairs) item, per chunk of LCHUNK l the lane's df64 sums are
-// reduced across the warp in df64 and rounded to FP64 once
+// rounded to FP64 and reduced across the warp in FP64 (measured faster than
+// a double-float reduction)
 __global__ void __launch_bounds__(ANA_THREADS)
     k_legendre_anal_dd(const RingPair *__restrict__ pairs, int npairs, int lmax, long nalm,
                        const double *__restrict__ rc, const int *__restrict__ seed_l,
@@ -1022,7 +1003,7 @@ __global__ void __launch_bounds__(ANA_THREADS)
     __syncwarp();
     double *out = scratch + 2 * ((long)tile * nalm + base - m);  // out[2 l + re/im]
     for (int lc = lc0; lc <= L; lc += LCHUNK) {
-      dd v[32];
+      double v[32];
       const bool inj = lc <= linj;
 #pragma unroll
       for (int jj = 0; jj < LCHUNK; ++jj) {
@@ -1044,10 +1025,10 @@ __global__ void __launch_bounds__(ANA_THREADS)
             dd_acc(ai, u, even ? pim[j] : qim[j]);
           }
         }
-        v[2 * jj] = ar;
-        v[2 * jj + 1] = ai;
+        v[2 * jj] = dd_val(ar);
+        v[2 * jj + 1] = dd_val(ai);
       }
-      const double tot = dd_val(dd_transpose_reduce32(v, lane));
+      const double tot = transpose_reduce32<double>(v, lane);
       const int l = lc + (lane >> 1);
       if (l <= L) out[2 * l + (lane & 1)] = tot;
     }
