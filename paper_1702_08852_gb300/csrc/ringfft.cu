@@ -79,6 +79,18 @@ __device__ __forceinline__ T2 rot_q(T2 a) {
   return INV ? CT<T2>::mk(-a.y, a.x) : CT<T2>::mk(a.y, -a.x);
 }
 
+// Shared-memory layout of the FFT buffer: element i is stored at
+// sw(i) = i ^ (h(i >> 4) & 15), h(b) = b ^ (b << 2) -- an XOR inside each
+// aligned block of 16 complex values.  Unit-stride sweeps stay conflict-free,
+// and the radix-2^2 passes of short span (whose four operands sit 1..8
+// elements apart, 16 lanes in the same few banks) spread over all banks:
+// with it every pass of every power-of-two length needs the minimum number
+// of shared-memory wavefronts.
+__device__ __forceinline__ int sw(int i) {
+  const int b = i >> 4;
+  return i ^ ((b ^ (b << 2)) & 15);
+}
+
 // Twiddles of one pass: pair(j) gives W_2h^j = e^{-i pi j / h} and
 // W_h^j = (W_2h^j)^2 (h a power of two, 0 <= j < h).  FP32 computes them:
 // sincospi of the exact argument j / h (1/h is exact) and one complex square
@@ -128,22 +140,22 @@ __device__ void fft_dif(T2 *buf, int M, const T2 *__restrict__ tw, int Mmax) {
       const int i0 = ((b - j) << 2) + j, i1 = i0 + q, i2 = i0 + h, i3 = i2 + q;
       T2 w1 = w1f, w2 = w2f;  // W_2h^j, W_h^j
       if (!fixed) tp.pair(j, w1, w2);
-      const T2 x0 = buf[i0], x1 = buf[i1], x2 = buf[i2], x3 = buf[i3];
+      const T2 x0 = buf[sw(i0)], x1 = buf[sw(i1)], x2 = buf[sw(i2)], x3 = buf[sw(i3)];
       const T2 a0 = cadd(x0, x2), a1 = cadd(x1, x3);
       const T2 a2 = INV ? cmulc(csub(x0, x2), w1) : cmul(csub(x0, x2), w1);
       const T2 a3 = rot_q<T2, INV>(INV ? cmulc(csub(x1, x3), w1) : cmul(csub(x1, x3), w1));
-      buf[i0] = cadd(a0, a1);
-      buf[i1] = INV ? cmulc(csub(a0, a1), w2) : cmul(csub(a0, a1), w2);
-      buf[i2] = cadd(a2, a3);
-      buf[i3] = INV ? cmulc(csub(a2, a3), w2) : cmul(csub(a2, a3), w2);
+      buf[sw(i0)] = cadd(a0, a1);
+      buf[sw(i1)] = INV ? cmulc(csub(a0, a1), w2) : cmul(csub(a0, a1), w2);
+      buf[sw(i2)] = cadd(a2, a3);
+      buf[sw(i3)] = INV ? cmulc(csub(a2, a3), w2) : cmul(csub(a2, a3), w2);
     }
     __syncthreads();
   }
   if (h == 1) {
     for (int b = threadIdx.x; b < (M >> 1); b += blockDim.x) {
-      const T2 a = buf[2 * b], c = buf[2 * b + 1];
-      buf[2 * b] = cadd(a, c);
-      buf[2 * b + 1] = csub(a, c);
+      const T2 a = buf[sw(2 * b)], c = buf[sw(2 * b + 1)];
+      buf[sw(2 * b)] = cadd(a, c);
+      buf[sw(2 * b + 1)] = csub(a, c);
     }
     __syncthreads();
   }
@@ -158,9 +170,9 @@ __device__ void fft_dit(T2 *buf, int M, const T2 *__restrict__ tw, int Mmax) {
   while ((1 << bits) < M) ++bits;
   if (bits & 1) {
     for (int b = threadIdx.x; b < (M >> 1); b += blockDim.x) {
-      const T2 a = buf[2 * b], c = buf[2 * b + 1];
-      buf[2 * b] = cadd(a, c);
-      buf[2 * b + 1] = csub(a, c);
+      const T2 a = buf[sw(2 * b)], c = buf[sw(2 * b + 1)];
+      buf[sw(2 * b)] = cadd(a, c);
+      buf[sw(2 * b + 1)] = csub(a, c);
     }
     __syncthreads();
     h = 2;
@@ -176,17 +188,17 @@ __device__ void fft_dit(T2 *buf, int M, const T2 *__restrict__ tw, int Mmax) {
       const int i0 = ((b - j) << 2) + j, i1 = i0 + h, i2 = i0 + 2 * h, i3 = i2 + h;
       T2 wa = waf, wb = wbf;  // W_2h^j, W_4h^j
       if (!fixed) tp.pair(j, wb, wa);
-      const T2 x0 = buf[i0], x1 = buf[i1], x2 = buf[i2], x3 = buf[i3];
+      const T2 x0 = buf[sw(i0)], x1 = buf[sw(i1)], x2 = buf[sw(i2)], x3 = buf[sw(i3)];
       const T2 c1 = INV ? cmulc(x1, wa) : cmul(x1, wa);
       const T2 c3 = INV ? cmulc(x3, wa) : cmul(x3, wa);
       const T2 a0 = cadd(x0, c1), a1 = csub(x0, c1);
       const T2 a2 = cadd(x2, c3), a3 = csub(x2, c3);
       const T2 d2 = INV ? cmulc(a2, wb) : cmul(a2, wb);
       const T2 d3 = rot_q<T2, INV>(INV ? cmulc(a3, wb) : cmul(a3, wb));
-      buf[i0] = cadd(a0, d2);
-      buf[i2] = csub(a0, d2);
-      buf[i1] = cadd(a1, d3);
-      buf[i3] = csub(a1, d3);
+      buf[sw(i0)] = cadd(a0, d2);
+      buf[sw(i2)] = csub(a0, d2);
+      buf[sw(i1)] = cadd(a1, d3);
+      buf[sw(i3)] = csub(a1, d3);
     }
     __syncthreads();
   }
@@ -200,11 +212,11 @@ __device__ void bluestein(T2 *buf, int n, int M, const T2 *__restrict__ tw,
                           const T2 *__restrict__ bhat) {
   fft_dif<T2, false>(buf, M, tw, Mmax);
   #pragma unroll 8
-  for (int q = threadIdx.x; q < M; q += blockDim.x) buf[q] = cmul(buf[q], bhat[q]);
+  for (int q = threadIdx.x; q < M; q += blockDim.x) buf[sw(q)] = cmul(buf[sw(q)], bhat[q]);
   __syncthreads();
   fft_dit<T2, true>(buf, M, tw, Mmax);
   #pragma unroll 8
-  for (int k = threadIdx.x; k < n; k += blockDim.x) buf[k] = cmulc(buf[k], chirp[k]);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) buf[sw(k)] = cmulc(buf[sw(k)], chirp[k]);
   __syncthreads();
 }
 
@@ -358,7 +370,7 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
         cN = cmul(cN, ph);
         cS = cmul(cS, ph);
         const T2 Zk = CT<T2>::mk(cN.x - cS.y, cN.y + cS.x);  // cN + i cS
-        buf[k] = blue ? cmulc(cconj(Zk), chirp[k]) : Zk;
+        buf[sw(k)] = blue ? cmulc(cconj(Zk), chirp[k]) : Zk;
       }
     } else {
       #pragma unroll 4
@@ -370,11 +382,11 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
           if (south) cS = fold(FS, k, n, Lf, sgn, ph);
         }
         const T2 Zk = CT<T2>::mk(cN.x - cS.y, cN.y + cS.x);  // cN + i cS
-        buf[k] = blue ? cmulc(cconj(Zk), chirp[k]) : Zk;
+        buf[sw(k)] = blue ? cmulc(cconj(Zk), chirp[k]) : Zk;
       }
     }
     if (blue)
-      for (int k = n + threadIdx.x; k < M; k += blockDim.x) buf[k] = zero;
+      for (int k = n + threadIdx.x; k < M; k += blockDim.x) buf[sw(k)] = zero;
     __syncthreads();
     if (blue) {
       bluestein<T2>(buf, n, M, tw, Mmax, chirp, bhat);  // DFT(conj Z)
@@ -385,7 +397,7 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
     #pragma unroll 4
     for (int q = threadIdx.x; q < n; q += blockDim.x) {
       const int j = blue ? q : bitrev_n(q, bits);
-      T2 zz = buf[q];
+      T2 zz = buf[sw(q)];
       if (blue) zz = cconj(zz);
       const double sN = (double)zz.x, sS = (double)zz.y;
       const long pN = rp.ofsN + j, pS = south ? rp.ofsS + j : -1;
@@ -419,12 +431,12 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
           }
           tt = CT<T2>::mk((T)tN, (T)tS);
         }
-        buf[q] = blue ? cmulc(tt, chirp[q]) : tt;
+        buf[sw(q)] = blue ? cmulc(tt, chirp[q]) : tt;
       }
     }
     if (MODE == RING_SYNTH) return;
     if (blue)
-      for (int k = n + threadIdx.x; k < M; k += blockDim.x) buf[k] = zero;
+      for (int k = n + threadIdx.x; k < M; k += blockDim.x) buf[sw(k)] = zero;
     __syncthreads();
   } else {
     #pragma unroll 4
@@ -433,12 +445,12 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
       const double tS = south ? in_map[rp.ofsS + j] : 0.0;
       const T2 tt = CT<T2>::mk((T)tN, (T)tS);
       if (blue)
-        buf[j] = cmulc(tt, chirp[j]);
+        buf[sw(j)] = cmulc(tt, chirp[j]);
       else
-        buf[bitrev_n(j, bits)] = tt;
+        buf[sw(bitrev_n(j, bits))] = tt;
     }
     if (blue)
-      for (int k = n + threadIdx.x; k < M; k += blockDim.x) buf[k] = zero;
+      for (int k = n + threadIdx.x; k < M; k += blockDim.x) buf[sw(k)] = zero;
     __syncthreads();
   }
   // forward DFT of t (natural order output)
@@ -462,7 +474,7 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
     for (int k = (n < (int)blockDim.x ? (int)threadIdx.x % n : (int)threadIdx.x);
          k <= kmax; k += kstep) {
       const int kk = k == 0 ? 0 : n - k;
-      const T2 X = buf[k], Xc = cconj(buf[kk]);
+      const T2 X = buf[sw(k)], Xc = cconj(buf[sw(kk)]);
       const T2 ph = cconj(ring_phase<T2>(k, rp.phi_num, rp.phi_den, tstep, tw));
       const T2 tN = cmul(CT<T2>::mk(half * (X.x + Xc.x), half * (X.y + Xc.y)), ph);
       // (X - Xc) / (2i)
