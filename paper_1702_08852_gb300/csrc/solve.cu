@@ -510,8 +510,10 @@ static wf_status capture_graph(Plan &P, int which, T2 *F, T2 *G, const double *d
 // have been uploaded.
 template <typename T2>
 static wf_status run_loop(Plan &P, int which, T2 *F, T2 *G, const double *tinit,
-                          const double *data, const double2 *src) {
-  if (tinit) {
+                          const double *data, const double2 *src, bool keep_G = false) {
+  if (keep_G) {
+    // G already holds the messenger's ring coefficients
+  } else if (tinit) {
     WF_TRY(launch_ring<T2>(P, RING_ANALYSIS, nullptr, G, tinit, nullptr, nullptr,
                            P.lmax));
   } else {
@@ -563,6 +565,72 @@ __global__ void k_make_source(const double2 *gx, const double2 *x, const double 
   }
 }
 
+// gx = f U on l <= L (0 above), f = Sbar / (Sbar + xi Omega); partials of
+// ||gx - x||^2 and ||gx||^2 per m (weights 1 for m = 0, 2 else)
+__global__ void k_filter_from_u(const double2 *__restrict__ U, const double2 *__restrict__ x,
+                                const double *__restrict__ cl, double xi, double mu,
+                                double omega, int L, int lmax, double2 *__restrict__ gx,
+                                double *__restrict__ partials) {
+  __shared__ double sn[128], sd[128];
+  const int m = blockIdx.x;
+  const long base = (long)m * (2 * lmax + 1 - m) / 2;
+  const double wm = m == 0 ? 1.0 : 2.0;
+  double num = 0.0, den = 0.0;
+  for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
+    const long i = base + l;
+    double2 g = make_double2(0.0, 0.0);
+    if (l <= L) {
+      const double sb = fmax(cl[l] - mu * omega, 0.0);
+      const double f = sb / (sb + xi * omega);
+      g = make_double2(f * U[i].x, f * U[i].y);
+    }
+    const double dr = g.x - x[i].x, di = g.y - x[i].y;
+    num += wm * (dr * dr + di * di);
+    den += wm * (g.x * g.x + g.y * g.y);
+    gx[i] = g;
+  }
+  sn[threadIdx.x] = num;
+  sd[threadIdx.x] = den;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sn[threadIdx.x] += sn[threadIdx.x + s];
+      sd[threadIdx.x] += sd[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[2 * m] = sn[0];
+    partials[2 * m + 1] = sd[0];
+  }
+}
+
+// Source of the first iteration after a stage boundary between anchored
+// stages: with the previous anchor's U = Omega Y^T t_a (old stage's weights)
+// and the correction messenger tau still in place, the analysis
+// f (Omega Y^T tau + xi Omega src) must give f (Omega Y^T tau + U) - x_last,
+// i.e. the paper's first step of the new stage from the old messenger:
+// src = U / (xi Omega) - x_last (Sbar + xi Omega) / (Sbar xi Omega) where
+// Sbar > 0 (0 elsewhere, where x_last = 0 as well)
+__global__ void k_make_source_carry(const double2 *__restrict__ U,
+                                    const double2 *__restrict__ x, const double *__restrict__ cl,
+                                    double xi, double mu, double omega, int L, int lmax,
+                                    double2 *__restrict__ src) {
+  const int m = blockIdx.x;
+  const long base = (long)m * (2 * lmax + 1 - m) / 2;
+  const double xo = xi * omega;
+  for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
+    const long i = base + l;
+    const double sb = fmax(cl[l] - mu * omega, 0.0);
+    double2 v = make_double2(0.0, 0.0);
+    if (l <= L && sb > 0.0) {
+      const double s = (sb + xo) / (sb * xo);
+      v = make_double2(U[i].x / xo - s * x[i].x, U[i].y / xo - s * x[i].y);
+    }
+    src[i] = v;
+  }
+}
+
 __global__ void k_alm_add(double2 *x, const double2 *y, long n) {
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long)gridDim.x * blockDim.x)
@@ -574,12 +642,16 @@ __global__ void k_alm_add(double2 *x, const double2 *y, long n) {
 // One iteration map of stage (xi, mu, band L) from x into gx, and the
 // squared step norm.  dd: the Legendre transforms in double-float (the
 // anchors of a mixed solve with opts.anchor = 1); else plain FP64.
+// U (optional): also keep the unfiltered analysis Omega Y^T t up to band
+// max(L, Lu) (the next stage's band) -- gx is then f U.
 static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
-                           double xi, double mu, int L, bool dd = false) {
+                           double xi, double mu, int L, bool dd = false,
+                           double2 *U = nullptr, int Lu = -1) {
   SolverState s = initial_state(P);
   s.xi = xi;
   s.mu = mu;
-  s.lcur = s.lnext = L;
+  s.lcur = L;
+  s.lnext = U ? std::max(L, Lu) : L;
   s.done = 0;
   *P.state_h = s;
   WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
@@ -593,10 +665,21 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
     WF_TRY(launch_legendre_synth<double2>(P, P.xs64, P.F64, nullptr, std::max(L, 0)));
   WF_TRY(launch_ring<double2>(P, RING_FUSED, P.F64, P.G64, P.dmap, nullptr, P.state,
                               P.lmax));
-  if (dd)
+  if (U) {
+    const int Lb = std::max(L, Lu);
+    if (dd)
+      WF_TRY(launch_legendre_anal_dd(P, P.G64, U, nullptr, ANA_PLAIN, Lb));
+    else
+      WF_TRY(launch_legendre_anal<double2>(P, P.G64, U, nullptr, ANA_PLAIN, Lb));
+    ++P.nlaunch;
+    k_filter_from_u<<<P.lmax + 1, 128, 0, P.stream>>>(U, x, P.cl_d, xi, mu, P.omega, L,
+                                                      P.lmax, gx, P.partials);
+    WF_CUDA(cudaGetLastError());
+  } else if (dd) {
     WF_TRY(launch_legendre_anal_dd(P, P.G64, gx, P.state, ANA_FILTER, P.lmax));
-  else
+  } else {
     WF_TRY(launch_legendre_anal<double2>(P, P.G64, gx, P.state, ANA_FILTER, P.lmax));
+  }
   std::vector<double> part(2 * (P.lmax + 1));
   WF_CUDA(cudaMemcpyAsync(part.data(), P.partials, sizeof(double) * part.size(),
                           cudaMemcpyDeviceToHost, P.stream));
@@ -646,6 +729,7 @@ static wf_status account_work(Plan &P, int i0, int i1) {
   for (int i = i0; i < i1; ++i) {
     const TraceEntry &e = h[i - i0];
     if (e.lcur < 0) continue;
+    if (std::find(P.untimed.begin(), P.untimed.end(), i) != P.untimed.end()) continue;
     double t = 0.0;
     WF_TRY(legendre_terms(P, e.lcur, &t));
     P.kern_flop[0] += 7.0 * t;
@@ -686,6 +770,7 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
     return WF_ERR_STATE;
   }
   WF_CUDA(cudaEventRecord(P.ev0, P.stream));
+  P.untimed.clear();
   const long launches0 = P.nlaunch;
   ++P.nlaunch;
   k_mask_data<<<304, 256, 0, P.stream>>>(d, P.nvar, P.npix, P.dmap);
@@ -743,15 +828,31 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
                             cudaMemcpyDeviceToDevice, P.stream));
     double prev_rel = -1.0, rate_floor = 0.0;
     int cycles = 0, reanchors = 0, cycle_start = total_iter;
+    if (!P.uacc[0]) {
+      WF_CUDA(cudaMalloc(&P.uacc[0], sizeof(double2) * P.nalm));
+      WF_CUDA(cudaMalloc(&P.uacc[1], sizeof(double2) * P.nalm));
+      WF_CUDA(cudaMalloc(&P.src2, sizeof(double2) * P.nalm));
+    }
+    // At a boundary between anchored stages the paper's iteration takes the
+    // new stage's first step from the old stage's messenger t (Algorithm 2
+    // carries t, not x, across the cooling step).  The correction form does
+    // the same: the last anchor's unfiltered U = Omega Y^T t_a and the
+    // correction messenger tau still in G32 give the first step through a
+    // one-off source; the new anchor's source takes over from the second.
+    int ucur = 0;
+    const double2 *uprev = nullptr;
+    bool boundary = false;
     while (anchored && reanchors <= MAX_REANCHORS && cycles <= P.opts.refine_max) {
       const SolverState stage = h;  // stage parameters of this anchor
+      const bool carry = boundary && uprev != nullptr;
       double num = 0.0, xn = 0.0;
       WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num, stage.xi, stage.mu, stage.lcur,
-                       P.opts.anchor == 1));
+                       P.opts.anchor == 1, P.uacc[ucur], stage.lnext));
       WF_TRY(alm_dot(P, P.xacc, P.xacc, nullptr, &xn));
       ++P.nlaunch;
       k_make_source<<<P.lmax + 1, 128, 0, P.stream>>>(P.xtmp, P.xacc, P.cl_d, stage.xi,
-                                                      stage.mu, P.omega, P.lmax, P.src);
+                                                      stage.mu, P.omega, P.lmax,
+                                                      carry ? P.src2 : P.src);
       WF_CUDA(cudaGetLastError());
       WF_CUDA(cudaMemsetAsync(P.x, 0, sizeof(double2) * P.nalm, P.stream));
       SolverState s = initial_state(P);
@@ -771,7 +872,24 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       h = s;
       WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
                               cudaMemcpyHostToDevice, P.stream));
-      WF_TRY(run_loop<float2>(P, 2, P.F32, P.G32, nullptr, nullptr, P.src));
+      if (carry) {
+        ++P.nlaunch;
+        k_make_source_carry<<<P.lmax + 1, 128, 0, P.stream>>>(
+            uprev, P.xacc, P.cl_d, stage.xi, stage.mu, P.omega, stage.lcur, P.lmax, P.src);
+        WF_CUDA(cudaGetLastError());
+        P.untimed.push_back(h.iter);
+        WF_TRY(enqueue_iteration<float2>(P, P.F32, P.G32, nullptr, P.src, -1));
+        WF_CUDA(cudaMemcpyAsync(P.src, P.src2, sizeof(double2) * P.nalm,
+                                cudaMemcpyDeviceToDevice, P.stream));
+        WF_CUDA(cudaMemcpyAsync(P.state_h, P.state, sizeof(SolverState),
+                                cudaMemcpyDeviceToHost, P.stream));
+        WF_CUDA(cudaStreamSynchronize(P.stream));
+        if (!h.done) WF_TRY(run_loop<float2>(P, 2, P.F32, P.G32, nullptr, nullptr, P.src, true));
+      } else {
+        WF_TRY(run_loop<float2>(P, 2, P.F32, P.G32, nullptr, nullptr, P.src));
+      }
+      uprev = P.uacc[ucur];
+      ucur ^= 1;
       total_iter = h.iter;
       if (h.numeric_error) {
         set_error("wf_solve: NaN or Inf in an anchored stage");
@@ -783,6 +901,7 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       k_alm_add<<<304, 256, 0, P.stream>>>(P.xacc, P.x, P.nalm);
       WF_CUDA(cudaGetLastError());
       ++refinements;
+      boundary = h.at_boundary != 0;
       if (h.at_boundary) continue;  // next stage: h holds its parameters
       if (h.reanchor || (h.stagnated && h.mu == 0.0)) {
         ++reanchors;  // same stage, new anchor

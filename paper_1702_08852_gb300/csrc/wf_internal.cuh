@@ -159,6 +159,12 @@ struct Plan {
   double2 *xs64 = nullptr;       // [nalm] g_lm x_lm, synthesis input (FP64)
   float2 *xs32 = nullptr;        // [nalm] g_lm x_lm, synthesis input (FP32)
   double2 *src = nullptr;        // [nalm] harmonic source of a correction solve
+  // mixed solver, stage boundaries between anchored stages: the unfiltered
+  // FP64 analysis U = Omega Y^T t_a of the last two anchors and the next
+  // source (allocated by the first mixed solve)
+  double2 *uacc[2] = {nullptr, nullptr};
+  double2 *src2 = nullptr;
+  std::vector<int> untimed;      // iterations run outside the timed graphs
   double *dmap = nullptr;        // [npix] data with masked pixels zeroed
   float *dmap32 = nullptr;       // [npix] FP32 copy of dmap (FP32 ring step)
   int data_iters = 0;            // iterations of the last solve that read d
