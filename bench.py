@@ -28,9 +28,10 @@ if ROOT not in sys.path:
 
 METRIC = "WF solves/s to 1e-6 rel at Nside 1024"
 UNIT = "solves/s"
-# iterations of the GPU solve of this workload (measured), used to scale the
-# oracle's per-iteration cost in the reference arm
-REF_ITERATIONS = {1024: 2200, 256: 3800}
+# iterations of the plain FP64 solve of this workload (measured on the GPU:
+# the FP64 oracle would take the same path), used to scale the oracle's
+# per-iteration cost in the reference arm
+REF_ITERATIONS = {1024: 2048, 256: 4216}
 
 
 def parse():
@@ -362,7 +363,7 @@ def run_reference(args, rank, world):
     for _ in range(args.warmup):
         pass
     pair_s, sample, threads = oracle_sample(args.nside, args.cpu_sample_s)
-    iterations = REF_ITERATIONS.get(args.nside, 2200)
+    iterations = REF_ITERATIONS.get(args.nside, 2048)
     steps_s = []
     for _ in range(args.steps):
         steps_s.append(pair_s * iterations)
