@@ -121,6 +121,23 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+# DRAM bytes (read + write, ncu) of one full-band launch of the FP32 analysis
+# variant the autotuner picks at Nside 1024 / lmax 2048 (kernel-case capture,
+# profiles/legendre_f32_nside1024.md); scaled to a live launch by its share
+# of the full band's terms.  None once the kernel changes after a capture.
+ANALYSIS_DRAM_FULL_BAND = {"nside": 1024, "bytes": 179246080.0 + 79453440.0,
+                           "terms": 3140761977.0}
+
+
+def analysis_traffic(nside, gflop, launches):
+    """Bytes per live analysis launch from the captured full-band figure."""
+    ref = ANALYSIS_DRAM_FULL_BAND
+    if ref["bytes"] is None or nside != ref["nside"] or not launches:
+        return None
+    terms_per_launch = gflop * 1e9 / 7.0 / launches
+    return ref["bytes"] * terms_per_launch / ref["terms"]
+
+
 # FP32 peak of the non-tensor pipe: 152 SMs x 128 FP32 lanes x 2 flop (FMA)
 # x the SM clock (2070 MHz maximum on this part)
 def fp32_alu_peak_tflops(sm_mhz=2070.0):
@@ -284,7 +301,8 @@ def run_ours(args, rank, world):
                      "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
                      "frac": (achieved / peak32) if achieved else None,
                      "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz",
-                     "traffic": None,
+                     "traffic": analysis_traffic(args.nside, k0["gflop"], k0["launches"]),
+                     "traffic_source": "ncu dram bytes of the full-band launch, scaled by terms",
                      "launches": k0["launches"], "avg_launch_ms": k0["ms"] / max(1, k0["launches"]),
                      "synthesis": {"achieved": (kern[1]["gflop"] / (kern[1]["ms"] / 1e3) / 1e3)
                                    if kern[1]["ms"] > 0 else None,
