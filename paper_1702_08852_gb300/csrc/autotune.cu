@@ -18,7 +18,7 @@ namespace wf {
 namespace {
 struct Choice {
   int syn[2], ana[2], ana_queue, syn_x2, ana_x2, ana_gacc;
-  float syn_ms[2][5], ana_ms[2][11];  // the timings the choice was made from
+  float syn_ms[2][6], ana_ms[2][11];  // the timings the choice was made from
 };
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, Choice> g_tune_cache;
@@ -81,13 +81,14 @@ wf_status autotune(Plan &P) {
     float best = 1e30f;
     int pick = P.syn_np[k];
     int pick_x2 = 0;
-    // FP32 also tries the packed f32x2 synthesis with 2 and 4 pairs
-    const int nsyn = k ? 5 : 3;
+    // FP32 also tries the packed f32x2 synthesis with 2 and 4 pairs (slots
+    // 3, 4) and with duplicated tables and 2 pairs (slot 5)
+    const int nsyn = k ? 6 : 3;
     for (int ci = 0; ci < nsyn; ++ci) {
       const bool x2 = ci >= 3;
-      const int c = x2 ? (ci == 3 ? 2 : 4) : syn_cand[ci];
+      const int c = x2 ? (ci == 4 ? 4 : 2) : syn_cand[ci];
       P.syn_np[k] = c;
-      if (k) P.syn_x2 = x2 ? 1 : 0;
+      if (k) P.syn_x2 = ci == 5 ? 2 : (x2 ? 1 : 0);
       float ms = 0.f;
       st = k ? time_synth<float2>(P, P.xs32, P.F32, e0, e1, &ms)
              : time_synth<double2>(P, P.xs64, P.F64, e0, e1, &ms);
@@ -96,7 +97,7 @@ wf_status autotune(Plan &P) {
       if (ms < best) {
         best = ms;
         pick = c;
-        pick_x2 = x2 ? 1 : 0;
+        pick_x2 = ci == 5 ? 2 : (x2 ? 1 : 0);
       }
     }
     if (k) P.syn_x2 = pick_x2;

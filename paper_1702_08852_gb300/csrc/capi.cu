@@ -397,7 +397,7 @@ wf_status wf_get_tuning(wf_plan_t plan, wf_tuning *out) {
   for (int k = 0; k < 2; ++k) {
     out->syn_np[k] = plan->syn_np[k];
     out->ana_np[k] = plan->ana_np[k];
-    for (int c = 0; c < 5; ++c) out->syn_ms[k][c] = plan->tune_syn_ms[k][c];
+    for (int c = 0; c < 6; ++c) out->syn_ms[k][c] = plan->tune_syn_ms[k][c];
     for (int c = 0; c < 11; ++c) out->ana_ms[k][c] = plan->tune_ana_ms[k][c];
   }
   out->syn_packed = plan->syn_x2;
@@ -421,8 +421,8 @@ wf_status wf_set_tuning(wf_plan_t plan, const wf_tuning *in) {
   if (!one_of(in->ana_np[0], {2, 4, 8}))
     return arg_error("wf_set_tuning: FP64 ana_np must be 2, 4 or 8");
   if (!one_of(in->ana_queue, {0, 1}) || !one_of(in->ana_packed, {0, 1}) ||
-      !one_of(in->syn_packed, {0, 1}))
-    return arg_error("wf_set_tuning: ana_queue, ana_packed, syn_packed must be 0 or 1");
+      !one_of(in->syn_packed, {0, 1, 2}))
+    return arg_error("wf_set_tuning: ana_queue, ana_packed must be 0 or 1, syn_packed 0, 1 or 2");
   if (in->ana_queue && in->ana_packed)
     return arg_error("wf_set_tuning: ana_queue and ana_packed exclude each other");
   if (!one_of(in->ana_global_acc, {0, 1}))
@@ -434,8 +434,10 @@ wf_status wf_set_tuning(wf_plan_t plan, const wf_tuning *in) {
                                      : !one_of(in->ana_np[1], {2, 4, 8, 16}))
     return arg_error("wf_set_tuning: FP32 ana_np must be 2, 4, 8 or 16 (queue: 4, 8; "
                      "packed: 4, 6, 8)");
-  if (in->syn_packed && !one_of(in->syn_np[1], {2, 4}))
+  if (in->syn_packed == 1 && !one_of(in->syn_np[1], {2, 4}))
     return arg_error("wf_set_tuning: packed FP32 synthesis needs syn_np 2 or 4");
+  if (in->syn_packed == 2 && in->syn_np[1] != 2)
+    return arg_error("wf_set_tuning: packed FP32 synthesis with duplicated tables needs syn_np 2");
   for (int k = 0; k < 2; ++k) {
     plan->syn_np[k] = in->syn_np[k];
     plan->ana_np[k] = in->ana_np[k];

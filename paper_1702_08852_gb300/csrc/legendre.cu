@@ -113,7 +113,16 @@ __device__ __forceinline__ void mul2(float &dx, float &dy, float ax, float ay, f
       : "=f"(dx), "=f"(dy)
       : "f"(ax), "f"(ay), "f"(bx), "f"(by));
 }
-// the FP32 recurrence step for rings j, j' at once (same roundings as rec_step)
+// the FP32 recurrence step for rings j, j' at once (same roundings as
+// rec_step); cx, cy both hold c_l (a register pair when loaded as one)
+__device__ __forceinline__ void rec_step2(float cx, float cy, float zh0, float zh1,
+                                          float zl0, float zl1, float u10, float u11,
+                                          float u20, float u21, float &s0, float &s1) {
+  float a0, a1, t0, t1;
+  mul2(a0, a1, cx, cy, u10, u11);
+  fma2(t0, t1, a0, a1, zl0, zl1, u20, u21);
+  fma2(s0, s1, a0, a1, zh0, zh1, t0, t1);
+}
 __device__ __forceinline__ void rec_step2(float c, float zh0, float zh1, float zl0,
                                           float zl1, float u10, float u11, float u20,
                                           float u21, float &s0, float &s1) {
@@ -134,7 +143,10 @@ __device__ __forceinline__ size_t align16d(size_t b) { return (b + 15) & ~(size_
 // ------------------------------------------------------------------ synthesis
 constexpr int SYN_THREADS = 128;
 
-template <typename T, int NP, bool X2 = false>
+// DUP (with X2): the coefficient and input tables are kept duplicated in
+// shared memory, (c, c) and (x_re, x_re, x_im, x_im), so that each packed
+// operand pair arrives from one load instead of a load and a copy.
+template <typename T, int NP, bool X2 = false, bool DUP = false>
 __global__ void __launch_bounds__(SYN_THREADS)
     k_legendre_synth(const RingPair *__restrict__ pairs, int npairs, int lmax,
                      const double *__restrict__ rc, const float *__restrict__ rc32,
@@ -155,11 +167,20 @@ __global__ void __launch_bounds__(SYN_THREADS)
   const int nl = L - m + 1;
   T2 *sx = reinterpret_cast<T2 *>(smraw);
   T *sc = reinterpret_cast<T *>(smraw + align16d(sizeof(T2) * nl));
+  float4 *sx4 = reinterpret_cast<float4 *>(smraw);                 // DUP layout
+  float2 *sc2 = reinterpret_cast<float2 *>(smraw + sizeof(float4) * nl);
   const long base = lm_index(lmax, m, m);
   for (int j = threadIdx.x; j < nl; j += blockDim.x) {
     const long i = base + j;
-    sc[j] = coef<T>(rc, rc32, i);
-    sx[j] = xs[i];
+    if constexpr (DUP) {
+      const float c = rc32[i];
+      const float2 x = reinterpret_cast<const float2 *>(xs)[i];
+      sc2[j] = make_float2(c, c);
+      sx4[j] = make_float4(x.x, x.x, x.y, x.y);
+    } else {
+      sc[j] = coef<T>(rc, rc32, i);
+      sx[j] = xs[i];
+    }
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -202,8 +223,15 @@ __global__ void __launch_bounds__(SYN_THREADS)
       for (int p = 0; p < 2; ++p) {
         const int ll = l + p;
         const int li = min(ll, L) - m;  // ll > L only on the last odd step
-        const T c = sc[li];
-        T2 xv = sx[li];
+        T c;
+        T2 xv;
+        if constexpr (DUP) {
+          c = sc2[li].x;
+          xv = Vec2<T>::make(sx4[li].x, sx4[li].z);
+        } else {
+          c = sc[li];
+          xv = sx[li];
+        }
         if (ll > L) xv = Vec2<T>::make((T)0, (T)0);
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
@@ -226,6 +254,29 @@ __global__ void __launch_bounds__(SYN_THREADS)
     // l - m is even here: (c_l, c_l+1) is one aligned pair of T and, in
     // FP32, (x_l, x_l+1) one aligned 16-byte load
     for (; l + 1 <= L; l += 2) {
+      if constexpr (DUP) {
+        // (c_l, c_l, c_l+1, c_l+1) and (x_re, x_re, x_im, x_im) for l, l+1
+        const float4 cq = *reinterpret_cast<const float4 *>(sc2 + (l - m));
+        const float4 xa = sx4[l - m], xb = sx4[l + 1 - m];
+#pragma unroll
+        for (int jp = 0; jp < NP / 2; ++jp) {
+          const int j0 = 2 * jp, j1 = 2 * jp + 1;
+          float w0, w1, v0, v1;
+          rec_step2(cq.x, cq.y, zh[j0], zh[j1], zl[j0], zl[j1], u1[j0], u1[j1], u2[j0],
+                    u2[j1], w0, w1);
+          fma2(er[j0], er[j1], w0, w1, xa.x, xa.y, er[j0], er[j1]);
+          fma2(ei[j0], ei[j1], w0, w1, xa.z, xa.w, ei[j0], ei[j1]);
+          rec_step2(cq.z, cq.w, zh[j0], zh[j1], zl[j0], zl[j1], w0, w1, u1[j0], u1[j1], v0,
+                    v1);
+          fma2(orr[j0], orr[j1], v0, v1, xb.x, xb.y, orr[j0], orr[j1]);
+          fma2(oi[j0], oi[j1], v0, v1, xb.z, xb.w, oi[j0], oi[j1]);
+          u2[j0] = w0;
+          u2[j1] = w1;
+          u1[j0] = v0;
+          u1[j1] = v1;
+        }
+        continue;
+      }
       const T2 cp = *reinterpret_cast<const T2 *>(sc + (l - m));
       const T c0 = cp.x, c1 = cp.y;
       T2 x0, x1;
@@ -271,8 +322,15 @@ __global__ void __launch_bounds__(SYN_THREADS)
       }
     }
     if (l <= L) {
-      const T c0 = sc[l - m];
-      const T2 x0 = sx[l - m];
+      T c0;
+      T2 x0;
+      if constexpr (DUP) {
+        c0 = sc2[l - m].x;
+        x0 = Vec2<T>::make(sx4[l - m].x, sx4[l - m].z);
+      } else {
+        c0 = sc[l - m];
+        x0 = sx[l - m];
+      }
 #pragma unroll
       for (int j = 0; j < NP; ++j) {
         T u = rec_step(c0, zh[j], zl[j], u1[j], u2[j]);
@@ -1048,14 +1106,15 @@ struct Kernels<float2> {
   typedef float T;
 };
 
-template <typename T, int NP, bool X2 = false>
+template <typename T, int NP, bool X2 = false, bool DUP = false>
 static void synth_variant(const Plan &P, const typename Vec2<T>::type *xs,
                           typename Vec2<T>::type *F, const SolverState *st, int lstatic) {
   typedef typename Vec2<T>::type T2;
-  const size_t smem = align16(sizeof(T2) * (P.lmax + 1)) + sizeof(T) * (P.lmax + 1);
+  const size_t smem = DUP ? (sizeof(float4) + sizeof(float2)) * (P.lmax + 1)
+                          : align16(sizeof(T2) * (P.lmax + 1)) + sizeof(T) * (P.lmax + 1);
   const int pairs_per_cta = SYN_THREADS * NP;
   dim3 grid((P.npairs + pairs_per_cta - 1) / pairs_per_cta, P.lmax + 1);
-  k_legendre_synth<T, NP, X2><<<grid, SYN_THREADS, smem, P.stream>>>(
+  k_legendre_synth<T, NP, X2, DUP><<<grid, SYN_THREADS, smem, P.stream>>>(
       P.pairs, P.npairs, P.lmax, P.rc, P.rc32, P.rg, P.seed_l, P.seed_u, xs, F, st,
       lstatic);
 }
@@ -1114,7 +1173,9 @@ wf_status launch_legendre_synth(const Plan &P, const T2 *xs, T2 *F,
   ++P.nlaunch;
   if constexpr (sizeof(T) == 4) {
     if (P.syn_x2) {
-      if (np == 4)
+      if (P.syn_x2 == 2)
+        synth_variant<T, 2, true, true>(P, xs, F, st, lstatic);
+      else if (np == 4)
         synth_variant<T, 4, true>(P, xs, F, st, lstatic);
       else
         synth_variant<T, 2, true>(P, xs, F, st, lstatic);
@@ -1218,9 +1279,9 @@ wf_status launch_legendre_anal_dd(const Plan &P, const double2 *G, double2 *x,
   return WF_OK;
 }
 
-template <typename T, int NP, bool X2 = false>
+template <typename T, int NP, bool X2 = false, bool DUP = false>
 static cudaError_t set_big_smem_synth(int big) {
-  return cudaFuncSetAttribute(k_legendre_synth<T, NP, X2>,
+  return cudaFuncSetAttribute(k_legendre_synth<T, NP, X2, DUP>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 template <typename T, int NP, bool X2 = false, bool GACC = false>
@@ -1247,6 +1308,7 @@ wf_status init_legendre_attributes() {
   WF_CUDA((set_big_smem_anal<float, 16>(big)));
   WF_CUDA((set_big_smem_synth<float, 2, true>(big)));
   WF_CUDA((set_big_smem_synth<float, 4, true>(big)));
+  WF_CUDA((set_big_smem_synth<float, 2, true, true>(big)));
   WF_CUDA((set_big_smem_anal<float, 4, true>(big)));
   WF_CUDA((set_big_smem_anal<float, 8, true>(big)));
   WF_CUDA((set_big_smem_anal<float, 6, true>(big)));

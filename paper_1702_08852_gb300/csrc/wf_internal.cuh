@@ -121,7 +121,8 @@ struct Plan {
   // FP32 analysis scheduling: 0 = one CTA per m, 1 = warps take (m, tile)
   // items from a queue and a combine kernel sums the tiles (ana_scratch)
   int ana_queue = 0;
-  // FP32 kernels on packed f32x2 pairs of rings (NP even): 0 / 1
+  // FP32 kernels on packed f32x2 pairs of rings (NP even): 0 / 1 (synthesis:
+  // 2 = packed with duplicated shared-memory tables)
   int syn_x2 = 0, ana_x2 = 0;
   // packed per-m FP32 analysis with its per-warp accumulators in global
   // scratch (ana_scratch rows [warp][alm]) instead of shared memory
@@ -130,7 +131,7 @@ struct Plan {
   int *ana_lstart = nullptr;     // [lmax+1][tiles] first l written per item
   int *ana_counter = nullptr;    // the queue's next item (reset by the combine)
   int num_sms = 0;
-  float tune_syn_ms[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};
+  float tune_syn_ms[2][6] = {{-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}};
   float tune_ana_ms[2][11] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
                               {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1}};
 
