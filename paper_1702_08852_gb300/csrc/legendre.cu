@@ -13,15 +13,20 @@
 // (lam = g u, tables from plan.cu) from FP64 seeds at the first l where
 // |lam| >= 2^-100, so no value ever leaves the normal range of FP32 or FP64.
 //
-// Work split: synthesis -- one CTA row per m, one thread per 2 ring pairs,
+// Work split: synthesis -- one CTA row per m, one thread per NP ring pairs,
 // a warp-uniform loop over l (pairs with a later seed stay at u = 0 until
-// their seed is injected).  Analysis -- one CTA per m, warps own ring pairs,
-// each warp accumulates 16 l values x (re, im) per lane and reduces them
-// across the warp with a 31-shuffle transpose-reduction; per-warp partial
-// sums live in shared memory and are combined in a fixed order at the end
-// (deterministic).  The analysis of the solver fuses the truncated-spectrum
-// filter f_l = Sbar_l / (Sbar_l + xi Omega), Sbar_l = max(C_l - mu Omega, 0)
-// (Eq. 15, App. B) and the partial sums of the Cauchy norms.
+// their seed is injected).  Analysis -- one CTA per m, warps own tiles of
+// ring pairs, each warp accumulates 16 l values x (re, im) per lane and
+// reduces them across the warp with a 31-shuffle transpose-reduction; per-warp
+// partial sums (shared memory, or global scratch rows) are combined in a
+// fixed order at the end (deterministic).  The analysis of the solver fuses
+// the truncated-spectrum filter f_l = Sbar_l / (Sbar_l + xi Omega), Sbar_l =
+// max(C_l - mu Omega, 0) (Eq. 15, App. B) and the partial sums of the Cauchy
+// norms.  Launch variants (pairs per thread, packed f32x2 pairs of rings,
+// queue scheduling, global accumulators) are picked per geometry by the
+// autotuner; the FP32 variants run the sign-folded recurrence below, and the
+// double-float kernels at the end of the file serve the mixed solver's
+// anchor steps.
 #include <limits.h>
 
 #include <algorithm>
