@@ -560,12 +560,9 @@ static wf_status launch_ring_mode(const Plan &P, const T2 *F, T2 *G,
     // the FFT buffer and the partial-sum area
     const size_t base_smem = sizeof(T2) * (Mg + (nmin < threads ? 2 * threads : 0));
     const size_t stage_bytes = sizeof(T2) * 2 * (P.lmax + 1);
-    // Polar group only (its CTAs are register-limited to 2 per SM, so the
-    // extra shared memory costs no occupancy; the equatorial group would drop
-    // from 4 to 3 CTAs per SM, measured slower), and not when it would not
-    // fit the block's shared memory: the fold then reads global memory.
-    const bool stage =
-        MODE != RING_ANALYSIS && g == 0 && base_smem + stage_bytes <= 220 * 1024;
+    // (not when it would not fit the block's shared memory: the fold then
+    // reads global memory directly)
+    const bool stage = MODE != RING_ANALYSIS && base_smem + stage_bytes <= 220 * 1024;
     const int stage_ofs = stage ? Mg + (nmin < threads ? 2 * threads : 0) : 0;
     const size_t smem = base_smem + (stage ? stage_bytes : 0);
     cudaStream_t s = (fork && g == 1) ? P.side_stream : P.stream;
