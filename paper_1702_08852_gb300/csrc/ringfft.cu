@@ -277,17 +277,6 @@ __device__ __forceinline__ T2 fold(const T2 *__restrict__ Fr, int k, int n, int 
   return cmul(acc, ph);
 }
 
-// asynchronous global -> shared copy of one complex value (8 or 16 bytes;
-// both addresses naturally aligned)
-template <typename T2>
-__device__ __forceinline__ void cp_async_t2(T2 *dst, const T2 *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  if constexpr (sizeof(T2) == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-
 // threads per ring pair: 512 for launches whose largest FFT has 8192 or more
 // points (the polar Bluestein rings at Nside >= 1024: more warps to hide the
 // latency of the table and twiddle loads at 3 CTAs per SM), else 256
@@ -302,8 +291,7 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
            const double *__restrict__ nvar, const T2 *__restrict__ tw, int Mmax,
            const T2 *__restrict__ chirp_all, const T2 *__restrict__ bhat_all,
            const SolverState *__restrict__ st, int lstatic, int reverse,
-           const float *__restrict__ in32, const float *__restrict__ nv32, int red_ofs,
-           int stage_ofs) {
+           const float *__restrict__ in32, const float *__restrict__ nv32, int red_ofs) {
   typedef typename CT<T2>::T T;
   // reverse: the polar rings grow with the pair index; taking the largest
   // first keeps the small ones for the tail of the launch
@@ -340,21 +328,6 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
   if (MODE != RING_ANALYSIS) {
     const T2 *FN = F + rp.ringN * stride;
     const T2 *FS = south ? F + rp.ringS * stride : nullptr;
-    if (stage_ofs > 0 && Lf >= 0) {
-      // stage the ring pair's two rows F[0..Lf] into shared memory with
-      // asynchronous copies: every load of the fold in flight at once, no
-      // registers held, one wait
-      T2 *sN = buf + stage_ofs, *sS = sN + (Lf + 1);
-      for (int m = threadIdx.x; m <= Lf; m += blockDim.x) {
-        cp_async_t2(sN + m, FN + m);
-        if (south) cp_async_t2(sS + m, FS + m);
-      }
-      asm volatile("cp.async.commit_group;\n" ::: "memory");
-      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-      __syncthreads();
-      FN = sN;
-      FS = south ? sS : nullptr;
-    }
     if (n < (int)blockDim.x) {
       // small rings (n < threads): each k's sums over j are split across
       // P = threads / n threads (j = part mod P), whose partials are added
@@ -556,21 +529,13 @@ static wf_status launch_ring_mode(const Plan &P, const T2 *F, T2 *G,
     // rings with fewer pixels than threads fold through a partial-sum area
     // of 2 x threads entries placed after the FFT buffer
     const int red_ofs = nmin < threads ? Mg : 0;
-    // synthesis and fused modes stage the two F rows (lmax + 1 each) after
-    // the FFT buffer and the partial-sum area
-    const size_t base_smem = sizeof(T2) * (Mg + (nmin < threads ? 2 * threads : 0));
-    const size_t stage_bytes = sizeof(T2) * 2 * (P.lmax + 1);
-    // (not when it would not fit the block's shared memory: the fold then
-    // reads global memory directly)
-    const bool stage = MODE != RING_ANALYSIS && base_smem + stage_bytes <= 220 * 1024;
-    const int stage_ofs = stage ? Mg + (nmin < threads ? 2 * threads : 0) : 0;
-    const size_t smem = base_smem + (stage ? stage_bytes : 0);
+    const size_t smem = sizeof(T2) * (Mg + (nmin < threads ? 2 * threads : 0));
     cudaStream_t s = (fork && g == 1) ? P.side_stream : P.stream;
     ++P.nlaunch;
     kern<<<e - b, threads, smem, s>>>(
         P.pairs, b, P.lmax, F, G, in_map, out_map, P.nvar, Tables<T2>::tw(P),
         P.fftMmax, Tables<T2>::ch(P), Tables<T2>::bh(P), st, lstatic, g == 0, in32,
-        P.nvar32, red_ofs, stage_ofs);
+        P.nvar32, red_ofs);
     WF_CUDA(cudaGetLastError());
   }
   if (fork) {
