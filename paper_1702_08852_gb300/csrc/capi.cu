@@ -398,7 +398,7 @@ wf_status wf_get_tuning(wf_plan_t plan, wf_tuning *out) {
     out->syn_np[k] = plan->syn_np[k];
     out->ana_np[k] = plan->ana_np[k];
     for (int c = 0; c < 6; ++c) out->syn_ms[k][c] = plan->tune_syn_ms[k][c];
-    for (int c = 0; c < 11; ++c) out->ana_ms[k][c] = plan->tune_ana_ms[k][c];
+    for (int c = 0; c < 13; ++c) out->ana_ms[k][c] = plan->tune_ana_ms[k][c];
   }
   out->syn_packed = plan->syn_x2;
   out->ana_queue = plan->ana_queue;
@@ -425,10 +425,12 @@ wf_status wf_set_tuning(wf_plan_t plan, const wf_tuning *in) {
     return arg_error("wf_set_tuning: ana_queue, ana_packed must be 0 or 1, syn_packed 0, 1 or 2");
   if (in->ana_queue && in->ana_packed)
     return arg_error("wf_set_tuning: ana_queue and ana_packed exclude each other");
-  if (!one_of(in->ana_global_acc, {0, 1}))
-    return arg_error("wf_set_tuning: ana_global_acc must be 0 or 1");
-  if (in->ana_global_acc && !(in->ana_packed && one_of(in->ana_np[1], {4, 6})))
-    return arg_error("wf_set_tuning: ana_global_acc needs ana_packed with ana_np 4 or 6");
+  if (!one_of(in->ana_global_acc, {0, 1, 2}))
+    return arg_error("wf_set_tuning: ana_global_acc must be 0, 1 or 2");
+  if (in->ana_global_acc == 1 && !(in->ana_packed && one_of(in->ana_np[1], {4, 6})))
+    return arg_error("wf_set_tuning: ana_global_acc 1 needs ana_packed with ana_np 4 or 6");
+  if (in->ana_global_acc == 2 && !(in->ana_packed && one_of(in->ana_np[1], {6, 8})))
+    return arg_error("wf_set_tuning: ana_global_acc 2 needs ana_packed with ana_np 6 or 8");
   if (in->ana_queue ? !one_of(in->ana_np[1], {4, 8})
                     : in->ana_packed ? !one_of(in->ana_np[1], {4, 6, 8})
                                      : !one_of(in->ana_np[1], {2, 4, 8, 16}))

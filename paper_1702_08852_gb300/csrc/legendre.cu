@@ -362,6 +362,27 @@ constexpr int ANA_WARPS = ANA_THREADS / 32;
 constexpr int LCHUNK = 16;
 
 
+// v[0..NV) per lane (NV = 16 or 32) -> lane i returns the sum over lanes of
+// v[i / R], R = 32 / NV (R lanes end with each value)
+template <typename T, int NV>
+__device__ __forceinline__ T transpose_reduce(T (&v)[NV], int lane) {
+  constexpr int R = 32 / NV;
+#pragma unroll
+  for (int s = 16; s >= R; s >>= 1) {
+    const int h = s / R;
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const T send = upper ? v[j] : v[j + h];
+      const T keep = upper ? v[j + h] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+#pragma unroll
+  for (int s = R / 2; s >= 1; s >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], s);
+  return v[0];
+}
+
 // v[0..31] per lane -> lane i returns sum over lanes of v[i]
 template <typename T>
 __device__ __forceinline__ T transpose_reduce32(T (&v)[32], int lane) {
@@ -384,8 +405,8 @@ __device__ __forceinline__ T transpose_reduce32(T (&v)[32], int lane) {
 // chunk.  TAIL: the chunk runs past L (l > L contributes 0).  In FP32 full
 // chunks the coefficients c_l come from shared memory in 16-byte loads
 // (lc - m is a multiple of LCHUNK and the table starts 16-byte aligned).
-template <typename T, int NP, bool INJ, bool TAIL, bool X2 = false>
-__device__ __forceinline__ void anal_chunk(T (&v)[32], int lc, int L, int m,
+template <typename T, int NP, bool INJ, bool TAIL, bool X2 = false, int LC = LCHUNK>
+__device__ __forceinline__ void anal_chunk(T (&v)[2 * LC], int lc, int L, int m,
                                            const T *__restrict__ sc, const T (&zh)[NP],
                                            const T (&zl)[NP], T (&u1)[NP], T (&u2)[NP],
                                            const T (&s0)[NP], const T (&s1)[NP],
@@ -394,17 +415,17 @@ __device__ __forceinline__ void anal_chunk(T (&v)[32], int lc, int L, int m,
                                            const T (&qim)[NP]) {
   // FP32 full chunks: the 16 coefficients in four 16-byte loads
   constexpr bool VEC = sizeof(T) == 4 && !TAIL;
-  T cc[VEC ? LCHUNK : 1];
+  T cc[VEC ? LC : 1];
   if constexpr (VEC) {
     const uint4 *s4 = reinterpret_cast<const uint4 *>(sc + (lc - m));
 #pragma unroll
-    for (int q = 0; q < LCHUNK / 4; ++q) {
+    for (int q = 0; q < LC / 4; ++q) {
       const uint4 w = s4[q];
       memcpy(&cc[4 * q], &w, 16);
     }
   }
 #pragma unroll
-  for (int jj = 0; jj < LCHUNK; ++jj) {
+  for (int jj = 0; jj < LC; ++jj) {
     const int l = lc + jj;
     // two partial sums (even, odd j) halve the dependent FMA chain
     T a_re = (T)0, a_im = (T)0, b_re = (T)0, b_im = (T)0;
@@ -574,7 +595,8 @@ __device__ __forceinline__ void anal_partials(double num, double den, int m,
 // [warp][alm], L2-resident) instead of shared memory, so shared memory no
 // longer caps the CTAs per SM; each chunk's old value is loaded before the
 // chunk's arithmetic and written back after its reduction.
-template <typename T, int NP, bool X2 = false, bool GACC = false>
+// LC: l values per chunk (16, or 8 to free registers for more ring pairs)
+template <typename T, int NP, bool X2 = false, bool GACC = false, int LC = LCHUNK>
 __global__ void __launch_bounds__(ANA_THREADS)
     k_legendre_anal(const RingPair *__restrict__ pairs, int npairs, int lmax,
                     const double *__restrict__ rc, const float *__restrict__ rc32,
@@ -658,28 +680,31 @@ __global__ void __launch_bounds__(ANA_THREADS)
       lmin = warp_min(lmin);
       linj = warp_max(linj);
       if (lmin > L) continue;
-      const int lc0 = m + ((lmin - m) / LCHUNK) * LCHUNK;
-      for (int lc = lc0; lc <= L; lc += LCHUNK) {
-        T v[32];
+      const int lc0 = m + ((lmin - m) / LC) * LC;
+      constexpr int R = 16 / LC;  // lanes holding each reduced value
+      for (int lc = lc0; lc <= L; lc += LC) {
+        T v[2 * LC];
         // three specialisations of the chunk body: seeds still to come in
         // this warp (selects on every step), a full chunk with every seed of
         // the warp already in (the plain recurrence: 5 FP instructions per
         // term), and the last, partial chunk
-        const int lmine = lc + (lane >> 1);  // this lane's l after the reduction
-        T *mine = reinterpret_cast<T *>(myacc + (lmine - m)) + (lane & 1);
+        const int idx = lane / R;             // this lane's value after the reduction
+        const int lmine = lc + (idx >> 1);
+        const bool writer = (lane % R) == 0;
+        T *mine = reinterpret_cast<T *>(myacc + (lmine - m)) + (idx & 1);
         T old = (T)0;
-        if (GACC && lmine <= L) old = *mine;  // in flight during the chunk
-        if (lc + LCHUNK - 1 > L)
-          anal_chunk<T, NP, true, true, X2>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
-                                        pr, pim, qr, qim);
+        if (GACC && writer && lmine <= L) old = *mine;  // in flight during the chunk
+        if (lc + LC - 1 > L)
+          anal_chunk<T, NP, true, true, X2, LC>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
+                                                pr, pim, qr, qim);
         else if (lc <= linj)
-          anal_chunk<T, NP, true, false, X2>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
-                                         pr, pim, qr, qim);
+          anal_chunk<T, NP, true, false, X2, LC>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1,
+                                                 ls, pr, pim, qr, qim);
         else
-          anal_chunk<T, NP, false, false, X2>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
-                                          pr, pim, qr, qim);
-        const T tot = transpose_reduce32<T>(v, lane);
-        if (lmine <= L) {
+          anal_chunk<T, NP, false, false, X2, LC>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1,
+                                                  ls, pr, pim, qr, qim);
+        const T tot = transpose_reduce<T, 2 * LC>(v, lane);
+        if (writer && lmine <= L) {
           if constexpr (GACC)
             *mine = old + tot;
           else
@@ -1124,14 +1149,14 @@ static void synth_variant(const Plan &P, const typename Vec2<T>::type *xs,
       lstatic);
 }
 
-template <typename T, int NP, bool X2 = false, bool GACC = false>
+template <typename T, int NP, bool X2 = false, bool GACC = false, int LC = LCHUNK>
 static void anal_variant(const Plan &P, const typename Vec2<T>::type *G, double2 *x,
                          const SolverState *st, int mode, int lstatic, const double2 *src,
                          typename Vec2<T>::type *xs_out) {
   typedef typename Vec2<T>::type T2;
   const size_t smem = (GACC ? 0 : align16(sizeof(T2) * (P.lmax + 1) * ANA_WARPS)) +
                       sizeof(T) * (P.lmax + 1);
-  k_legendre_anal<T, NP, X2, GACC><<<P.lmax + 1, ANA_THREADS, smem, P.stream>>>(
+  k_legendre_anal<T, NP, X2, GACC, LC><<<P.lmax + 1, ANA_THREADS, smem, P.stream>>>(
       P.pairs, P.npairs, P.lmax, P.rc, P.rc32, P.rg, P.seed_l, P.seed_u, P.cl_d, P.omega,
       G, x, P.partials, src, xs_out, st, mode, lstatic,
       GACC ? reinterpret_cast<T *>(P.ana_scratch) : nullptr, P.nalm);
@@ -1211,6 +1236,14 @@ wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
       return np == 4 ? anal_queue_variant<4>(P, g, x, st, mode, lstatic, src, xo)
                      : anal_queue_variant<8>(P, g, x, st, mode, lstatic, src, xo);
     }
+    if (P.ana_x2 && P.ana_gacc == 2) {  // 8-l chunks
+      if (np == 8)
+        anal_variant<T, 8, true, true, 8>(P, G, x, st, mode, lstatic, src, xs_out);
+      else
+        anal_variant<T, 6, true, true, 8>(P, G, x, st, mode, lstatic, src, xs_out);
+      WF_CUDA(cudaGetLastError());
+      return WF_OK;
+    }
     if (P.ana_x2 && P.ana_gacc) {
       if (np == 6)
         anal_variant<T, 6, true, true>(P, G, x, st, mode, lstatic, src, xs_out);
@@ -1289,9 +1322,9 @@ static cudaError_t set_big_smem_synth(int big) {
   return cudaFuncSetAttribute(k_legendre_synth<T, NP, X2, DUP>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
-template <typename T, int NP, bool X2 = false, bool GACC = false>
+template <typename T, int NP, bool X2 = false, bool GACC = false, int LC = LCHUNK>
 static cudaError_t set_big_smem_anal(int big) {
-  return cudaFuncSetAttribute(k_legendre_anal<T, NP, X2, GACC>,
+  return cudaFuncSetAttribute(k_legendre_anal<T, NP, X2, GACC, LC>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
@@ -1319,6 +1352,8 @@ wf_status init_legendre_attributes() {
   WF_CUDA((set_big_smem_anal<float, 6, true>(big)));
   WF_CUDA((set_big_smem_anal<float, 4, true, true>(big)));
   WF_CUDA((set_big_smem_anal<float, 6, true, true>(big)));
+  WF_CUDA((set_big_smem_anal<float, 8, true, true, 8>(big)));
+  WF_CUDA((set_big_smem_anal<float, 6, true, true, 8>(big)));
   WF_CUDA(cudaFuncSetAttribute(k_legendre_synth_dd,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_dd,

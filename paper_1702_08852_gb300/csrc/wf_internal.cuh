@@ -125,15 +125,16 @@ struct Plan {
   // 2 = packed with duplicated shared-memory tables)
   int syn_x2 = 0, ana_x2 = 0;
   // packed per-m FP32 analysis with its per-warp accumulators in global
-  // scratch (ana_scratch rows [warp][alm]) instead of shared memory
+  // scratch (ana_scratch rows [warp][alm]) instead of shared memory: 1 with
+  // 16-l chunks, 2 with 8-l chunks
   int ana_gacc = 0;
   float *ana_scratch = nullptr;  // [tiles of 128 pairs][nalm] float2
   int *ana_lstart = nullptr;     // [lmax+1][tiles] first l written per item
   int *ana_counter = nullptr;    // the queue's next item (reset by the combine)
   int num_sms = 0;
   float tune_syn_ms[2][6] = {{-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}};
-  float tune_ana_ms[2][11] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
-                              {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1}};
+  float tune_ana_ms[2][13] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
+                              {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1}};
 
   // FFT tables
   int fftMmax = 1;

@@ -221,7 +221,8 @@ def test_mixed_precision_reaches_fp64_fixed_point(torch_cuda, osht, odm, nside, 
 @pytest.mark.parametrize("ana_np,ana_queue,packed,gacc", [(4, 1, 0, 0), (8, 1, 0, 0),
                                                           (16, 0, 0, 0), (2, 0, 0, 0),
                                                           (8, 0, 1, 0), (4, 0, 1, 0),
-                                                          (6, 0, 1, 0), (4, 0, 1, 1)])
+                                                          (6, 0, 1, 0), (4, 0, 1, 1),
+                                                          (8, 0, 1, 2)])
 def test_mixed_precision_variants_reach_fp64_fixed_point(torch_cuda, osht, odm, ana_np,
                                                          ana_queue, packed, gacc):
     """The same check with the FP32 analysis forced to each launch variant
