@@ -125,7 +125,7 @@ def measured_peaks():
 # variant the autotuner picks at Nside 1024 / lmax 2048 (kernel-case capture,
 # profiles/legendre_f32_nside1024.md); scaled to a live launch by its share
 # of the full band's terms.  None once the kernel changes after a capture.
-ANALYSIS_DRAM_FULL_BAND = {"nside": 1024, "bytes": 179246080.0 + 79453440.0,
+ANALYSIS_DRAM_FULL_BAND = {"nside": 1024, "bytes": 137106944.0 + 71930624.0,
                            "terms": 3140761977.0}
 
 

@@ -255,15 +255,17 @@ wf_status wf_kernel_stats(wf_plan_t plan, int kernel, double *ms, long *launches
  *  ana_packed  FP32 per-m analysis on packed f32x2 pairs (ana_np 4, 6, 8).
  *  ana_global_acc  with ana_packed: the per-warp accumulators in global
  *              scratch instead of shared memory (more CTAs/SM); 1: ana_np 4,
- *              6 with 16-l chunks, 2: ana_np 6, 8 with 8-l chunks.
+ *              6 with 16-l chunks, 2: ana_np 4, 6, 8 with 8-l chunks, 3:
+ *              ana_np 8 with 8-l chunks and the seeds in shared memory.
  *  syn_ms      candidates 1, 2, 4 pairs per thread, then (FP32) packed 2, 4
  *              and packed with duplicated tables 2: ms for two launches.
  *  ana_ms      candidates 2, 4, 8, 16 pairs per lane, then (FP32 only) queue
  *              4, 8, packed 4, 8, 6, packed with global accumulators 4, 6
- *              and the same with 8-l chunks 8, 6: ms for two launches. */
+ *              and the same with 8-l chunks 8, 6, 4 and with shared seeds 8:
+ *              ms for two launches. */
 typedef struct {
   int syn_np[2], syn_packed, ana_np[2], ana_queue, ana_packed, ana_global_acc;
-  float syn_ms[2][6], ana_ms[2][13];
+  float syn_ms[2][6], ana_ms[2][15];
 } wf_tuning;
 wf_status wf_get_tuning(wf_plan_t plan, wf_tuning *out);
 /* Set the launch variants (the int fields of *in; the ms fields are
@@ -271,7 +273,7 @@ wf_status wf_get_tuning(wf_plan_t plan, wf_tuning *out);
  * ana_queue, ana_packed 0 or 1, syn_packed 0, 1 or 2; ana_queue and ana_packed not both;
  * syn_packed 1 needs syn_np[1] in {2, 4}, syn_packed 2 needs syn_np[1] = 2; ana_queue needs ana_np[1] in {4, 8},
  * ana_packed in {4, 6, 8}; ana_global_acc 1 needs ana_packed and ana_np[1]
- * in {4, 6}, ana_global_acc 2 ana_packed and ana_np[1] in {6, 8}.  The plan's captured iteration graphs are dropped and
+ * in {4, 6}, ana_global_acc 2 ana_packed and ana_np[1] in {4, 6, 8}, ana_global_acc 3 ana_packed and ana_np[1] = 8.  The plan's captured iteration graphs are dropped and
  * re-captured on the next solve.  Errors: WF_ERR_ARG for NULL or a value
  * outside these sets (the plan is unchanged). */
 wf_status wf_set_tuning(wf_plan_t plan, const wf_tuning *in);

@@ -18,7 +18,7 @@ namespace wf {
 namespace {
 struct Choice {
   int syn[2], ana[2], ana_queue, syn_x2, ana_x2, ana_gacc;
-  float syn_ms[2][6], ana_ms[2][13];  // the timings the choice was made from
+  float syn_ms[2][6], ana_ms[2][15];  // the timings the choice was made from
 };
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, Choice> g_tune_cache;
@@ -110,14 +110,15 @@ wf_status autotune(Plan &P) {
     // FP32 also tries the queue-scheduled analysis (slots 4, 5: 4 and 8
     // pairs per lane), the packed f32x2 one (slots 6, 7, 8: 4, 8, 6), the
     // packed one with global accumulators (slots 9, 10: 4, 6) and the same
-    // with 8-l chunks (slots 11, 12: 8, 6)
-    const int ntot = k ? 13 : 3;
-    static const int x2_np[7] = {4, 8, 6, 4, 6, 8, 6};
+    // with 8-l chunks (slots 11, 12, 13: 8, 6, 4), the last also with the
+    // seeds in shared memory (slot 14: 8)
+    const int ntot = k ? 15 : 3;
+    static const int x2_np[9] = {4, 8, 6, 4, 6, 8, 6, 4, 8};
     for (int i = 0; i < ntot && st == WF_OK; ++i) {
       const bool q = k && i >= 4 && i < 6, x2 = k && i >= 6, ga = k && i >= 9;
       P.ana_queue = q ? 1 : 0;
       P.ana_x2 = x2 ? 1 : 0;
-      P.ana_gacc = ga ? (i >= 11 ? 2 : 1) : 0;
+      P.ana_gacc = ga ? (i >= 14 ? 3 : i >= 11 ? 2 : 1) : 0;
       P.ana_np[k] = q ? ((i & 1) ? 8 : 4) : x2 ? x2_np[i - 6] : cand[i];
       float ms = 0.f;
       st = k ? time_anal<float2>(P, P.G32, e0, e1, &ms)

@@ -35,7 +35,8 @@ static void free_plan(wf_plan_s *P) {
                   P->x,      P->xtmp,  P->dmap,    P->mtmp,   P->partials, P->red,
                   P->state,  P->trace, P->xacc,  P->src, P->xs64, P->xs32,
                   P->nvar32, P->dmap32, P->ana_scratch, P->ana_lstart,
-                  P->ana_counter, P->uacc[0], P->uacc[1], P->src2};
+                  P->ana_counter, P->uacc[0], P->uacc[1], P->src2,
+                  P->seed_s32, P->zs32, P->rg32, P->cl32};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (P->state_h) cudaFreeHost(P->state_h);
@@ -222,7 +223,10 @@ wf_status wf_set_cl(wf_plan_t plan, const double *cl_host) {
     if (!(cl_host[l] >= 0.0) || isinf(cl_host[l]))
       return arg_error("wf_set_cl: C_l must be finite and >= 0");
   plan->cl.assign(cl_host, cl_host + plan->lmax + 1);
+  const std::vector<float> cl32(plan->cl.begin(), plan->cl.end());
   WF_CUDA(cudaMemcpyAsync(plan->cl_d, plan->cl.data(), sizeof(double) * (plan->lmax + 1),
+                          cudaMemcpyHostToDevice, plan->stream));
+  WF_CUDA(cudaMemcpyAsync(plan->cl32, cl32.data(), sizeof(float) * (plan->lmax + 1),
                           cudaMemcpyHostToDevice, plan->stream));
   WF_CUDA(cudaStreamSynchronize(plan->stream));
   return WF_OK;
@@ -398,7 +402,7 @@ wf_status wf_get_tuning(wf_plan_t plan, wf_tuning *out) {
     out->syn_np[k] = plan->syn_np[k];
     out->ana_np[k] = plan->ana_np[k];
     for (int c = 0; c < 6; ++c) out->syn_ms[k][c] = plan->tune_syn_ms[k][c];
-    for (int c = 0; c < 13; ++c) out->ana_ms[k][c] = plan->tune_ana_ms[k][c];
+    for (int c = 0; c < 15; ++c) out->ana_ms[k][c] = plan->tune_ana_ms[k][c];
   }
   out->syn_packed = plan->syn_x2;
   out->ana_queue = plan->ana_queue;
@@ -425,12 +429,14 @@ wf_status wf_set_tuning(wf_plan_t plan, const wf_tuning *in) {
     return arg_error("wf_set_tuning: ana_queue, ana_packed must be 0 or 1, syn_packed 0, 1 or 2");
   if (in->ana_queue && in->ana_packed)
     return arg_error("wf_set_tuning: ana_queue and ana_packed exclude each other");
-  if (!one_of(in->ana_global_acc, {0, 1, 2}))
-    return arg_error("wf_set_tuning: ana_global_acc must be 0, 1 or 2");
+  if (!one_of(in->ana_global_acc, {0, 1, 2, 3}))
+    return arg_error("wf_set_tuning: ana_global_acc must be 0, 1, 2 or 3");
   if (in->ana_global_acc == 1 && !(in->ana_packed && one_of(in->ana_np[1], {4, 6})))
     return arg_error("wf_set_tuning: ana_global_acc 1 needs ana_packed with ana_np 4 or 6");
-  if (in->ana_global_acc == 2 && !(in->ana_packed && one_of(in->ana_np[1], {6, 8})))
-    return arg_error("wf_set_tuning: ana_global_acc 2 needs ana_packed with ana_np 6 or 8");
+  if (in->ana_global_acc == 2 && !(in->ana_packed && one_of(in->ana_np[1], {4, 6, 8})))
+    return arg_error("wf_set_tuning: ana_global_acc 2 needs ana_packed with ana_np 4, 6 or 8");
+  if (in->ana_global_acc == 3 && !(in->ana_packed && in->ana_np[1] == 8))
+    return arg_error("wf_set_tuning: ana_global_acc 3 needs ana_packed with ana_np 8");
   if (in->ana_queue ? !one_of(in->ana_np[1], {4, 8})
                     : in->ana_packed ? !one_of(in->ana_np[1], {4, 6, 8})
                                      : !one_of(in->ana_np[1], {2, 4, 8, 16}))

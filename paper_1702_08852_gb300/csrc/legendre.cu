@@ -141,6 +141,26 @@ __device__ __forceinline__ void split_z(double z, T &zh, T &zl) {
   zh = (T)z;
   zl = (T)(z - (double)zh);
 }
+// z (as zh + zl) and the two seed values of ring pair k at (m, k) = mk: FP32
+// from the plan's FP32 tables (s-units), FP64 from the pair and seed_u
+template <typename T>
+__device__ __forceinline__ void ring_seed(const RingPair *__restrict__ pairs,
+                                          const double2 *__restrict__ seed_u,
+                                          const Tab32 &t32, int k, long mk, T &zh, T &zl,
+                                          T &s0, T &s1) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 s = t32.seed_s[mk];
+    zh = t32.zh[k];
+    zl = t32.zl[k];
+    s0 = s.x;
+    s1 = s.y;
+  } else {
+    split_z<T>(pairs[k].z, zh, zl);
+    const double2 su = seed_u[mk];
+    s0 = su.x;
+    s1 = su.y;
+  }
+}
 
 static inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 __device__ __forceinline__ size_t align16d(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -159,7 +179,7 @@ __global__ void __launch_bounds__(SYN_THREADS)
                      const double2 *__restrict__ seed_u,
                      const typename Vec2<T>::type *__restrict__ xs,
                      typename Vec2<T>::type *__restrict__ F,
-                     const SolverState *__restrict__ st, int lstatic) {
+                     const SolverState *__restrict__ st, int lstatic, const Tab32 t32) {
   typedef typename Vec2<T>::type T2;
   const int m = blockIdx.y;
   int L = lstatic;
@@ -201,11 +221,8 @@ __global__ void __launch_bounds__(SYN_THREADS)
     const int k = pair0 + lane + 32 * j;
     u1[j] = u2[j] = er[j] = ei[j] = orr[j] = oi[j] = (T)0;
     if (k < npairs) {
-      split_z<T>(pairs[k].z, zh[j], zl[j]);
       ls[j] = seed_l[(long)m * npairs + k];
-      const double2 su = seed_u[(long)m * npairs + k];
-      s0[j] = (T)(fold_sign<T>(ls[j]) * su.x);
-      s1[j] = (T)(fold_sign<T>(ls[j] + 1) * su.y);
+      ring_seed<T>(pairs, seed_u, t32, k, (long)m * npairs + k, zh[j], zl[j], s0[j], s1[j]);
     } else {
       zh[j] = zl[j] = (T)0;
       ls[j] = INT_MAX - 2;
@@ -405,14 +422,19 @@ __device__ __forceinline__ T transpose_reduce32(T (&v)[32], int lane) {
 // chunk.  TAIL: the chunk runs past L (l > L contributes 0).  In FP32 full
 // chunks the coefficients c_l come from shared memory in 16-byte loads
 // (lc - m is a multiple of LCHUNK and the table starts 16-byte aligned).
-template <typename T, int NP, bool INJ, bool TAIL, bool X2 = false, int LC = LCHUNK>
+// SS: the seed values are read from shared memory (ssm: this lane's entry of
+// ring 0, ring j at ssm[32 j]) where a seed may enter, instead of being held
+// in registers for the whole tile.
+template <typename T, int NP, bool INJ, bool TAIL, bool X2 = false, int LC = LCHUNK,
+          bool SS = false>
 __device__ __forceinline__ void anal_chunk(T (&v)[2 * LC], int lc, int L, int m,
                                            const T *__restrict__ sc, const T (&zh)[NP],
                                            const T (&zl)[NP], T (&u1)[NP], T (&u2)[NP],
                                            const T (&s0)[NP], const T (&s1)[NP],
                                            const int (&ls)[NP], const T (&pr)[NP],
                                            const T (&pim)[NP], const T (&qr)[NP],
-                                           const T (&qim)[NP]) {
+                                           const T (&qim)[NP],
+                                           const float2 *__restrict__ ssm = nullptr) {
   // FP32 full chunks: the 16 coefficients in four 16-byte loads
   constexpr bool VEC = sizeof(T) == 4 && !TAIL;
   T cc[VEC ? LC : 1];
@@ -450,10 +472,18 @@ __device__ __forceinline__ void anal_chunk(T (&v)[2 * LC], int lc, int L, int m,
           rec_step2(c, zh[j0], zh[j1], zl[j0], zl[j1], u1[j0], u1[j1], u2[j0], u2[j1], w0,
                     w1);
           if (INJ) {
-            w0 = (l == ls[j0]) ? s0[j0] : w0;
-            w0 = (l == ls[j0] + 1) ? s1[j0] : w0;
-            w1 = (l == ls[j1]) ? s0[j1] : w1;
-            w1 = (l == ls[j1] + 1) ? s1[j1] : w1;
+            if constexpr (SS) {
+              const float2 e0 = ssm[32 * j0], e1 = ssm[32 * j1];
+              w0 = (l == ls[j0]) ? e0.x : w0;
+              w0 = (l == ls[j0] + 1) ? e0.y : w0;
+              w1 = (l == ls[j1]) ? e1.x : w1;
+              w1 = (l == ls[j1] + 1) ? e1.y : w1;
+            } else {
+              w0 = (l == ls[j0]) ? s0[j0] : w0;
+              w0 = (l == ls[j0] + 1) ? s1[j0] : w0;
+              w1 = (l == ls[j1]) ? s0[j1] : w1;
+              w1 = (l == ls[j1] + 1) ? s1[j1] : w1;
+            }
           }
           u2[j0] = u1[j0];
           u2[j1] = u1[j1];
@@ -546,6 +576,40 @@ __device__ __forceinline__ void anal_finish(long i, int l, double sr, double si,
   }
 }
 
+// The same epilogue for the FP32 kernels in FP32 arithmetic (this part's
+// FP64 pipe is ~1/64 of its FP32 pipe, and a division per coefficient
+// showed): ring sums in s-units times Omega g_l eps_l, the filter from the
+// FP32 C_l, om = Omega, xio = xi Omega, muo = mu Omega.  Only the Cauchy
+// differences against the FP64 iterate stay in FP64 (unweighted: the
+// caller multiplies by wm once).
+__device__ __forceinline__ void anal_finish32(long i, int l, float sr, float si, int mode,
+                                              const Tab32 &t32, float om, float xio,
+                                              float muo, const double2 *__restrict__ src,
+                                              double2 *__restrict__ x,
+                                              float2 *__restrict__ xs_out, double &num,
+                                              double &den) {
+  const float g = t32.rg[i];
+  float ar = om * (g * sr), ai = om * (g * si);
+  if (mode == ANA_FILTER) {
+    const float sbar = fmaxf(t32.cl[l] - muo, 0.f);
+    const float f = sbar > 0.f ? sbar / (sbar + xio) : 0.f;
+    if (src) {  // harmonic source term of a correction solve
+      const double2 sv = src[i];
+      ar = fmaf(xio, (float)sv.x, ar);
+      ai = fmaf(xio, (float)sv.y, ai);
+    }
+    ar *= f;
+    ai *= f;
+    const double2 old = x[i];
+    const double ard = ar, aid = ai;
+    const double dr = ard - old.x, di = aid - old.y;
+    num = fma(dr, dr, fma(di, di, num));
+    den = fma(ard, ard, fma(aid, aid, den));
+  }
+  x[i] = make_double2(ar, ai);
+  if (xs_out) xs_out[i] = make_float2(g * ar, g * ai);  // the synthesis input
+}
+
 // coefficients of this m above the band (l > L) are zero
 template <typename T>
 __device__ __forceinline__ void anal_zero_above(int m, int L, int lmax, long base,
@@ -595,10 +659,13 @@ __device__ __forceinline__ void anal_partials(double num, double den, int m,
 // [warp][alm], L2-resident) instead of shared memory, so shared memory no
 // longer caps the CTAs per SM; each chunk's old value is loaded before the
 // chunk's arithmetic and written back after its reduction.
-// LC: l values per chunk (16, or 8 to free registers for more ring pairs)
-template <typename T, int NP, bool X2 = false, bool GACC = false, int LC = LCHUNK>
-__global__ void __launch_bounds__(ANA_THREADS)
-    k_legendre_anal(const RingPair *__restrict__ pairs, int npairs, int lmax,
+// LC: l values per chunk (16, or 8 to free registers for more ring pairs).
+// SS (with GACC): each lane's seed values go to shared memory after the
+// tile load (the lane reads back only its own entries), freeing 2 NP
+// registers; that kernel is compiled for 4 CTAs per SM.
+template <typename T, int NP, bool X2, bool GACC, int LC, bool SS>
+__device__ __forceinline__ void
+    anal_body(const RingPair *__restrict__ pairs, int npairs, int lmax,
                     const double *__restrict__ rc, const float *__restrict__ rc32,
                     const double *__restrict__ rg, const int *__restrict__ seed_l,
                     const double2 *__restrict__ seed_u,
@@ -608,7 +675,7 @@ __global__ void __launch_bounds__(ANA_THREADS)
                     const double2 *__restrict__ src,
                     typename Vec2<T>::type *__restrict__ xs_out,
                     const SolverState *__restrict__ st, int mode, int lstatic,
-                    T *__restrict__ gacc, long nalm) {
+                    T *__restrict__ gacc, long nalm, const Tab32 &t32) {
   typedef typename Vec2<T>::type T2;
   const int m = blockIdx.x;
   int L = lstatic;
@@ -629,6 +696,10 @@ __global__ void __launch_bounds__(ANA_THREADS)
     const int nl = L - m + 1;
     T2 *acc = reinterpret_cast<T2 *>(smraw);  // [ANA_WARPS][nl]
     T *sc = reinterpret_cast<T *>(smraw + (GACC ? 0 : align16d(sizeof(T2) * nl * ANA_WARPS)));
+    static_assert(!SS || (GACC && sizeof(T) == 4), "shared seeds: FP32 with GACC");
+    float2 *ssm = SS ? reinterpret_cast<float2 *>(smraw + align16d(sizeof(T) * (lmax + 1))) +
+                           warp * 32 * NP + lane
+                     : nullptr;
     for (int j = tid; j < nl; j += ANA_THREADS) sc[j] = coef<T>(rc, rc32, base + j);
     if constexpr (GACC) {
       for (int w = 0; w < ANA_WARPS; ++w)
@@ -656,11 +727,10 @@ __global__ void __launch_bounds__(ANA_THREADS)
         u1[j] = u2[j] = (T)0;
         if (k < npairs) {
           const RingPair &rp = pairs[k];
-          split_z<T>(rp.z, zh[j], zl[j]);
           ls[j] = seed_l[(long)m * npairs + k];
-          const double2 su = seed_u[(long)m * npairs + k];
-          s0[j] = (T)(fold_sign<T>(ls[j]) * su.x);
-          s1[j] = (T)(fold_sign<T>(ls[j] + 1) * su.y);
+          ring_seed<T>(pairs, seed_u, t32, k, (long)m * npairs + k, zh[j], zl[j], s0[j],
+                       s1[j]);
+          if constexpr (SS) ssm[32 * j] = make_float2((float)s0[j], (float)s1[j]);
           const T2 gn = G[rp.ringN * stride + m];
           T2 gs = Vec2<T>::make((T)0, (T)0);
           if (rp.ringS >= 0) gs = G[rp.ringS * stride + m];
@@ -671,6 +741,7 @@ __global__ void __launch_bounds__(ANA_THREADS)
         } else {
           zh[j] = zl[j] = s0[j] = s1[j] = pr[j] = pim[j] = qr[j] = qim[j] = (T)0;
           ls[j] = INT_MAX - 2;
+          if constexpr (SS) ssm[32 * j] = make_float2(0.f, 0.f);
         }
         if (ls[j] <= L) {
           lmin = min(lmin, ls[j]);
@@ -695,14 +766,14 @@ __global__ void __launch_bounds__(ANA_THREADS)
         T old = (T)0;
         if (GACC && writer && lmine <= L) old = *mine;  // in flight during the chunk
         if (lc + LC - 1 > L)
-          anal_chunk<T, NP, true, true, X2, LC>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1, ls,
-                                                pr, pim, qr, qim);
+          anal_chunk<T, NP, true, true, X2, LC, SS>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1,
+                                                    ls, pr, pim, qr, qim, ssm);
         else if (lc <= linj)
-          anal_chunk<T, NP, true, false, X2, LC>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1,
-                                                 ls, pr, pim, qr, qim);
+          anal_chunk<T, NP, true, false, X2, LC, SS>(v, lc, L, m, sc, zh, zl, u1, u2, s0,
+                                                     s1, ls, pr, pim, qr, qim, ssm);
         else
-          anal_chunk<T, NP, false, false, X2, LC>(v, lc, L, m, sc, zh, zl, u1, u2, s0, s1,
-                                                  ls, pr, pim, qr, qim);
+          anal_chunk<T, NP, false, false, X2, LC, SS>(v, lc, L, m, sc, zh, zl, u1, u2, s0,
+                                                      s1, ls, pr, pim, qr, qim, ssm);
         const T tot = transpose_reduce<T, 2 * LC>(v, lane);
         if (writer && lmine <= L) {
           if constexpr (GACC)
@@ -715,20 +786,61 @@ __global__ void __launch_bounds__(ANA_THREADS)
     __syncthreads();
     const T2 *accr = GACC ? reinterpret_cast<const T2 *>(gacc) + base : acc;
     const long wstride = GACC ? nalm : nl;
-    for (int j = tid; j < nl; j += ANA_THREADS) {
-      double sr = 0.0, si = 0.0;
+    if constexpr (sizeof(T) == 4) {
+      const float om = (float)omega, xio = (float)(xi * omega), muo = (float)(mu * omega);
+      double nu = 0.0, de = 0.0;
+      for (int j = tid; j < nl; j += ANA_THREADS) {
+        float sr = 0.f, si = 0.f;
 #pragma unroll
-      for (int w = 0; w < ANA_WARPS; ++w) {
-        sr += (double)accr[w * wstride + j].x;
-        si += (double)accr[w * wstride + j].y;
+        for (int w = 0; w < ANA_WARPS; ++w) {
+          sr += accr[w * wstride + j].x;
+          si += accr[w * wstride + j].y;
+        }
+        anal_finish32(base + j, m + j, sr, si, mode, t32, om, xio, muo, src, x, xs_out, nu,
+                      de);
       }
-      anal_finish<T>(base + j, m + j, sr, si, wm, mode, rg, cl, omega, xi, mu, src, x,
-                     xs_out, num, den);
+      num = wm * nu;
+      den = wm * de;
+    } else {
+      for (int j = tid; j < nl; j += ANA_THREADS) {
+        double sr = 0.0, si = 0.0;
+#pragma unroll
+        for (int w = 0; w < ANA_WARPS; ++w) {
+          sr += (double)accr[w * wstride + j].x;
+          si += (double)accr[w * wstride + j].y;
+        }
+        anal_finish<T>(base + j, m + j, sr, si, wm, mode, rg, cl, omega, xi, mu, src, x,
+                       xs_out, num, den);
+      }
     }
   }
   anal_zero_above<T>(m, L, lmax, base, wm, mode, x, xs_out, num);
   if (mode == ANA_FILTER) anal_partials(num, den, m, partials);
 }
+
+#define WF_ANAL_PARAMS(T)                                                                 \
+  const RingPair *__restrict__ pairs, int npairs, int lmax, const double *__restrict__ rc, \
+      const float *__restrict__ rc32, const double *__restrict__ rg,                       \
+      const int *__restrict__ seed_l, const double2 *__restrict__ seed_u,                  \
+      const double *__restrict__ cl, double omega,                                         \
+      const typename Vec2<T>::type *__restrict__ G, double2 *__restrict__ x,              \
+      double *__restrict__ partials, const double2 *__restrict__ src,                      \
+      typename Vec2<T>::type *__restrict__ xs_out, const SolverState *__restrict__ st,     \
+      int mode, int lstatic, T *__restrict__ gacc, long nalm, const Tab32 t32
+#define WF_ANAL_ARGS                                                                       \
+  pairs, npairs, lmax, rc, rc32, rg, seed_l, seed_u, cl, omega, G, x, partials, src, xs_out, \
+      st, mode, lstatic, gacc, nalm, t32
+
+template <typename T, int NP, bool X2 = false, bool GACC = false, int LC = LCHUNK>
+__global__ void __launch_bounds__(ANA_THREADS) k_legendre_anal(WF_ANAL_PARAMS(T)) {
+  anal_body<T, NP, X2, GACC, LC, false>(WF_ANAL_ARGS);
+}
+template <int NP>
+__global__ void __launch_bounds__(ANA_THREADS, 4) k_legendre_anal_ss(WF_ANAL_PARAMS(float)) {
+  anal_body<float, NP, true, true, 8, true>(WF_ANAL_ARGS);
+}
+#undef WF_ANAL_PARAMS
+#undef WF_ANAL_ARGS
 
 // ------------------------------------------------- analysis, queue-scheduled
 // The same contraction with the work split into items (m, tile of 32 NP ring
@@ -748,7 +860,7 @@ __global__ void __launch_bounds__(ANA_THREADS)
                       const int *__restrict__ seed_l, const double2 *__restrict__ seed_u,
                       const typename Vec2<T>::type *__restrict__ G, T *__restrict__ scratch,
                       int *__restrict__ lstart, int *__restrict__ counter,
-                      const SolverState *__restrict__ st, int lstatic) {
+                      const SolverState *__restrict__ st, int lstatic, const Tab32 t32) {
   int L = lstatic;
   if (st) {
     if (st->done) return;
@@ -781,11 +893,8 @@ __global__ void __launch_bounds__(ANA_THREADS)
       u1[j] = u2[j] = (T)0;
       if (k < npairs) {
         const RingPair &rp = pairs[k];
-        split_z<T>(rp.z, zh[j], zl[j]);
         ls[j] = seed_l[(long)m * npairs + k];
-        const double2 su = seed_u[(long)m * npairs + k];
-        s0[j] = (T)(fold_sign<T>(ls[j]) * su.x);
-        s1[j] = (T)(fold_sign<T>(ls[j] + 1) * su.y);
+        ring_seed<T>(pairs, seed_u, t32, k, (long)m * npairs + k, zh[j], zl[j], s0[j], s1[j]);
         const typename Vec2<T>::type gn = G[rp.ringN * stride + m];
         typename Vec2<T>::type gs = Vec2<T>::make((T)0, (T)0);
         if (rp.ringS >= 0) gs = G[rp.ringS * stride + m];
@@ -840,7 +949,8 @@ __global__ void __launch_bounds__(ANA_THREADS)
                    double omega, double2 *__restrict__ x, double *__restrict__ partials,
                    const double2 *__restrict__ src,
                    typename Vec2<T>::type *__restrict__ xs_out,
-                   const SolverState *__restrict__ st, int mode, int lstatic) {
+                   const SolverState *__restrict__ st, int mode, int lstatic,
+                   const Tab32 t32) {
   const int m = blockIdx.x;
   int L = lstatic;
   double xi = 0.0, mu = 0.0;
@@ -855,17 +965,35 @@ __global__ void __launch_bounds__(ANA_THREADS)
   const double wm = (m == 0) ? 1.0 : 2.0;
   double num = 0.0, den = 0.0;
   if (m <= L) {
-    for (int j = threadIdx.x; j <= L - m; j += ANA_THREADS) {
-      const int l = m + j;
-      double sr = 0.0, si = 0.0;
-      for (int t = 0; t < ntiles; ++t) {
-        if (l < __ldg(lstart + (long)m * ntiles + t)) continue;
-        const T *p = scratch + 2 * ((long)t * nalm + base + j);
-        sr += (double)p[0];
-        si += (double)p[1];
+    if constexpr (sizeof(T) == 4) {  // FP32 tiles: the FP32 epilogue
+      const float om = (float)omega, xio = (float)(xi * omega), muo = (float)(mu * omega);
+      double nu = 0.0, de = 0.0;
+      for (int j = threadIdx.x; j <= L - m; j += ANA_THREADS) {
+        const int l = m + j;
+        float sr = 0.f, si = 0.f;
+        for (int t = 0; t < ntiles; ++t) {
+          if (l < __ldg(lstart + (long)m * ntiles + t)) continue;
+          const T *p = scratch + 2 * ((long)t * nalm + base + j);
+          sr += p[0];
+          si += p[1];
+        }
+        anal_finish32(base + j, l, sr, si, mode, t32, om, xio, muo, src, x, xs_out, nu, de);
       }
-      anal_finish<T>(base + j, l, sr, si, wm, mode, rg, cl, omega, xi, mu, src, x, xs_out,
-                     num, den);
+      num = wm * nu;
+      den = wm * de;
+    } else {
+      for (int j = threadIdx.x; j <= L - m; j += ANA_THREADS) {
+        const int l = m + j;
+        double sr = 0.0, si = 0.0;
+        for (int t = 0; t < ntiles; ++t) {
+          if (l < __ldg(lstart + (long)m * ntiles + t)) continue;
+          const T *p = scratch + 2 * ((long)t * nalm + base + j);
+          sr += (double)p[0];
+          si += (double)p[1];
+        }
+        anal_finish<T>(base + j, l, sr, si, wm, mode, rg, cl, omega, xi, mu, src, x, xs_out,
+                       num, den);
+      }
     }
   }
   anal_zero_above<T>(m, L, lmax, base, wm, mode, x, xs_out, num);
@@ -1136,6 +1264,10 @@ struct Kernels<float2> {
   typedef float T;
 };
 
+static Tab32 tab32(const Plan &P) {
+  return {P.seed_s32, P.zs32, P.zs32 + P.npairs, P.rg32, P.cl32};
+}
+
 template <typename T, int NP, bool X2 = false, bool DUP = false>
 static void synth_variant(const Plan &P, const typename Vec2<T>::type *xs,
                           typename Vec2<T>::type *F, const SolverState *st, int lstatic) {
@@ -1146,7 +1278,7 @@ static void synth_variant(const Plan &P, const typename Vec2<T>::type *xs,
   dim3 grid((P.npairs + pairs_per_cta - 1) / pairs_per_cta, P.lmax + 1);
   k_legendre_synth<T, NP, X2, DUP><<<grid, SYN_THREADS, smem, P.stream>>>(
       P.pairs, P.npairs, P.lmax, P.rc, P.rc32, P.rg, P.seed_l, P.seed_u, xs, F, st,
-      lstatic);
+      lstatic, tab32(P));
 }
 
 template <typename T, int NP, bool X2 = false, bool GACC = false, int LC = LCHUNK>
@@ -1159,7 +1291,18 @@ static void anal_variant(const Plan &P, const typename Vec2<T>::type *G, double2
   k_legendre_anal<T, NP, X2, GACC, LC><<<P.lmax + 1, ANA_THREADS, smem, P.stream>>>(
       P.pairs, P.npairs, P.lmax, P.rc, P.rc32, P.rg, P.seed_l, P.seed_u, P.cl_d, P.omega,
       G, x, P.partials, src, xs_out, st, mode, lstatic,
-      GACC ? reinterpret_cast<T *>(P.ana_scratch) : nullptr, P.nalm);
+      GACC ? reinterpret_cast<T *>(P.ana_scratch) : nullptr, P.nalm, tab32(P));
+}
+// packed FP32 analysis, 8-l chunks, global accumulators, seeds in shared memory
+template <int NP>
+static void anal_ss_variant(const Plan &P, const float2 *G, double2 *x,
+                            const SolverState *st, int mode, int lstatic, const double2 *src,
+                            float2 *xs_out) {
+  const size_t smem = align16(sizeof(float) * (P.lmax + 1)) + sizeof(float2) * ANA_THREADS * NP;
+  k_legendre_anal_ss<NP><<<P.lmax + 1, ANA_THREADS, smem, P.stream>>>(
+      P.pairs, P.npairs, P.lmax, P.rc, P.rc32, P.rg, P.seed_l, P.seed_u, P.cl_d, P.omega,
+      G, x, P.partials, src, xs_out, st, mode, lstatic,
+      reinterpret_cast<float *>(P.ana_scratch), P.nalm, tab32(P));
 }
 
 // queue-scheduled FP32 analysis: persistent grid of ANA_Q_CTAS_PER_SM CTAs
@@ -1184,12 +1327,12 @@ static wf_status anal_queue_variant(const Plan &P, const float2 *G, double2 *x,
   }
   k_legendre_anal_q<float, NP><<<P.num_sms * per_sm, ANA_THREADS, smem, P.stream>>>(
       P.pairs, P.npairs, P.lmax, P.nalm, P.rc, P.rc32, P.seed_l, P.seed_u, G,
-      P.ana_scratch, P.ana_lstart, P.ana_counter, st, lstatic);
+      P.ana_scratch, P.ana_lstart, P.ana_counter, st, lstatic, tab32(P));
   WF_CUDA(cudaGetLastError());
   ++P.nlaunch;
   k_anal_combine<float><<<P.lmax + 1, ANA_THREADS, 0, P.stream>>>(
       P.lmax, P.nalm, ntiles, P.ana_scratch, P.ana_lstart, P.ana_counter, P.rg, P.cl_d,
-      P.omega, x, P.partials, src, xs_out, st, mode, lstatic);
+      P.omega, x, P.partials, src, xs_out, st, mode, lstatic, tab32(P));
   WF_CUDA(cudaGetLastError());
   return WF_OK;
 }
@@ -1236,11 +1379,19 @@ wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
       return np == 4 ? anal_queue_variant<4>(P, g, x, st, mode, lstatic, src, xo)
                      : anal_queue_variant<8>(P, g, x, st, mode, lstatic, src, xo);
     }
+    if (P.ana_x2 && P.ana_gacc == 3) {  // 8-l chunks, seeds in shared memory
+      anal_ss_variant<8>(P, reinterpret_cast<const float2 *>(G), x, st, mode, lstatic, src,
+                         reinterpret_cast<float2 *>(xs_out));
+      WF_CUDA(cudaGetLastError());
+      return WF_OK;
+    }
     if (P.ana_x2 && P.ana_gacc == 2) {  // 8-l chunks
       if (np == 8)
         anal_variant<T, 8, true, true, 8>(P, G, x, st, mode, lstatic, src, xs_out);
-      else
+      else if (np == 6)
         anal_variant<T, 6, true, true, 8>(P, G, x, st, mode, lstatic, src, xs_out);
+      else
+        anal_variant<T, 4, true, true, 8>(P, G, x, st, mode, lstatic, src, xs_out);
       WF_CUDA(cudaGetLastError());
       return WF_OK;
     }
@@ -1312,7 +1463,7 @@ wf_status launch_legendre_anal_dd(const Plan &P, const double2 *G, double2 *x,
   ++P.nlaunch;
   k_anal_combine<double><<<P.lmax + 1, ANA_THREADS, 0, P.stream>>>(
       P.lmax, P.nalm, ntiles, scratch, P.ana_lstart, P.ana_counter, P.rg, P.cl_d, P.omega,
-      x, P.partials, src, xs_out, st, mode, lstatic);
+      x, P.partials, src, xs_out, st, mode, lstatic, Tab32{});
   WF_CUDA(cudaGetLastError());
   return WF_OK;
 }
@@ -1354,6 +1505,9 @@ wf_status init_legendre_attributes() {
   WF_CUDA((set_big_smem_anal<float, 6, true, true>(big)));
   WF_CUDA((set_big_smem_anal<float, 8, true, true, 8>(big)));
   WF_CUDA((set_big_smem_anal<float, 6, true, true, 8>(big)));
+  WF_CUDA((set_big_smem_anal<float, 4, true, true, 8>(big)));
+  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_ss<8>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   WF_CUDA(cudaFuncSetAttribute(k_legendre_synth_dd,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_dd,

@@ -197,7 +197,7 @@ static wf_status make_fft_tables(Plan &P) {
 static wf_status make_recurrence_tables(Plan &P) {
   const int L = P.lmax;
   std::vector<double> c(P.nalm, 0.0), g(P.nalm, 1.0);
-  std::vector<float> c32(P.nalm, 0.0f);
+  std::vector<float> c32(P.nalm, 0.0f), g32(P.nalm, 1.0f);
   for (int m = 0; m <= L; ++m) {
     double a_prev = 0.0, g2 = 1.0, g1 = 1.0;  // g_{l-2}, g_{l-1}
     for (int l = m; l <= L; ++l) {
@@ -205,6 +205,7 @@ static wf_status make_recurrence_tables(Plan &P) {
       if (l == m) {
         g[i] = 1.0;
         c[i] = 0.0;
+        g32[i] = ((l >> 1) & 1) ? -1.0f : 1.0f;
         continue;
       }
       double a = sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
@@ -221,6 +222,7 @@ static wf_status make_recurrence_tables(Plan &P) {
       // -c_l for even l, +c_l for odd l (no negated operand, so two rings
       // fit one packed f32x2 FMA)
       c32[i] = (float)((l % 2 == 0) ? -c[i] : c[i]);
+      g32[i] = (float)(((l >> 1) & 1) ? -gl : gl);  // g_l eps_l
       a_prev = a;
       g2 = g1;
       g1 = gl;
@@ -229,6 +231,8 @@ static wf_status make_recurrence_tables(Plan &P) {
   WF_CUDA(cudaMalloc(&P.rc, sizeof(double) * P.nalm));
   WF_CUDA(cudaMalloc(&P.rg, sizeof(double) * P.nalm));
   WF_CUDA(cudaMalloc(&P.rc32, sizeof(float) * P.nalm));
+  WF_CUDA(cudaMalloc(&P.rg32, sizeof(float) * P.nalm));
+  WF_CUDA(cudaMemcpy(P.rg32, g32.data(), sizeof(float) * P.nalm, cudaMemcpyHostToDevice));
   WF_CUDA(cudaMemcpy(P.rc, c.data(), sizeof(double) * P.nalm,
                      cudaMemcpyHostToDevice));
   WF_CUDA(cudaMemcpy(P.rg, g.data(), sizeof(double) * P.nalm,
@@ -263,7 +267,8 @@ __global__ void k_seed_diag(const RingPair *pairs, int npairs, int lmax,
 // and store the start l and the two rescaled values there.
 __global__ void k_seed_walk(const RingPair *pairs, int npairs, int lmax,
                             const double *mant, const int *expo,
-                            const double *rg, int *seed_l, double2 *seed_u) {
+                            const double *rg, int *seed_l, double2 *seed_u,
+                            float2 *seed_s32) {
   long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long)npairs * (lmax + 1)) return;
   const int m = (int)(t / npairs);
@@ -309,6 +314,9 @@ __global__ void k_seed_walk(const RingPair *pairs, int npairs, int lmax,
     if (found + 1 <= lmax) u.y = lam1 / rg[alm_idx_d(lmax, found + 1, m)];
   }
   seed_u[t] = u;
+  // s-units of the FP32 kernels: s_l = eps_l u_l, eps_l = (-1)^floor(l/2)
+  const double e0 = ((found >> 1) & 1) ? -1.0 : 1.0, e1 = (((found + 1) >> 1) & 1) ? -1.0 : 1.0;
+  seed_s32[t] = make_float2((float)(e0 * u.x), (float)(e1 * u.y));
 }
 
 static wf_status make_seeds(Plan &P) {
@@ -319,11 +327,12 @@ static wf_status make_seeds(Plan &P) {
   WF_CUDA(cudaMalloc(&expo, sizeof(int) * n));
   WF_CUDA(cudaMalloc(&P.seed_l, sizeof(int) * n));
   WF_CUDA(cudaMalloc(&P.seed_u, sizeof(double2) * n));
+  WF_CUDA(cudaMalloc(&P.seed_s32, sizeof(float2) * n));
   k_seed_diag<<<(P.npairs + 127) / 128, 128, 0, P.stream>>>(P.pairs, P.npairs,
                                                             P.lmax, mant, expo);
   WF_CUDA(cudaGetLastError());
   k_seed_walk<<<(unsigned)((n + 255) / 256), 256, 0, P.stream>>>(
-      P.pairs, P.npairs, P.lmax, mant, expo, P.rg, P.seed_l, P.seed_u);
+      P.pairs, P.npairs, P.lmax, mant, expo, P.rg, P.seed_l, P.seed_u, P.seed_s32);
   WF_CUDA(cudaGetLastError());
   WF_CUDA(cudaStreamSynchronize(P.stream));
   WF_CUDA(cudaFree(mant));
@@ -342,6 +351,20 @@ wf_status build_tables(Plan &P) {
   WF_CUDA(cudaMalloc(&P.cl_d, sizeof(double) * (P.lmax + 1)));
   WF_CUDA(cudaMemcpy(P.cl_d, P.cl.data(), sizeof(double) * (P.lmax + 1),
                      cudaMemcpyHostToDevice));
+  {
+    const std::vector<float> cl32(P.cl.begin(), P.cl.end());
+    std::vector<float> zs(2 * (size_t)P.npairs);
+    for (int k = 0; k < P.npairs; ++k) {  // z = zh + zl to ~2^-48
+      const double z = P.pairs_h[k].z;
+      zs[k] = (float)z;
+      zs[P.npairs + k] = (float)(z - (double)zs[k]);
+    }
+    WF_CUDA(cudaMalloc(&P.cl32, sizeof(float) * (P.lmax + 1)));
+    WF_CUDA(cudaMemcpy(P.cl32, cl32.data(), sizeof(float) * (P.lmax + 1),
+                       cudaMemcpyHostToDevice));
+    WF_CUDA(cudaMalloc(&P.zs32, sizeof(float) * zs.size()));
+    WF_CUDA(cudaMemcpy(P.zs32, zs.data(), sizeof(float) * zs.size(), cudaMemcpyHostToDevice));
+  }
   WF_TRY(make_recurrence_tables(P));
   WF_TRY(make_seeds(P));
   return WF_OK;

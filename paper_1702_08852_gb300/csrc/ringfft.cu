@@ -308,9 +308,19 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
     alpha = st->alpha;
   }
   // FP32 step: w = (xi / alpha) / (sigma^2 / alpha + mu / alpha) -- the same
-  // weight with every operand scaled to O(1) for the FP32 range
+  // weight with every operand scaled to O(1) for the FP32 range.  The two
+  // quotients are uniform: lane 0 of each warp divides (FP64 division is
+  // slow on this part) and broadcasts.
   constexpr bool F32STEP = MODE == RING_FUSED && sizeof(T) == 4;
-  const float xia = (float)(xi / alpha), mua = (float)(mu / alpha);
+  float xia = 0.f, mua = 0.f;
+  if constexpr (F32STEP) {
+    if ((threadIdx.x & 31) == 0) {
+      xia = (float)(xi / alpha);
+      mua = (float)(mu / alpha);
+    }
+    xia = __shfl_sync(0xffffffffu, xia, 0);
+    mua = __shfl_sync(0xffffffffu, mua, 0);
+  }
   extern __shared__ __align__(16) unsigned char smraw[];
   T2 *buf = reinterpret_cast<T2 *>(smraw);
   const int n = rp.nphi, M = rp.fftM;

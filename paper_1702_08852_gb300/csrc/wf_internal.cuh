@@ -36,6 +36,14 @@ void set_error_static(const char *msg);
 // One iso-latitude ring pair: the north ring and its mirror image in the
 // south (the equator ring is a "pair" with no south ring).  Both rings share
 // nphi, |z| and phi0.
+// the FP32 tables as one kernel argument
+struct Tab32 {
+  const float2 *seed_s;
+  const float *zh, *zl;
+  const float *rg;
+  const float *cl;
+};
+
 struct RingPair {
   double z;        // z of the north ring
   double sth;      // sin(theta) of the north ring
@@ -113,6 +121,14 @@ struct Plan {
   float *rc32 = nullptr;         // [nalm] FP32 copy of rc
   int *seed_l = nullptr;         // [lmax+1][npairs] first l with |lambda| >= 2^-100
   double2 *seed_u = nullptr;     // [lmax+1][npairs] (u_ls, u_ls+1)
+  // FP32 kernels' tables (no FP64 arithmetic left in their tile loads and
+  // epilogues): seeds in s-units (eps_ls u_ls, eps_ls+1 u_ls+1), z of each
+  // pair split as zh + zl (two arrays: the packed kernels pair the zh of two
+  // rings, so each value is loaded on its own), g_lm eps_l, C_l
+  float2 *seed_s32 = nullptr;    // [lmax+1][npairs]
+  float *zs32 = nullptr;         // [2][npairs]: zh, then zl
+  float *rg32 = nullptr;         // [nalm]
+  float *cl32 = nullptr;         // [lmax+1]
 
   // launch variants (ring pairs per thread), [0] = FP64, [1] = FP32; set by
   // the autotuner (opts.autotune) or the defaults below
@@ -133,8 +149,8 @@ struct Plan {
   int *ana_counter = nullptr;    // the queue's next item (reset by the combine)
   int num_sms = 0;
   float tune_syn_ms[2][6] = {{-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}};
-  float tune_ana_ms[2][13] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
-                              {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1}};
+  float tune_ana_ms[2][15] = {{-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1},
+                              {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1}};
 
   // FFT tables
   int fftMmax = 1;

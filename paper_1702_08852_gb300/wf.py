@@ -55,7 +55,7 @@ class _Tuning(ctypes.Structure):
                 ("ana_np", ctypes.c_int * 2), ("ana_queue", ctypes.c_int),
                 ("ana_packed", ctypes.c_int), ("ana_global_acc", ctypes.c_int),
                 ("syn_ms", (ctypes.c_float * 6) * 2),
-                ("ana_ms", (ctypes.c_float * 13) * 2)]
+                ("ana_ms", (ctypes.c_float * 15) * 2)]
 
 
 _lib = None

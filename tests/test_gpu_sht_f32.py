@@ -102,6 +102,8 @@ VARIANTS = [dict(ana_np=(4, 2), ana_queue=0), dict(ana_np=(4, 4), ana_queue=0),
             dict(ana_np=(4, 6), ana_queue=0, ana_packed=1, ana_global_acc=1),
             dict(ana_np=(4, 8), ana_queue=0, ana_packed=1, ana_global_acc=2),
             dict(ana_np=(4, 6), ana_queue=0, ana_packed=1, ana_global_acc=2),
+            dict(ana_np=(4, 4), ana_queue=0, ana_packed=1, ana_global_acc=2),
+            dict(ana_np=(4, 8), ana_queue=0, ana_packed=1, ana_global_acc=3),
             dict(syn_np=(2, 1)), dict(syn_np=(2, 4)),
             dict(syn_np=(2, 2), syn_packed=1), dict(syn_np=(2, 4), syn_packed=1),
             dict(syn_np=(2, 2), syn_packed=2)]
@@ -143,7 +145,8 @@ def test_tuning_report_and_bad_values(torch_cuda):
                     dict(ana_np=(4, 8), ana_queue=1, ana_packed=1),
                     dict(syn_np=(2, 1), syn_packed=1), dict(syn_np=(2, 4), syn_packed=2),
                     dict(ana_np=(4, 8), ana_packed=1, ana_global_acc=1),
-                    dict(ana_np=(4, 4), ana_packed=1, ana_global_acc=2),
+                    dict(ana_np=(4, 4), ana_packed=0, ana_global_acc=2),
+                    dict(ana_np=(4, 6), ana_packed=1, ana_global_acc=3),
                     dict(ana_np=(4, 4), ana_packed=0, ana_global_acc=1)):
             with pytest.raises(wf.WFError):
                 p.set_tuning(**bad)

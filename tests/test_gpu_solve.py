@@ -222,7 +222,8 @@ def test_mixed_precision_reaches_fp64_fixed_point(torch_cuda, osht, odm, nside, 
                                                           (16, 0, 0, 0), (2, 0, 0, 0),
                                                           (8, 0, 1, 0), (4, 0, 1, 0),
                                                           (6, 0, 1, 0), (4, 0, 1, 1),
-                                                          (8, 0, 1, 2)])
+                                                          (8, 0, 1, 2), (4, 0, 1, 2),
+                                                          (8, 0, 1, 3)])
 def test_mixed_precision_variants_reach_fp64_fixed_point(torch_cuda, osht, odm, ana_np,
                                                          ana_queue, packed, gacc):
     """The same check with the FP32 analysis forced to each launch variant
