@@ -6,7 +6,7 @@ warm-or-cold decision).
 The net maps (d, log sigma^2, mask) to (t0, a0).  A warm solve starts
 Algorithm 2 from (a0, t0) with a cooling start mu0 = mu0_over_alpha * alpha
 instead of the cold start (s = 0, t = d, mu0 Omega = beta max C_l), i.e. it
-skips the stages above mu0.  The plain method judges the warm start: it is
+skips the stages above mu0.  The plain method decides on the warm start: it is
 used only if its Wiener-filter residual ||A x - y|| / ||y|| (App. C) is
 below both the zero start's (1) and the tolerance of the stage it enters,
 eps_k = min(eps_cap, eps_final mu0 / alpha); the cold stages would hand that

@@ -107,7 +107,7 @@ def test_training_lowers_the_loss_and_warm_solve_is_exact(torch_cuda, osht, odm)
             wnet = wf.Net(wp, 8, 5, 16)
             wnet.set_params(net.get_params())
             alm, mp, st, used, res = learned.warm_solve(wnet, wp, torch.from_numpy(d).cuda())
-            # the judge: warm only when within the entry stage's tolerance
+            # the acceptance rule: warm only when within the entry stage's tolerance
             assert used == (res < learned.entry_tolerance(wp, 30.0))
             wnet.close()
         net.close()
