@@ -72,7 +72,12 @@ typedef struct {
   int max_iter;      /* bound on the total number of iterations (default 200000) */
   int stop_rule;     /* wf_stop_rule (default WF_STOP_CAUCHY, the paper's
                         criterion of Sect. 3) */
-  int precision;     /* wf_precision (default WF_PREC_FP64) */
+  int precision;     /* wf_precision (default WF_PREC_FP64).  WF_PREC_MIXED
+                        keeps FP32 copies of C_l, of the data and of
+                        sigma^2 / alpha: C_l, |d| and the alm must lie in
+                        FP32's normal range (~1e-38 to 3e38) for its FP32
+                        stages to be accurate; the last stage's acceptance
+                        test is FP64 either way. */
   int band_limit;    /* 1: restrict each stage's transforms to the band where
                         the truncated spectrum is nonzero (exact; default 1) */
   int graph_chunk;   /* iterations per captured CUDA graph launch; 0 = auto */
