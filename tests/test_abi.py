@@ -83,3 +83,42 @@ def test_null_plan_calls(wflib):
     assert L.wf_solve(None, None, None, None, None, None, None) == wflib.WF_ERR_ARG
     assert L.wf_alm2map(None, None, None) == wflib.WF_ERR_ARG
     L.wf_destroy(None)
+
+
+def _c_layout(tmp_path, structs):
+    """sizeof and field offsets of the header's structs, from a C program
+    compiled against include/wf.h (gcc, the host ABI the library uses)."""
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "wf.h"', "int main(void) {"]
+    for cname, fields in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for line in out.splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    return got
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The binding's ctypes structures have the header's sizes and field
+    offsets (a field added to one side only would shift every later field)."""
+    import shutil
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_1702_08852_gb300 import wf
+    pairs = {"wf_opts": wf.wf_opts, "wf_stats": wf.wf_stats, "wf_tuning": wf._Tuning}
+    structs = {c: [f for f, _ in py._fields_] for c, py in pairs.items()}
+    got = _c_layout(tmp_path, structs)
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
