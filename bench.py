@@ -124,15 +124,26 @@ def measured_peaks():
 # DRAM bytes (read + write, ncu) of one full-band launch of the FP32 analysis
 # variant the autotuner picks at Nside 1024 / lmax 2048 (kernel-case capture,
 # profiles/legendre_f32_nside1024.md); scaled to a live launch by its share
-# of the full band's terms.  None once the kernel changes after a capture.
+# of the full band's terms.  None once the kernel changes after a capture,
+# and for a plan whose autotuner picked another analysis variant.
 ANALYSIS_DRAM_FULL_BAND = {"nside": 1024, "bytes": 137106944.0 + 71930624.0,
-                           "terms": 3140761977.0}
+                           "terms": 3140761977.0,
+                           "variant": {"ana_np": 4, "ana_queue": 0, "ana_packed": 1,
+                                       "ana_global_acc": 1}}
 
 
-def analysis_traffic(nside, gflop, launches):
+def analysis_variant(tuning):
+    """The FP32 analysis launch variant of a plan's tuning report."""
+    return {"ana_np": tuning["ana_np"][1], "ana_queue": tuning["ana_queue"],
+            "ana_packed": tuning["ana_packed"], "ana_global_acc": tuning["ana_global_acc"]}
+
+
+def analysis_traffic(nside, gflop, launches, variant=None):
     """Bytes per live analysis launch from the captured full-band figure."""
     ref = ANALYSIS_DRAM_FULL_BAND
     if ref["bytes"] is None or nside != ref["nside"] or not launches:
+        return None
+    if variant is not None and variant != ref["variant"]:
         return None
     terms_per_launch = gflop * 1e9 / 7.0 / launches
     return ref["bytes"] * terms_per_launch / ref["terms"]
@@ -233,6 +244,7 @@ def run_ours(args, rank, world):
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(step_ms), dist, dev)
     kern = [plan.kernel_stats(k) for k in (0, 1, 2)]
+    ana_variant = analysis_variant(plan.tuning())
     ms_step_mean = sum(step_ms) / len(step_ms)
 
     # end to end through the C ABI with host buffers (pinned)
@@ -301,8 +313,10 @@ def run_ours(args, rank, world):
                      "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
                      "frac": (achieved / peak32) if achieved else None,
                      "peak_source": "152 SM x 128 FP32 lanes x 2 x 2070 MHz",
-                     "traffic": analysis_traffic(args.nside, k0["gflop"], k0["launches"]),
+                     "traffic": analysis_traffic(args.nside, k0["gflop"], k0["launches"],
+                                                 ana_variant),
                      "traffic_source": "ncu dram bytes of the full-band launch, scaled by terms",
+                     "variant": ana_variant,
                      "launches": k0["launches"], "avg_launch_ms": k0["ms"] / max(1, k0["launches"]),
                      "synthesis": {"achieved": (kern[1]["gflop"] / (kern[1]["ms"] / 1e3) / 1e3)
                                    if kern[1]["ms"] > 0 else None,

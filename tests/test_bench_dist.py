@@ -50,3 +50,21 @@ def test_single_rank_defaults():
     import bench
     assert bench.max_over_ranks(12.5) == 12.5
     assert bench.aggregate_value(1, 2, 4000.0) == pytest.approx(0.5)
+
+
+def test_analysis_traffic_only_for_the_captured_variant():
+    import bench
+    ref = bench.ANALYSIS_DRAM_FULL_BAND
+    tuning = {"ana_np": [4, ref["variant"]["ana_np"]], "ana_queue": ref["variant"]["ana_queue"],
+              "ana_packed": ref["variant"]["ana_packed"],
+              "ana_global_acc": ref["variant"]["ana_global_acc"]}
+    v = bench.analysis_variant(tuning)
+    assert v == ref["variant"]
+    # a launch covering the full band's terms carries the captured bytes
+    gflop = 7.0 * ref["terms"] / 1e9
+    assert bench.analysis_traffic(ref["nside"], gflop, 1, v) == pytest.approx(ref["bytes"])
+    assert bench.analysis_traffic(ref["nside"], 2 * gflop, 4, v) == pytest.approx(ref["bytes"] / 2)
+    other = dict(v, ana_queue=1, ana_packed=0)
+    assert bench.analysis_traffic(ref["nside"], gflop, 1, other) is None
+    assert bench.analysis_traffic(ref["nside"] // 2, gflop, 1, v) is None
+    assert bench.analysis_traffic(ref["nside"], gflop, 0, v) is None
