@@ -261,3 +261,25 @@ def test_mixed_stage_lengths_match_fp64(torch_cuda, osht, nside, kind, seed):
     n32 = np.bincount(np.asarray(tr32["stage"]))
     assert len(n32) == len(n64)
     assert np.all(np.abs(n32.astype(int) - n64.astype(int)) <= 2), (n32, n64)
+
+
+def test_set_cl_equals_a_plan_made_with_it(torch_cuda, osht):
+    """wf_set_cl refreshes every copy of C_l the solver reads (the FP64 one
+    and the FP32 one of the mixed path's FP32 stages): a plan made with C_l
+    and then given 1.7 C_l solves exactly as a plan made with 1.7 C_l."""
+    torch = torch_cuda
+    from paper_1702_08852_gb300 import wf
+    p, d = problem(osht, "lognormal", 16, 12)
+    cl2 = 1.7 * p.cl
+    nv = torch.from_numpy(p.noise_var).cuda()
+    mk = torch.from_numpy(p.mask.astype(np.uint8)).cuda()
+    dt = torch.from_numpy(d).cuda()
+    out = []
+    for cl_make, cl_set in ((p.cl, cl2), (cl2, None)):
+        with wf.Plan(p.nside, p.lmax, cl_make, nv, mk, precision=1, eps_final=1e-7) as plan:
+            if cl_set is not None:
+                plan.set_cl(cl_set)
+            alm, _, st = plan.solve(dt)
+            out.append((alm.cpu().numpy(), st["iterations"]))
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
