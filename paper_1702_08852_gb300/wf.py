@@ -209,6 +209,8 @@ class Plan:
 
     def set_cl(self, cl):
         cl = np.ascontiguousarray(cl, dtype=np.float64)
+        if cl.shape != (self.lmax + 1,):  # the library reads lmax + 1 values
+            raise ValueError("cl must have lmax + 1 entries")
         _check(lib().wf_set_cl(self.handle, cl.ctypes.data_as(ctypes.c_void_p)))
         self._cl = cl
 
@@ -235,6 +237,8 @@ class Plan:
 
     def solve_host(self, d_host, want_alm=True, want_map=True):
         d = np.ascontiguousarray(d_host, dtype=np.float64)
+        if d.shape != (self.npix,):  # the library reads Npix values
+            raise ValueError("d_host must have Npix entries")
         alm = np.empty(self.nalm, dtype=np.complex128) if want_alm else None
         mp = np.empty(self.npix, dtype=np.float64) if want_map else None
         st = wf_stats()

@@ -122,3 +122,17 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_binding_checks_host_array_lengths():
+    """Host arrays handed to the library by pointer are checked against the
+    lengths it reads before any call (no plan, no GPU needed)."""
+    from paper_1702_08852_gb300 import wf
+    p = wf.Plan.__new__(wf.Plan)
+    p.nside, p.lmax, p.npix, p.nalm, p.handle = 4, 8, wf.wf_npix(4), wf.wf_nalm(8), None
+    with pytest.raises(ValueError):
+        p.set_cl(np.ones(8))
+    with pytest.raises(ValueError):
+        p.solve_host(np.zeros(p.npix - 1))
+    with pytest.raises(ValueError):
+        wf.Plan(4, 8, np.ones(5))
