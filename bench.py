@@ -336,44 +336,60 @@ def run_ours(args, rank, world):
 
 
 # ---------------------------------------------------------------- oracle
-def oracle_sample(nside, budget_s):
-    """Time the oracle's direct FP64 transforms on a bounded sample of the
+class OracleSampler:
+    """Times the oracle's direct FP64 transforms on bounded samples of the
     Nside workload: synthesis of k pixels and analysis of k coefficients,
-    scaled to one transform pair.  Returns (seconds per SHT pair, sample,
-    threads)."""
-    import numpy as np
-    from oracle import sht
-    from paper_1702_08852_gb300 import inputs
-    lmax = 2 * nside
-    cl = inputs.cl_spectrum(lmax, nside)
-    rng = np.random.default_rng(1)
-    a = inputs.random_alm(rng, np.maximum(cl, 1e-30))
-    npix = 12 * nside * nside
-    m = rng.standard_normal(npix)
-    ls, ms = inputs.lm_of_slots(lmax)
-    sht.lib()
-    kp = 8
-    t0 = time.perf_counter()
-    sht.alm2map_pixels(a, nside, lmax, rng.integers(0, npix, kp))
-    t_pix = (time.perf_counter() - t0) / kp
-    ka = 4
-    sel = rng.integers(0, len(ls), ka)
-    t0 = time.perf_counter()
-    sht.adjoint_modes(m, nside, lmax, ls[sel], ms[sel])
-    t_mode = (time.perf_counter() - t0) / ka
-    # grow the sample to the budget
-    scale = max(1, int(budget_s / 2 / max(t_pix * kp + t_mode * ka, 1e-3)))
-    kp2, ka2 = kp * scale, ka * scale
-    t0 = time.perf_counter()
-    sht.alm2map_pixels(a, nside, lmax, rng.integers(0, npix, kp2))
-    t_pix = (time.perf_counter() - t0) / kp2
-    t0 = time.perf_counter()
-    sht.adjoint_modes(m, nside, lmax, ls[sel[:1].repeat(ka2)], ms[sel[:1].repeat(ka2)])
-    t_mode = (time.perf_counter() - t0) / ka2
-    pair_s = t_pix * npix + t_mode * len(ls)
-    sample = (f"direct synthesis of {kp2} pixels and analysis of {ka2} coefficients "
-              f"at Nside {nside}, scaled to one transform pair ({pair_s:.3g} s)")
-    return pair_s, sample, sht.threads()
+    scaled to one transform pair.  The inputs are drawn once; each call of
+    step() is one timed sample sized to its budget."""
+
+    def __init__(self, nside):
+        import numpy as np
+        from oracle import sht
+        from paper_1702_08852_gb300 import inputs
+        self.sht, self.nside, self.lmax = sht, nside, 2 * nside
+        cl = inputs.cl_spectrum(self.lmax, nside)
+        self.rng = np.random.default_rng(1)
+        self.a = inputs.random_alm(self.rng, np.maximum(cl, 1e-30))
+        self.npix = 12 * nside * nside
+        self.m = self.rng.standard_normal(self.npix)
+        self.ls, self.ms = inputs.lm_of_slots(self.lmax)
+        sht.lib()
+        # calibration: seconds per pixel and per coefficient on a tiny sample
+        self.t_pix, self.t_mode = self._time(8, 4)
+
+    def _time(self, kp, ka):
+        t0 = time.perf_counter()
+        self.sht.alm2map_pixels(self.a, self.nside, self.lmax,
+                                self.rng.integers(0, self.npix, kp))
+        t_pix = (time.perf_counter() - t0) / kp
+        sel = self.rng.integers(0, len(self.ls), ka)
+        t0 = time.perf_counter()
+        self.sht.adjoint_modes(self.m, self.nside, self.lmax, self.ls[sel], self.ms[sel])
+        t_mode = (time.perf_counter() - t0) / ka
+        return t_pix, t_mode
+
+    def step(self, budget_s):
+        """(seconds per SHT pair, description) from one sample of ~budget_s."""
+        unit = 8 * self.t_pix + 4 * self.t_mode
+        scale = max(1, int(budget_s / max(unit, 1e-4)))
+        kp, ka = 8 * scale, 4 * scale
+        t_pix, t_mode = self._time(kp, ka)
+        self.t_pix, self.t_mode = t_pix, t_mode  # sizes the next sample
+        pair_s = t_pix * self.npix + t_mode * len(self.ls)
+        sample = (f"direct synthesis of {kp} pixels and analysis of {ka} coefficients "
+                  f"at Nside {self.nside}, scaled to one transform pair ({pair_s:.3g} s)")
+        return pair_s, sample
+
+    def threads(self):
+        return self.sht.threads()
+
+
+def oracle_sample(nside, budget_s):
+    """One bounded sample: (seconds per SHT pair, sample, threads)."""
+    s = OracleSampler(nside)
+    s.step(min(0.5, budget_s / 10))  # untimed: warms up and sizes the sample
+    pair_s, sample = s.step(budget_s / 2)
+    return pair_s, sample, s.threads()
 
 
 def cpu_baseline(args, iterations):
@@ -389,16 +405,23 @@ def cpu_baseline(args, iterations):
 
 
 def run_reference(args, rank, world):
+    """The oracle, as it stands, on the host cores: each step one timed
+    bounded sample of the workload's transform pair, times the iteration
+    count of the plain FP64 solve (the cpu_sample_s budget is split over
+    the steps; warm-up samples are untimed).  Rank 0 only."""
     if rank != 0:
         return None
     t0 = time.perf_counter()
+    sampler = OracleSampler(args.nside)
+    per_step = max(0.5, args.cpu_sample_s / max(1, args.steps))
     for _ in range(args.warmup):
-        pass
-    pair_s, sample, threads = oracle_sample(args.nside, args.cpu_sample_s)
+        sampler.step(min(0.5, per_step))
     iterations = REF_ITERATIONS.get(args.nside, 2048)
-    steps_s = []
+    steps_s, sample = [], ""
     for _ in range(args.steps):
+        pair_s, sample = sampler.step(per_step)
         steps_s.append(pair_s * iterations)
+    threads = sampler.threads()
     value = args.steps / sum(steps_s)
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -407,8 +430,8 @@ def run_reference(args, rank, world):
             "config": {"workload": f"Nside {args.nside} lmax {2 * args.nside}, oracle "
                                    "direct transforms", "nside": args.nside},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads,
-                             "kind": "oracle", "sample": sample +
-                             f"; x {iterations} iterations (extrapolated)"},
+                             "kind": "oracle", "sample": f"{args.steps} samples, the last: " +
+                             sample + f"; x {iterations} iterations (extrapolated)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t0}

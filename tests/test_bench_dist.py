@@ -68,3 +68,21 @@ def test_analysis_traffic_only_for_the_captured_variant():
     assert bench.analysis_traffic(ref["nside"], gflop, 1, other) is None
     assert bench.analysis_traffic(ref["nside"] // 2, gflop, 1, v) is None
     assert bench.analysis_traffic(ref["nside"], gflop, 0, v) is None
+
+
+def test_reference_arm_times_each_step(osht):
+    """The reference arm (the oracle on the host cores) times every step as
+    its own bounded sample and prints the contract's keys; other ranks do
+    no work."""
+    import argparse
+    import bench
+    args = argparse.Namespace(nside=8, steps=3, warmup=1, cpu_sample_s=0.3)
+    out = bench.run_reference(args, 0, 1)
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "cpu_baseline", "e2e", "config"):
+        assert k in out
+    assert out["impl"] == "reference" and out["value"] > 0
+    assert out["ms_per_step"] == pytest.approx(1e3 * 3 / out["value"] / 3)
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] >= 1
+    assert out["e2e"]["h2d_bytes_per_step"] == 0
+    assert bench.run_reference(args, 1, 2) is None
