@@ -122,8 +122,8 @@ def measured_peaks():
 
 
 # DRAM bytes (read + write, ncu) of one full-band launch of the FP32 analysis
-# variant the autotuner picks at Nside 1024 / lmax 2048 (kernel-case capture,
-# profiles/legendre_f32_nside1024.md); scaled to a live launch by its share
+# variant the autotuner picks at Nside 1024 / lmax 2048 (an ncu capture of
+# the --kernel-case legendre32 run); scaled to a live launch by its share
 # of the full band's terms.  None once the kernel changes after a capture,
 # and for a plan whose autotuner picked another analysis variant.
 ANALYSIS_DRAM_FULL_BAND = {"nside": 1024, "bytes": 137106944.0 + 71930624.0,
@@ -251,7 +251,7 @@ def run_ours(args, rank, world):
     d_host = torch.empty(d.numel(), dtype=torch.float64, pin_memory=True)
     d_host.copy_(d.cpu())
     e2e_s = []
-    for _ in range(1):
+    for _ in range(args.steps):
         t0 = time.perf_counter()
         a_h, _, _ = plan.solve_host(d_host.numpy(), want_alm=True, want_map=False)
         e2e_s.append(time.perf_counter() - t0)

@@ -179,20 +179,26 @@ wf_status wf_residual(wf_plan_t plan, const double *d_dev, const double *alm_dev
                       double *rel_res_wf, double *rel_res_fp, double *chi2);
 
 /* The same three diagnostics as wf_residual for callers that cannot
- * allocate device memory while they run: work recorded into a CUDA graph
- * (cudaMalloc cannot be captured), code bound to a fixed memory budget or to
- * an allocator it does not control, real-time loops that must not block on
- * allocation.  wf_residual takes its temporaries from cudaMalloc on each
- * call; this variant allocates nothing (no cudaMalloc, no cudaFree, no host
- * heap) and takes them from one static device array of 4.8 MB that every GPU
- * loading the library holds until exit.  The paper has no counterpart; the
- * results equal wf_residual's.
+ * allocate device memory while they run: code bound to a fixed device-memory
+ * budget, or running inside a framework whose pool allocator owns the device
+ * memory (a cudaMalloc can fail there, or take memory the pool counts on),
+ * and loops with a time budget per pass (cudaMalloc / cudaFree may
+ * synchronise the device and stall them).  wf_residual takes its temporaries
+ * from cudaMalloc on each call; this variant allocates nothing (no
+ * cudaMalloc, no cudaFree, no host heap) and takes them from one static
+ * device array of 4.8 MB that every GPU loading the library holds until
+ * exit.  The paper has no counterpart; the results equal wf_residual's.
  *  - Size limit: 2 Npix + 6 Nalm + 3 (lmax + 1) + 256 doubles must fit in
  *    600,000 (e.g. nside <= 128 with lmax <= 256); larger plans get
  *    WF_ERR_ARG, and should use wf_residual.
+ *  - Host-synchronous: the call waits for the plan's stream and returns the
+ *    diagnostics as host scalars.
+ *  - The current device must be the plan's (else WF_ERR_STATE).
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress); make that call before any stream capture.
- *  - All calls share the array: calls that overlap on the GPU race.
+ *  - All calls share the array: calls that overlap on the GPU race.  The
+ *    call also uses the plan's own workspaces, so it must not overlap any
+ *    other call on the same plan.
  * Arguments and outputs as for wf_residual. */
 wf_status wf_residual_static(wf_plan_t plan, const double *d_dev, const double *alm_dev,
                              double *rel_res_wf, double *rel_res_fp, double *chi2);

@@ -73,6 +73,7 @@ static wf_status alloc_work(Plan &P) {
     const long tiles = (P.npairs + 127) / 128;
     int dev = 0;
     WF_CUDA(cudaGetDevice(&dev));
+    P.device = dev;
     WF_CUDA(cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, dev));
     // 16 bytes per entry: FP32 complex for the FP32 kernels, FP64 complex
     // for the double-float anchor analysis

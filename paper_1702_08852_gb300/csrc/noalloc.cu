@@ -2,13 +2,17 @@
 // without allocating any memory during the call.
 //
 // wf_residual takes its temporary maps and coefficient arrays from
-// cudaMalloc on every call.  Some callers cannot do that: code that records
-// its GPU work into a CUDA graph (an allocation cannot be captured), code
-// running under a fixed device-memory budget or a pool it does not own, and
-// real-time loops that must not stall on the allocator.  For them this
+// cudaMalloc on every call.  Some callers cannot do that: code that runs
+// under a fixed device-memory budget, or inside a framework whose pool
+// allocator owns the device memory, where a cudaMalloc can fail or take
+// memory the pool counts on; and loops with a time budget per pass, where
+// cudaMalloc / cudaFree may synchronise the device and stall.  For them this
 // variant takes every temporary from one statically sized device array
 // defined in this file.  The plan itself (created beforehand, when allocating
 // is allowed) still provides its own workspaces.
+//
+// The call is host-synchronous: it waits for the plan's stream and returns
+// its three diagnostics as host scalars.
 //
 // The array is a file-scope __device__ variable: each GPU that loads the
 // library holds it (STATIC_SCRATCH_DOUBLES doubles, 4.8 MB) until the process
@@ -16,8 +20,11 @@
 // address is looked up with cudaGetSymbolAddress once per device, by the first
 // call on that device; make that first call before any stream capture.  All
 // calls share the array: calls that overlap on the GPU (other streams, other
-// host threads) race on it.  Nothing in it needs to start at zero: every slot
-// is written before it is read within a call.
+// host threads) race on it.  The call also writes the plan's own workspaces
+// (state, data map, ring coefficients, alm buffers, partial sums), so it must
+// not overlap any other call on the same plan either.  Nothing in the array
+// needs to start at zero: every slot is written before it is read within a
+// call.
 #include <math.h>
 
 #include <mutex>
@@ -104,6 +111,12 @@ wf_status residual_static(Plan &P, const double *d, const double *alm, double *r
                      "(2 Npix + 6 Nalm + 3 (lmax+1) + 256 doubles must fit in 600000); "
                      "use wf_residual, which allocates");
     return WF_ERR_ARG;
+  }
+  int dev = -1;
+  WF_CUDA(cudaGetDevice(&dev));
+  if (dev != P.device) {
+    set_error_static("wf_residual_static: the current device is not the plan's device");
+    return WF_ERR_STATE;
   }
   double *base = nullptr;
   WF_TRY(scratch_address(&base));

@@ -101,6 +101,7 @@ struct TraceEntry {
 // ---------------------------------------------------------------- plan
 struct Plan {
   int nside = 0, lmax = 0, nring = 0, npairs = 0;
+  int device = -1;  // the CUDA device current when the plan was created
   long npix = 0, nalm = 0;
   double omega = 0.0;
   cudaStream_t stream = nullptr;

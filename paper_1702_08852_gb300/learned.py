@@ -61,16 +61,20 @@ def entry_tolerance(plan, mu0_over_alpha):
     return min(o.eps_cap, o.eps_final * max(1.0, mu0_over_alpha))
 
 
-def warm_solve(net, plan, d, mu0_over_alpha=30.0, cold_plan=None):
+def warm_solve(net, plan, d, cold_plan, mu0_over_alpha=30.0):
     """Solve with the net's warm start when the plain method accepts it (see
     the module docstring).  ``plan`` is the net's plan (the problem's noise,
     mask, spectrum) with its cooling start set to mu0_over_alpha * alpha;
-    ``cold_plan`` (default: ``plan``) runs the cold start when the warm one
-    is rejected.  Returns (alm, map, stats, used_warm, residual)."""
+    ``cold_plan`` (required) is a plan of the same problem with the plain
+    method's cooling start, which runs the cold start when the warm one is
+    rejected.  Returns (alm, map, stats, used_warm, residual)."""
+    if cold_plan is None:
+        raise ValueError("warm_solve: cold_plan is required (the plain method's "
+                         "cold start is the fallback)")
     t0, a0 = net.forward(d)
     res = plan.residual(d, a0)["rel_res_wf"]
     if res < min(1.0, entry_tolerance(plan, mu0_over_alpha)):
         alm, mp, st = plan.solve(d, init_alm=a0, init_map=t0)
         return alm, mp, st, True, res
-    alm, mp, st = (cold_plan or plan).solve(d)
+    alm, mp, st = cold_plan.solve(d)
     return alm, mp, st, False, res

@@ -262,8 +262,10 @@ class Plan:
 
     def residual_static(self, d, alm):
         """wf_residual without allocation during the call (see include/wf.h):
-        for callers that must not allocate device memory, e.g. inside a
-        captured CUDA graph.  Small plans only."""
+        for callers under a fixed device-memory budget or a pool allocator
+        they do not own, and loops that must not stall on cudaMalloc.
+        Host-synchronous; must not overlap other calls on this plan.  Small
+        plans only."""
         import torch
         r1, r2, c2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         _check(lib().wf_residual_static(

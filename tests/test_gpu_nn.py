@@ -103,10 +103,12 @@ def test_training_lowers_the_loss_and_warm_solve_is_exact(torch_cuda, osht, odm)
         plan.set_cl(p.cl)
         alpha = float(np.min(p.noise_var[~p.mask]))
         with wf.Plan(p.nside, p.lmax, p.cl, nv, mk, eps_final=1e-12, stop_rule=1,
-                     mu0=30.0 * alpha) as wp:
+                     mu0=30.0 * alpha) as wp, \
+                wf.Plan(p.nside, p.lmax, p.cl, nv, mk, eps_final=1e-12, stop_rule=1) as cp:
             wnet = wf.Net(wp, 8, 5, 16)
             wnet.set_params(net.get_params())
-            alm, mp, st, used, res = learned.warm_solve(wnet, wp, torch.from_numpy(d).cuda())
+            alm, mp, st, used, res = learned.warm_solve(wnet, wp, torch.from_numpy(d).cuda(),
+                                                        cold_plan=cp)
             # the acceptance rule: warm only when within the entry stage's tolerance
             assert used == (res < learned.entry_tolerance(wp, 30.0))
             wnet.close()

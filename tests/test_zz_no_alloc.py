@@ -1,7 +1,8 @@
 """wf_residual_static: the residual diagnostics for callers that cannot
-allocate device memory during the call (graph capture, fixed memory budgets).
-It must give wf_residual's results.  Kept in a file of its own that pytest
-collects last."""
+allocate device memory during the call (a fixed device-memory budget, a pool
+allocator they do not own, loops that must not stall on cudaMalloc).  It must
+give wf_residual's results.  Kept in a file of its own that pytest collects
+last."""
 import numpy as np
 import pytest
 
