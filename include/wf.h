@@ -94,6 +94,12 @@ typedef struct {
                         significand) on the FP32 pipe, ring FFTs in FP64;
                         0: plain FP64.  The last stage's acceptance test
                         and fp_residual always use plain FP64. */
+  double anchor_eps; /* WF_PREC_MIXED: stages whose tolerance is below
+                        anchor_eps run anchored (correction form around an
+                        FP64 anchor); the others run plain FP32 iterations.
+                        >= eps_cap anchors every stage (default 3e-5). */
+  double anchor_cap; /* WF_PREC_MIXED: an anchored stage takes a new anchor
+                        when ||delta|| > anchor_cap ||x_a|| (default 1e-2). */
 } wf_opts;
 
 /* Per-solve statistics. */
@@ -292,6 +298,18 @@ wf_status wf_set_tuning(wf_plan_t plan, const wf_tuning *in);
 /* Algorithmic work of one Legendre transform at band limit L (<= lmax): the
  * number of (l, m, ring pair) terms with l <= L and |lambda_lm| >= 2^-100. */
 wf_status wf_legendre_terms(wf_plan_t plan, int L, double *terms);
+
+/* Measured peak of the arithmetic pipe the Legendre kernels run on (the
+ * denominator of their roofline; the paper has no counterpart): independent
+ * FMA chains in every thread of a grid that fills every SM of the current
+ * device, timed with CUDA events.
+ *  kind     0 = FP64 FMA, 1 = FP32 FMA, 2 = packed FP32 (fma.rn.f32x2).
+ *  reps     timed launches (1..100), each ~50 ms; the fastest is reported.
+ *  tflops   out: 2 flops per FMA / the fastest launch's time, in TFLOP/s.
+ *  best_ms, num_sms  out (may be NULL): that launch's time, the SM count.
+ * Allocates one small output buffer and a stream of its own for the call.
+ * Errors: WF_ERR_ARG for an unknown kind or reps out of range. */
+wf_status wf_alu_peak(int kind, int reps, double *tflops, double *best_ms, int *num_sms);
 
 /* ---- learned warm start (the paper has none; an extension of the method)
  * A small network maps (d, log sigma^2, mask) to an initial messenger field

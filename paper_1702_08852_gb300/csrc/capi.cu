@@ -84,7 +84,8 @@ static wf_status alloc_work(Plan &P) {
     WF_CUDA(cudaMemsetAsync(P.ana_counter, 0, sizeof(int), P.stream));
   }
   WF_CUDA(cudaMalloc(&P.mtmp, sizeof(double) * P.npix));
-  WF_CUDA(cudaMalloc(&P.partials, sizeof(double) * 2 * (P.lmax + 1)));
+  // per m: ||x_new - x_old||^2, ||x_new||^2, then (anchored stages) ||x_a + delta||^2
+  WF_CUDA(cudaMalloc(&P.partials, sizeof(double) * 3 * (P.lmax + 1)));
   WF_CUDA(cudaMalloc(&P.red, sizeof(double) * 1024));
   WF_CUDA(cudaMalloc(&P.state, sizeof(SolverState)));
   WF_CUDA(cudaMallocHost(&P.state_h, sizeof(SolverState)));
@@ -111,6 +112,8 @@ static wf_status check_opts(const wf_opts &o) {
   if (o.graph_chunk < 0 || o.graph_chunk > 4096)
     return arg_error("wf: graph_chunk out of range");
   if (o.anchor != 0 && o.anchor != 1) return arg_error("wf: anchor must be 0 or 1");
+  if (!(o.anchor_eps >= 0.0) || !(o.anchor_cap > 0.0 && o.anchor_cap <= 1.0))
+    return arg_error("wf: anchor_eps must be >= 0 and anchor_cap in (0, 1]");
   return WF_OK;
 }
 
@@ -134,6 +137,8 @@ void wf_opts_default(wf_opts *o) {
   o->graph_chunk = 0;
   o->refine_max = 8;
   o->anchor = 1;
+  o->anchor_eps = 3e-5;
+  o->anchor_cap = 1e-2;
 }
 
 long wf_npix(int nside) { return 12L * nside * nside; }

@@ -550,9 +550,10 @@ __device__ __forceinline__ void anal_finish(long i, int l, double sr, double si,
                                             const double *__restrict__ cl, double omega,
                                             double xi, double mu,
                                             const double2 *__restrict__ src,
+                                            const double2 *__restrict__ xa,
                                             double2 *__restrict__ x,
                                             typename Vec2<T>::type *__restrict__ xs_out,
-                                            double &num, double &den) {
+                                            double &num, double &den, double &dx) {
   const double s = omega * rg[i] * fold_sign<T>(l);  // ring sums are in s-units
   double ar = s * sr, ai = s * si;
   if (mode == ANA_FILTER) {
@@ -568,6 +569,11 @@ __device__ __forceinline__ void anal_finish(long i, int l, double sr, double si,
     const double dr = ar - old.x, di = ai - old.y;
     num += wm * (dr * dr + di * di);
     den += wm * (ar * ar + ai * ai);
+    if (xa) {  // anchored stage: ||x_a + delta||^2
+      const double2 b = xa[i];
+      const double tr = ar + b.x, ti = ai + b.y;
+      dx += wm * (tr * tr + ti * ti);
+    }
   }
   x[i] = make_double2(ar, ai);
   if (xs_out) {  // the synthesis input g a (times eps_l in FP32)
@@ -585,9 +591,10 @@ __device__ __forceinline__ void anal_finish(long i, int l, double sr, double si,
 __device__ __forceinline__ void anal_finish32(long i, int l, float sr, float si, int mode,
                                               const Tab32 &t32, float om, float xio,
                                               float muo, const double2 *__restrict__ src,
+                                              const double2 *__restrict__ xa,
                                               double2 *__restrict__ x,
                                               float2 *__restrict__ xs_out, double &num,
-                                              double &den) {
+                                              double &den, double &dx) {
   const float g = t32.rg[i];
   float ar = om * (g * sr), ai = om * (g * si);
   if (mode == ANA_FILTER) {
@@ -605,6 +612,11 @@ __device__ __forceinline__ void anal_finish32(long i, int l, float sr, float si,
     const double dr = ard - old.x, di = aid - old.y;
     num = fma(dr, dr, fma(di, di, num));
     den = fma(ard, ard, fma(aid, aid, den));
+    if (xa) {  // anchored stage: ||x_a + delta||^2
+      const double2 b = xa[i];
+      const double tr = ard + b.x, ti = aid + b.y;
+      dx = fma(tr, tr, fma(ti, ti, dx));
+    }
   }
   x[i] = make_double2(ar, ai);
   if (xs_out) xs_out[i] = make_float2(g * ar, g * ai);  // the synthesis input
@@ -629,29 +641,34 @@ __device__ __forceinline__ void anal_zero_above(int m, int L, int lmax, long bas
   }
 }
 
-// block sums of the Cauchy partials -> partials[2m], partials[2m + 1]
-// (fixed order: lanes by xor-butterfly, then warps in index order)
-__device__ __forceinline__ void anal_partials(double num, double den, int m,
-                                              double *__restrict__ partials) {
-  __shared__ double wsum[2][ANA_WARPS];
+// block sums of the Cauchy partials -> partials[2m], partials[2m + 1] and
+// (anchored stages) partials[2 (lmax + 1) + m] (fixed order: lanes by
+// xor-butterfly, then warps in index order)
+__device__ __forceinline__ void anal_partials(double num, double den, double dx, int m,
+                                              int lmax, double *__restrict__ partials) {
+  __shared__ double wsum[3][ANA_WARPS];
   for (int o = 16; o > 0; o >>= 1) {
     num += __shfl_xor_sync(0xffffffffu, num, o);
     den += __shfl_xor_sync(0xffffffffu, den, o);
+    dx += __shfl_xor_sync(0xffffffffu, dx, o);
   }
   const int warp = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
     wsum[0][warp] = num;
     wsum[1][warp] = den;
+    wsum[2][warp] = dx;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
+    double a = 0.0, b = 0.0, c = 0.0;
     for (int w = 0; w < ANA_WARPS; ++w) {
       a += wsum[0][w];
       b += wsum[1][w];
+      c += wsum[2][w];
     }
     partials[2 * m] = a;
     partials[2 * m + 1] = b;
+    partials[2 * (lmax + 1) + m] = c;
   }
 }
 
@@ -680,16 +697,18 @@ __device__ __forceinline__ void
   const int m = blockIdx.x;
   int L = lstatic;
   double xi = 0.0, mu = 0.0;
+  const double2 *xa = nullptr;  // anchored stage: the anchor iterate x_a
   if (st) {
     if (st->done) return;
     L = st->lcur;
     xi = st->xi;
     mu = st->mu;
+    xa = st->xa;
   }
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long base = lm_index(lmax, m, m);
   const double wm = (m == 0) ? 1.0 : 2.0;
-  double num = 0.0, den = 0.0;
+  double num = 0.0, den = 0.0, dx = 0.0;
 
   if (m <= L) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -788,7 +807,7 @@ __device__ __forceinline__ void
     const long wstride = GACC ? nalm : nl;
     if constexpr (sizeof(T) == 4) {
       const float om = (float)omega, xio = (float)(xi * omega), muo = (float)(mu * omega);
-      double nu = 0.0, de = 0.0;
+      double nu = 0.0, de = 0.0, dxu = 0.0;
       for (int j = tid; j < nl; j += ANA_THREADS) {
         float sr = 0.f, si = 0.f;
 #pragma unroll
@@ -796,11 +815,12 @@ __device__ __forceinline__ void
           sr += accr[w * wstride + j].x;
           si += accr[w * wstride + j].y;
         }
-        anal_finish32(base + j, m + j, sr, si, mode, t32, om, xio, muo, src, x, xs_out, nu,
-                      de);
+        anal_finish32(base + j, m + j, sr, si, mode, t32, om, xio, muo, src, xa, x, xs_out,
+                      nu, de, dxu);
       }
       num = wm * nu;
       den = wm * de;
+      dx = wm * dxu;
     } else {
       for (int j = tid; j < nl; j += ANA_THREADS) {
         double sr = 0.0, si = 0.0;
@@ -809,13 +829,13 @@ __device__ __forceinline__ void
           sr += (double)accr[w * wstride + j].x;
           si += (double)accr[w * wstride + j].y;
         }
-        anal_finish<T>(base + j, m + j, sr, si, wm, mode, rg, cl, omega, xi, mu, src, x,
-                       xs_out, num, den);
+        anal_finish<T>(base + j, m + j, sr, si, wm, mode, rg, cl, omega, xi, mu, src, xa, x,
+                       xs_out, num, den, dx);
       }
     }
   }
   anal_zero_above<T>(m, L, lmax, base, wm, mode, x, xs_out, num);
-  if (mode == ANA_FILTER) anal_partials(num, den, m, partials);
+  if (mode == ANA_FILTER) anal_partials(num, den, dx, m, lmax, partials);
 }
 
 #define WF_ANAL_PARAMS(T)                                                                 \
@@ -954,20 +974,22 @@ __global__ void __launch_bounds__(ANA_THREADS)
   const int m = blockIdx.x;
   int L = lstatic;
   double xi = 0.0, mu = 0.0;
+  const double2 *xa = nullptr;  // anchored stage: the anchor iterate x_a
   if (st) {
     if (st->done) return;
     L = st->lcur;
     xi = st->xi;
     mu = st->mu;
+    xa = st->xa;
   }
   if (m == 0 && threadIdx.x == 0) *counter = 0;
   const long base = lm_index(lmax, m, m);
   const double wm = (m == 0) ? 1.0 : 2.0;
-  double num = 0.0, den = 0.0;
+  double num = 0.0, den = 0.0, dx = 0.0;
   if (m <= L) {
     if constexpr (sizeof(T) == 4) {  // FP32 tiles: the FP32 epilogue
       const float om = (float)omega, xio = (float)(xi * omega), muo = (float)(mu * omega);
-      double nu = 0.0, de = 0.0;
+      double nu = 0.0, de = 0.0, dxu = 0.0;
       for (int j = threadIdx.x; j <= L - m; j += ANA_THREADS) {
         const int l = m + j;
         float sr = 0.f, si = 0.f;
@@ -977,10 +999,12 @@ __global__ void __launch_bounds__(ANA_THREADS)
           sr += p[0];
           si += p[1];
         }
-        anal_finish32(base + j, l, sr, si, mode, t32, om, xio, muo, src, x, xs_out, nu, de);
+        anal_finish32(base + j, l, sr, si, mode, t32, om, xio, muo, src, xa, x, xs_out, nu, de,
+                      dxu);
       }
       num = wm * nu;
       den = wm * de;
+      dx = wm * dxu;
     } else {
       for (int j = threadIdx.x; j <= L - m; j += ANA_THREADS) {
         const int l = m + j;
@@ -991,13 +1015,13 @@ __global__ void __launch_bounds__(ANA_THREADS)
           sr += (double)p[0];
           si += (double)p[1];
         }
-        anal_finish<T>(base + j, l, sr, si, wm, mode, rg, cl, omega, xi, mu, src, x, xs_out,
-                       num, den);
+        anal_finish<T>(base + j, l, sr, si, wm, mode, rg, cl, omega, xi, mu, src, xa, x, xs_out,
+                       num, den, dx);
       }
     }
   }
   anal_zero_above<T>(m, L, lmax, base, wm, mode, x, xs_out, num);
-  if (mode == ANA_FILTER) anal_partials(num, den, m, partials);
+  if (mode == ANA_FILTER) anal_partials(num, den, dx, m, lmax, partials);
 }
 
 // ------------------------------------------- double-float (df64) kernels

@@ -59,16 +59,8 @@ __device__ int band_of(const double *cl, int lmax, double mu, double omega,
 constexpr int CTRL_THREADS = 256;
 constexpr int PLATEAU_ITERS = 256;
 
-// mixed precision: the anchored last stage re-anchors when |delta| exceeds
-// ANCHOR_CAP |x_a|, which bounds the FP32 transform error it carries
-constexpr double ANCHOR_CAP = 1e-2;
+// mixed precision: bound on the re-anchorings of one solve
 constexpr int MAX_REANCHORS = 4096;
-// stages whose tolerance is below ANCHOR_EPS run anchored (the plain FP32
-// iteration has a Cauchy noise floor near 1e-5 at lmax = 2048; 3e-5 keeps a
-// factor 3 above it and took the same iteration counts as 1e-4 with 14
-// instead of 22 anchors at Nside 1024)
-constexpr double ANCHOR_EPS = 3e-5;
-
 
 __global__ void __launch_bounds__(CTRL_THREADS)
     k_control(SolverState *st, const double *__restrict__ partials, int lmax,
@@ -77,26 +69,32 @@ __global__ void __launch_bounds__(CTRL_THREADS)
   __shared__ int sh[CTRL_THREADS];
   __shared__ int advance;
   if (st->done) return;
-  double num = 0.0, den = 0.0;
+  __shared__ double sdx[CTRL_THREADS];
+  double num = 0.0, den = 0.0, dx = 0.0;
+  const bool anchored = st->xa != nullptr;
   for (int m = threadIdx.x; m <= lmax; m += CTRL_THREADS) {
     num += partials[2 * m];
     den += partials[2 * m + 1];
+    if (anchored) dx += partials[2 * (lmax + 1) + m];
   }
   snum[threadIdx.x] = num;
   sden[threadIdx.x] = den;
+  sdx[threadIdx.x] = dx;
   __syncthreads();
   for (int s = CTRL_THREADS / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
       snum[threadIdx.x] += snum[threadIdx.x + s];
       sden[threadIdx.x] += sden[threadIdx.x + s];
+      sdx[threadIdx.x] += sdx[threadIdx.x + s];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     num = snum[0];
     den = sden[0];
-    st->last_den = den;
-    if (st->den_fixed > 0.0) den = st->den_fixed;
+    st->last_den = den;  // anchored: ||delta||^2 (the re-anchoring test)
+    if (anchored) den = sdx[0];  // ||x_a + delta||^2 = ||x_i||^2
+    else if (st->den_fixed > 0.0) den = st->den_fixed;
     const double c = den > 0.0 ? sqrt(num / den) : 0.0;
     const int it = ++st->iter;
     const int si = st->stage_iter;          // iterations of this stage before this one
@@ -793,14 +791,14 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
   double fp_res = -1.0;
   *P.state_h = initial_state(P);
   if (P.opts.precision == WF_PREC_MIXED) {
-    // Mixed precision.  Stages with a loose tolerance (>= ANCHOR_EPS) run
+    // Mixed precision.  Stages with a loose tolerance (>= opts.anchor_eps) run
     // Algorithm 2 with FP32 transforms on x itself.  Every later stage runs
     // anchored: with x_a the iterate at the anchor and r = G64(x_a) - x_a
     // (one FP64 iteration map of the stage), iterate
     //   delta <- J32 delta + r,   x = x_a + delta,
     // which is the same iteration x <- G(x) written as a correction, so the
     // FP32 transform error scales with |delta| instead of |x|.  A new anchor
-    // is taken at each stage change, when |delta| exceeds ANCHOR_CAP |x_a|,
+    // is taken at each stage change, when |delta| exceeds opts.anchor_cap |x_a|,
     // and when progress stalls.
     bool converged = false;
     SolverState &h = *P.state_h;
@@ -808,8 +806,8 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
     k_data_f32<<<304, 256, 0, P.stream>>>(P.dmap, P.npix, P.dmap32);
     WF_CUDA(cudaGetLastError());
     h.noise_guard = 1;
-    h.anchor_eps = ANCHOR_EPS;
-    if (h.eps_k < ANCHOR_EPS) h.max_iter = 1;  // one plain step from t0 = d
+    h.anchor_eps = P.opts.anchor_eps;
+    if (h.eps_k < P.opts.anchor_eps) h.max_iter = 1;  // one plain step from t0 = d
     WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
                             cudaMemcpyHostToDevice, P.stream));
     WF_TRY(run_loop<float2>(P, 1, P.F32, P.G32, tinit, P.dmap, nullptr));
@@ -866,8 +864,8 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       s.lnext = stage.lnext;
       s.iter = total_iter;
       s.max_iter = P.opts.max_iter;
-      s.den_fixed = xn;
-      s.delta_cap2 = ANCHOR_CAP * ANCHOR_CAP * xn;
+      s.xa = P.xacc;  // Cauchy ratios of the iterate x_a + delta
+      s.delta_cap2 = P.opts.anchor_cap * P.opts.anchor_cap * xn;
       s.rate_floor = stage.mu == 0.0 ? rate_floor : 0.0;
       s.noise_guard = 1;
       s.boundary_stop = 1;

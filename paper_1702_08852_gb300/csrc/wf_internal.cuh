@@ -91,6 +91,10 @@ struct SolverState {
   double chist[16];   // Cauchy ratios of the last 16 iterations of the stage
   double cmin;        // smallest Cauchy ratio of the stage so far
   int since_min;      // iterations since cmin last fell by 1%
+  // anchored stage: the anchor iterate x_a (the analysis then also sums
+  // ||x_a + delta||^2, the Cauchy denominator ||x||^2 of the iterate the
+  // correction stands for); NULL otherwise
+  const double2 *xa;
 };
 
 struct TraceEntry {

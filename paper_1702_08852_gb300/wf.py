@@ -36,7 +36,8 @@ class wf_opts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("band_limit", ctypes.c_int),
                 ("graph_chunk", ctypes.c_int), ("refine_max", ctypes.c_int),
                 ("timing", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("anchor", ctypes.c_int)]
+                ("anchor", ctypes.c_int), ("anchor_eps", ctypes.c_double),
+                ("anchor_cap", ctypes.c_double)]
 
 
 class wf_stats(ctypes.Structure):
@@ -98,6 +99,8 @@ def lib():
             "wf_kernel_stats": (I, [_P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long),
                                     ctypes.POINTER(D), I]),
             "wf_legendre_terms": (I, [_P, I, ctypes.POINTER(D)]),
+            "wf_alu_peak": (I, [I, I, ctypes.POINTER(D), ctypes.POINTER(D),
+                                ctypes.POINTER(I)]),
             "wf_get_tuning": (I, [_P, ctypes.POINTER(_Tuning)]),
             "wf_set_tuning": (I, [_P, ctypes.POINTER(_Tuning)]),
             "wf_net_create": (I, [ctypes.POINTER(_P), _P, I, I, I, I]),
@@ -539,6 +542,15 @@ def wf_trace(plan):
 
 def wf_kernel_stats(plan, kernel=0, reset=False):
     return plan.kernel_stats(kernel, reset)
+
+
+def wf_alu_peak(kind, reps=5):
+    """Measured FMA-pipe peak of the current device: kind 0 = FP64, 1 = FP32,
+    2 = packed FP32.  Returns (tflops, best_ms, num_sms)."""
+    t, ms, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(lib().wf_alu_peak(int(kind), int(reps), ctypes.byref(t), ctypes.byref(ms),
+                             ctypes.byref(n)))
+    return t.value, ms.value, n.value
 
 
 def wf_legendre_terms(plan, L=None):

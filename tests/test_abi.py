@@ -136,3 +136,12 @@ def test_binding_checks_host_array_lengths():
         p.solve_host(np.zeros(p.npix - 1))
     with pytest.raises(ValueError):
         wf.Plan(4, 8, np.ones(5))
+
+
+def test_alu_peak_rejects_bad_arguments_before_cuda(wflib):
+    import ctypes as C
+    L = wflib.lib()
+    t = C.c_double()
+    assert L.wf_alu_peak(3, 1, C.byref(t), None, None) == wflib.WF_ERR_ARG
+    assert L.wf_alu_peak(1, 0, C.byref(t), None, None) == wflib.WF_ERR_ARG
+    assert L.wf_alu_peak(1, 1, None, None, None) == wflib.WF_ERR_ARG
