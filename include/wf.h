@@ -100,6 +100,11 @@ typedef struct {
                         >= eps_cap anchors every stage (default 3e-5). */
   double anchor_cap; /* WF_PREC_MIXED: an anchored stage takes a new anchor
                         when ||delta|| > anchor_cap ||x_a|| (default 1e-2). */
+  double decide_margin; /* WF_PREC_MIXED: when an anchored stage's Cauchy
+                        ratio first falls within (1 + decide_margin) of the
+                        stage's threshold, it takes a new anchor from a
+                        plain FP64 step, so the stage test runs on a fresh,
+                        small correction (0 = off). */
 } wf_opts;
 
 /* Per-solve statistics. */

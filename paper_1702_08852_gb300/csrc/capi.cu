@@ -114,6 +114,8 @@ static wf_status check_opts(const wf_opts &o) {
   if (o.anchor != 0 && o.anchor != 1) return arg_error("wf: anchor must be 0 or 1");
   if (!(o.anchor_eps >= 0.0) || !(o.anchor_cap > 0.0 && o.anchor_cap <= 1.0))
     return arg_error("wf: anchor_eps must be >= 0 and anchor_cap in (0, 1]");
+  if (!(o.decide_margin >= 0.0 && o.decide_margin <= 1.0))
+    return arg_error("wf: decide_margin must be in [0, 1]");
   return WF_OK;
 }
 
@@ -139,6 +141,7 @@ void wf_opts_default(wf_opts *o) {
   o->anchor = 1;
   o->anchor_eps = 3e-5;
   o->anchor_cap = 1e-2;
+  o->decide_margin = 0.0;
 }
 
 long wf_npix(int nside) { return 12L * nside * nside; }

@@ -120,9 +120,17 @@ __global__ void __launch_bounds__(CTRL_THREADS)
       st->since_min += 1;
     }
     const bool plateau = st->noise_guard && st->since_min >= PLATEAU_ITERS && c < 1e-3;
+    const double thr = st->mu == 0.0 ? st->eps_final : st->eps_k;
+    const bool near_window = anchored && st->near_factor > 1.0 && !st->near_done &&
+                             (st->mu != 0.0 || st->stop_rule == WF_STOP_CAUCHY) &&
+                             c >= thr && c < thr * st->near_factor;
     if (!isfinite(c) || !isfinite(num)) {
       st->numeric_error = 1;
       st->done = 1;
+    } else if (near_window) {
+      st->done = 1;
+      st->reanchor = 1;
+      st->near_hit = 1;
     } else if (st->mu == 0.0) {
       // arithmetic noise floor: the Cauchy ratio has stopped falling
       st->flat = (st->prev_c > 0.0 && c >= st->prev_c) ? st->flat + 1 : 0;
@@ -181,6 +189,7 @@ __global__ void __launch_bounds__(CTRL_THREADS)
                       ? st->eps_final
                       : fmin(st->eps_cap, st->eps_final * fmax(1.0, st->mu / st->alpha));
       st->lcur = st->lnext;
+      st->near_done = 0;
     }
     if (adv && st->mu == 0.0 && st->handoff) {
       st->done = 1;
@@ -510,7 +519,8 @@ static wf_status capture_graph(Plan &P, int which, T2 *F, T2 *G, const double *d
 // have been uploaded.
 template <typename T2>
 static wf_status run_loop(Plan &P, int which, T2 *F, T2 *G, const double *tinit,
-                          const double *data, const double2 *src, bool keep_G = false) {
+                          const double *data, const double2 *src, bool keep_G = false,
+                          bool timed = true) {
   if (keep_G) {
     // G already holds the messenger's ring coefficients
   } else if (tinit) {
@@ -528,7 +538,7 @@ static wf_status run_loop(Plan &P, int which, T2 *F, T2 *G, const double *tinit,
     WF_CUDA(cudaMemcpyAsync(P.state_h, P.state, sizeof(SolverState),
                             cudaMemcpyDeviceToHost, P.stream));
     WF_CUDA(cudaStreamSynchronize(P.stream));
-    if (P.opts.timing) {
+    if (P.opts.timing && timed) {
       // iterations that did work in this launch: the first (iter - it0)
       const int active = std::min(P.state_h->iter - it0, P.graph_chunk[which]);
       const int C = P.tev_chunk;
@@ -807,10 +817,18 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
     WF_CUDA(cudaGetLastError());
     h.noise_guard = 1;
     h.anchor_eps = P.opts.anchor_eps;
-    if (h.eps_k < P.opts.anchor_eps) h.max_iter = 1;  // one plain step from t0 = d
+    // every stage anchored: one plain FP64 step from t0 = d gives the first
+    // anchor (untimed: the kernel statistics cover the FP32 kernels)
+    const bool first64 = h.eps_k < P.opts.anchor_eps;
+    if (first64) h.max_iter = 1;
     WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
                             cudaMemcpyHostToDevice, P.stream));
-    WF_TRY(run_loop<float2>(P, 1, P.F32, P.G32, tinit, P.dmap, nullptr));
+    if (first64) {
+      P.untimed.push_back(0);
+      WF_TRY(run_loop<double2>(P, 0, P.F64, P.G64, tinit, P.dmap, nullptr, false, false));
+    } else {
+      WF_TRY(run_loop<float2>(P, 1, P.F32, P.G32, tinit, P.dmap, nullptr));
+    }
     if (h.numeric_error) {
       set_error("wf_solve: NaN or Inf in the iteration");
       return WF_ERR_NUMERIC;
@@ -846,8 +864,10 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       const SolverState stage = h;  // stage parameters of this anchor
       const bool carry = boundary && uprev != nullptr;
       double num = 0.0, xn = 0.0;
+      // a near-decision anchor runs in plain FP64: the stage test that
+      // follows needs the step to FP64 accuracy
       WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num, stage.xi, stage.mu, stage.lcur,
-                       P.opts.anchor == 1, P.uacc[ucur], stage.lnext));
+                       P.opts.anchor == 1 && !stage.near_hit, P.uacc[ucur], stage.lnext));
       WF_TRY(alm_dot(P, P.xacc, P.xacc, nullptr, &xn));
       ++P.nlaunch;
       k_make_source<<<P.lmax + 1, 128, 0, P.stream>>>(P.xtmp, P.xacc, P.cl_d, stage.xi,
@@ -869,6 +889,9 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       s.rate_floor = stage.mu == 0.0 ? rate_floor : 0.0;
       s.noise_guard = 1;
       s.boundary_stop = 1;
+      s.near_factor = 1.0 + P.opts.decide_margin;
+      s.near_done = stage.near_done || stage.near_hit;
+      s.near_hit = 0;
       h = s;
       WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
                               cudaMemcpyHostToDevice, P.stream));

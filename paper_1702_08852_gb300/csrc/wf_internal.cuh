@@ -95,6 +95,12 @@ struct SolverState {
   // ||x_a + delta||^2, the Cauchy denominator ||x||^2 of the iterate the
   // correction stands for); NULL otherwise
   const double2 *xa;
+  // anchored stage, near-decision re-anchoring: when the Cauchy ratio first
+  // falls below near_factor times the stage's threshold (but not below it),
+  // stop for a new anchor from a plain FP64 step (near_hit), so that the
+  // stage test runs on a fresh, small correction; once per stage (near_done)
+  double near_factor;
+  int near_hit, near_done;
 };
 
 struct TraceEntry {
