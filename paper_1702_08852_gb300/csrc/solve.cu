@@ -176,6 +176,9 @@ __global__ void __launch_bounds__(CTRL_THREADS)
     st->prev_c = c;
     st->last_c = c;
     if (adv) {
+      st->xi_prev = st->xi;
+      st->mu_prev = st->mu;
+      st->lcur_prev = st->lcur;
       const double xi = fmax(st->alpha, st->beta * st->xi);
       st->xi = xi;
       st->mu = xi > st->alpha ? xi - st->alpha : 0.0;
@@ -615,32 +618,6 @@ __global__ void k_filter_from_u(const double2 *__restrict__ U, const double2 *__
   }
 }
 
-// Source of the first iteration after a stage boundary between anchored
-// stages: with the previous anchor's U = Omega Y^T t_a (old stage's weights)
-// and the correction messenger tau still in place, the analysis
-// f (Omega Y^T tau + xi Omega src) must give f (Omega Y^T tau + U) - x_last,
-// i.e. the paper's first step of the new stage from the old messenger:
-// src = U / (xi Omega) - x_last (Sbar + xi Omega) / (Sbar xi Omega) where
-// Sbar > 0 (0 elsewhere, where x_last = 0 as well)
-__global__ void k_make_source_carry(const double2 *__restrict__ U,
-                                    const double2 *__restrict__ x, const double *__restrict__ cl,
-                                    double xi, double mu, double omega, int L, int lmax,
-                                    double2 *__restrict__ src) {
-  const int m = blockIdx.x;
-  const long base = (long)m * (2 * lmax + 1 - m) / 2;
-  const double xo = xi * omega;
-  for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
-    const long i = base + l;
-    const double sb = fmax(cl[l] - mu * omega, 0.0);
-    double2 v = make_double2(0.0, 0.0);
-    if (l <= L && sb > 0.0) {
-      const double s = (sb + xo) / (sb * xo);
-      v = make_double2(U[i].x / xo - s * x[i].x, U[i].y / xo - s * x[i].y);
-    }
-    src[i] = v;
-  }
-}
-
 __global__ void k_alm_add(double2 *x, const double2 *y, long n) {
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long)gridDim.x * blockDim.x)
@@ -773,6 +750,70 @@ static wf_status slow_rate(Plan &P, int i0, int i1, double *rate) {
   return WF_OK;
 }
 
+// First iterate of a new stage (h: the state just after the advance, with
+// the old stage in xi_prev, mu_prev, lcur_prev), as Algorithm 2 takes it:
+// t from the last iterate x = P.xacc with the old stage's weights, then
+// x_first = f_new Omega Y^T t on the new band -- in the anchor arithmetic
+// (the FP32 correction messenger, grown over the whole old stage, would
+// bring an error of the size of a step).  Updates P.xacc, the iteration
+// count and the trace; advances again (on the host, as k_control does) in
+// the rare case that this step already passes the new stage's test.
+static wf_status boundary_step(Plan &P, SolverState &hio, int *total_iter) {
+  SolverState h = hio;  // hio may be the host mirror, which fp64_step overwrites
+  for (;;) {
+    double num = 0.0;
+    WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num, h.xi_prev, h.mu_prev, h.lcur_prev,
+                     P.opts.anchor == 1, P.uacc[0], h.lcur));
+    ++P.nlaunch;
+    k_filter_from_u<<<P.lmax + 1, 128, 0, P.stream>>>(P.uacc[0], P.xacc, P.cl_d, h.xi, h.mu,
+                                                      P.omega, h.lcur, P.lmax, P.xtmp,
+                                                      P.partials);
+    WF_CUDA(cudaGetLastError());
+    std::vector<double> part(2 * (P.lmax + 1));
+    WF_CUDA(cudaMemcpyAsync(part.data(), P.partials, sizeof(double) * part.size(),
+                            cudaMemcpyDeviceToHost, P.stream));
+    WF_CUDA(cudaMemcpyAsync(P.xacc, P.xtmp, sizeof(double2) * P.nalm,
+                            cudaMemcpyDeviceToDevice, P.stream));
+    WF_CUDA(cudaStreamSynchronize(P.stream));
+    double nu = 0.0, de = 0.0;
+    for (int m = 0; m <= P.lmax; ++m) {
+      nu += part[2 * m];
+      de += part[2 * m + 1];
+    }
+    const double c = de > 0.0 ? sqrt(nu / de) : 0.0;
+    const int it = (*total_iter)++;
+    P.untimed.push_back(it);
+    if (it < P.trace_cap) {
+      TraceEntry e;
+      e.stage = h.stage;
+      e.lcur = h.lcur;
+      e.xi = h.xi;
+      e.mu = h.mu;
+      e.cauchy = c;
+      WF_CUDA(cudaMemcpy(P.trace + it, &e, sizeof(e), cudaMemcpyHostToDevice));
+    }
+    h.iter = *total_iter;
+    h.last_c = c;
+    if (!(h.mu > 0.0 && c < h.eps_k)) {
+      hio = h;
+      return WF_OK;
+    }
+    // the new stage's test passed at once: the next stage
+    h.xi_prev = h.xi;
+    h.mu_prev = h.mu;
+    h.lcur_prev = h.lcur;
+    h.xi = std::max(P.alpha, h.beta * h.xi);
+    h.mu = h.xi > P.alpha ? h.xi - P.alpha : 0.0;
+    h.stage += 1;
+    h.eps_k = h.mu == 0.0 ? h.eps_final
+                          : std::min(h.eps_cap, h.eps_final * std::max(1.0, h.mu / P.alpha));
+    h.lcur = h.lnext;
+    const double xi2 = std::max(P.alpha, h.beta * h.xi);
+    const double mu2 = xi2 > P.alpha ? xi2 - P.alpha : 0.0;
+    h.lnext = P.opts.band_limit ? band_host(P.cl, mu2, P.omega) : P.lmax;
+  }
+}
+
 wf_status solve(Plan &P, const double *d, double *alm, double *map,
                 const double *init_alm, const double *init_map, wf_stats *stats) {
   if (!P.has_noise) {
@@ -846,33 +887,28 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
                             cudaMemcpyDeviceToDevice, P.stream));
     double prev_rel = -1.0, rate_floor = 0.0;
     int cycles = 0, reanchors = 0, cycle_start = total_iter;
-    if (!P.uacc[0]) {
-      WF_CUDA(cudaMalloc(&P.uacc[0], sizeof(double2) * P.nalm));
-      WF_CUDA(cudaMalloc(&P.uacc[1], sizeof(double2) * P.nalm));
-      WF_CUDA(cudaMalloc(&P.src2, sizeof(double2) * P.nalm));
-    }
-    // At a boundary between anchored stages the paper's iteration takes the
-    // new stage's first step from the old stage's messenger t (Algorithm 2
-    // carries t, not x, across the cooling step).  The correction form does
-    // the same: the last anchor's unfiltered U = Omega Y^T t_a and the
-    // correction messenger tau still in G32 give the first step through a
-    // one-off source; the new anchor's source takes over from the second.
-    int ucur = 0;
-    const double2 *uprev = nullptr;
-    bool boundary = false;
+    if (!P.uacc[0]) WF_CUDA(cudaMalloc(&P.uacc[0], sizeof(double2) * P.nalm));
+    // At a stage boundary Algorithm 2 carries the messenger t, not x, across
+    // the cooling step: the new stage's first iterate is f_new Omega Y^T t
+    // with t from the last iterate and the old stage's weights.  That step is
+    // taken here in the anchor arithmetic (boundary_step), from the
+    // accumulated iterate x_a + delta; the new stage then anchors at it.
+    bool boundary = h.at_boundary != 0;
     while (anchored && reanchors <= MAX_REANCHORS && cycles <= P.opts.refine_max) {
+      if (boundary) {
+        WF_TRY(boundary_step(P, h, &total_iter));
+        boundary = false;
+      }
       const SolverState stage = h;  // stage parameters of this anchor
-      const bool carry = boundary && uprev != nullptr;
       double num = 0.0, xn = 0.0;
       // a near-decision anchor runs in plain FP64: the stage test that
       // follows needs the step to FP64 accuracy
       WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num, stage.xi, stage.mu, stage.lcur,
-                       P.opts.anchor == 1 && !stage.near_hit, P.uacc[ucur], stage.lnext));
+                       P.opts.anchor == 1 && !stage.near_hit));
       WF_TRY(alm_dot(P, P.xacc, P.xacc, nullptr, &xn));
       ++P.nlaunch;
       k_make_source<<<P.lmax + 1, 128, 0, P.stream>>>(P.xtmp, P.xacc, P.cl_d, stage.xi,
-                                                      stage.mu, P.omega, P.lmax,
-                                                      carry ? P.src2 : P.src);
+                                                      stage.mu, P.omega, P.lmax, P.src);
       WF_CUDA(cudaGetLastError());
       WF_CUDA(cudaMemsetAsync(P.x, 0, sizeof(double2) * P.nalm, P.stream));
       SolverState s = initial_state(P);
@@ -895,24 +931,7 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       h = s;
       WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
                               cudaMemcpyHostToDevice, P.stream));
-      if (carry) {
-        ++P.nlaunch;
-        k_make_source_carry<<<P.lmax + 1, 128, 0, P.stream>>>(
-            uprev, P.xacc, P.cl_d, stage.xi, stage.mu, P.omega, stage.lcur, P.lmax, P.src);
-        WF_CUDA(cudaGetLastError());
-        P.untimed.push_back(h.iter);
-        WF_TRY(enqueue_iteration<float2>(P, P.F32, P.G32, nullptr, P.src, -1));
-        WF_CUDA(cudaMemcpyAsync(P.src, P.src2, sizeof(double2) * P.nalm,
-                                cudaMemcpyDeviceToDevice, P.stream));
-        WF_CUDA(cudaMemcpyAsync(P.state_h, P.state, sizeof(SolverState),
-                                cudaMemcpyDeviceToHost, P.stream));
-        WF_CUDA(cudaStreamSynchronize(P.stream));
-        if (!h.done) WF_TRY(run_loop<float2>(P, 2, P.F32, P.G32, nullptr, nullptr, P.src, true));
-      } else {
-        WF_TRY(run_loop<float2>(P, 2, P.F32, P.G32, nullptr, nullptr, P.src));
-      }
-      uprev = P.uacc[ucur];
-      ucur ^= 1;
+      WF_TRY(run_loop<float2>(P, 2, P.F32, P.G32, nullptr, nullptr, P.src));
       total_iter = h.iter;
       if (h.numeric_error) {
         set_error("wf_solve: NaN or Inf in an anchored stage");

@@ -101,6 +101,9 @@ struct SolverState {
   // stage test runs on a fresh, small correction; once per stage (near_done)
   double near_factor;
   int near_hit, near_done;
+  // the stage before the last advance (its xi, mu and band)
+  double xi_prev, mu_prev;
+  int lcur_prev;
 };
 
 struct TraceEntry {
@@ -192,7 +195,6 @@ struct Plan {
   // FP64 analysis U = Omega Y^T t_a of the last two anchors and the next
   // source (allocated by the first mixed solve)
   double2 *uacc[2] = {nullptr, nullptr};
-  double2 *src2 = nullptr;
   std::vector<int> untimed;      // iterations run outside the timed graphs
   double *dmap = nullptr;        // [npix] data with masked pixels zeroed
   float *dmap32 = nullptr;       // [npix] FP32 copy of dmap (FP32 ring step)
