@@ -633,7 +633,7 @@ __global__ void k_alm_add(double2 *x, const double2 *y, long n) {
 // max(L, Lu) (the next stage's band) -- gx is then f U.
 static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
                            double xi, double mu, int L, bool dd = false,
-                           double2 *U = nullptr, int Lu = -1) {
+                           double2 *U = nullptr, int Lu = -1, double *den = nullptr) {
   SolverState s = initial_state(P);
   s.xi = xi;
   s.mu = mu;
@@ -671,9 +671,13 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
   WF_CUDA(cudaMemcpyAsync(part.data(), P.partials, sizeof(double) * part.size(),
                           cudaMemcpyDeviceToHost, P.stream));
   WF_CUDA(cudaStreamSynchronize(P.stream));
-  double acc = 0.0;
-  for (int m = 0; m <= P.lmax; ++m) acc += part[2 * m];
+  double acc = 0.0, acd = 0.0;
+  for (int m = 0; m <= P.lmax; ++m) {
+    acc += part[2 * m];
+    acd += part[2 * m + 1];
+  }
   *num = acc;
+  if (den) *den = acd;
   return WF_OK;
 }
 static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num) {
@@ -814,6 +818,63 @@ static wf_status boundary_step(Plan &P, SolverState &hio, int *total_iter) {
   }
 }
 
+// Iterations x <- G(x) of a tail stage (mu <= alpha) in the anchor
+// arithmetic, from P.xacc, with the Cauchy test of k_control.  Returns with
+// *last_done set when the last stage (mu = 0) passes its test, or with hio
+// advanced to the next stage (not yet entered: its first iterate is the
+// boundary step), or when max_iter is reached.
+static wf_status tail_stage(Plan &P, SolverState &hio, int *total_iter, bool *last_done) {
+  SolverState h = hio;  // hio may be the host mirror, which fp64_step overwrites
+  const bool dd = P.opts.anchor == 1;
+  *last_done = false;
+  while (*total_iter < P.opts.max_iter) {
+    double nu = 0.0, de = 0.0;
+    WF_TRY(fp64_step(P, P.xacc, P.xtmp, &nu, h.xi, h.mu, h.lcur, dd, nullptr, -1, &de));
+    WF_CUDA(cudaMemcpyAsync(P.xacc, P.xtmp, sizeof(double2) * P.nalm,
+                            cudaMemcpyDeviceToDevice, P.stream));
+    const double c = de > 0.0 ? sqrt(nu / de) : 0.0;
+    const int it = (*total_iter)++;
+    P.untimed.push_back(it);
+    if (it < P.trace_cap) {
+      TraceEntry e;
+      e.stage = h.stage;
+      e.lcur = h.lcur;
+      e.xi = h.xi;
+      e.mu = h.mu;
+      e.cauchy = c;
+      WF_CUDA(cudaMemcpy(P.trace + it, &e, sizeof(e), cudaMemcpyHostToDevice));
+    }
+    h.iter = *total_iter;
+    h.last_c = c;
+    if (!std::isfinite(c)) {
+      set_error("wf_solve: NaN or Inf in a tail stage");
+      return WF_ERR_NUMERIC;
+    }
+    if (h.mu == 0.0) {
+      if (c < h.eps_final) {
+        *last_done = true;
+        break;
+      }
+    } else if (c < h.eps_k) {
+      h.xi_prev = h.xi;
+      h.mu_prev = h.mu;
+      h.lcur_prev = h.lcur;
+      h.xi = std::max(P.alpha, h.beta * h.xi);
+      h.mu = h.xi > P.alpha ? h.xi - P.alpha : 0.0;
+      h.stage += 1;
+      h.eps_k = h.mu == 0.0 ? h.eps_final
+                            : std::min(h.eps_cap, h.eps_final * std::max(1.0, h.mu / P.alpha));
+      h.lcur = h.lnext;
+      const double xi2 = std::max(P.alpha, h.beta * h.xi);
+      const double mu2 = xi2 > P.alpha ? xi2 - P.alpha : 0.0;
+      h.lnext = P.opts.band_limit ? band_host(P.cl, mu2, P.omega) : P.lmax;
+      break;
+    }
+  }
+  hio = h;
+  return WF_OK;
+}
+
 wf_status solve(Plan &P, const double *d, double *alm, double *map,
                 const double *init_alm, const double *init_map, wf_stats *stats) {
   if (!P.has_noise) {
@@ -898,6 +959,33 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       if (boundary) {
         WF_TRY(boundary_step(P, h, &total_iter));
         boundary = false;
+      }
+      if (P.opts.tail_exact && h.mu <= P.alpha && P.opts.stop_rule == WF_STOP_CAUCHY) {
+        // the tail stages (mu <= alpha: each one's tolerance is eps_final)
+        // iterate in the anchor arithmetic, so that their Cauchy tests see
+        // the step to FP64 accuracy
+        bool last_done = false;
+        WF_TRY(tail_stage(P, h, &total_iter, &last_done));
+        if (!last_done) {
+          if (total_iter >= P.opts.max_iter) break;
+          boundary = true;  // the next stage starts with its boundary step
+          continue;
+        }
+        // accept when the plain FP64 step from the result passes the test
+        const SolverState keep = h;
+        double num = 0.0, xn2 = 0.0;
+        WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num, keep.xi, keep.mu, keep.lcur));
+        WF_TRY(alm_dot(P, P.xacc, P.xacc, nullptr, &xn2));
+        const double c64 = xn2 > 0.0 ? sqrt(num / xn2) : 0.0;
+        h = keep;
+        h.iter = total_iter;
+        if (c64 < P.opts.eps_final) {
+          converged = true;
+          fp_res = c64;
+          break;
+        }
+        ++reanchors;
+        continue;
       }
       const SolverState stage = h;  // stage parameters of this anchor
       double num = 0.0, xn = 0.0;
