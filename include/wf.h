@@ -105,6 +105,9 @@ typedef struct {
                         stage's threshold, it takes a new anchor from a
                         plain FP64 step, so the stage test runs on a fresh,
                         small correction (0 = off). */
+  double anchor_cap_tol; /* WF_PREC_MIXED: > 0 tightens anchor_cap to
+                        anchor_cap_tol times the stage's tolerance
+                        (default 0 = off). */
   int tail_exact;    /* WF_PREC_MIXED with WF_STOP_CAUCHY: 1 = the tail
                         stages (mu <= alpha, each with tolerance eps_final)
                         iterate in the anchor arithmetic instead of FP32, so

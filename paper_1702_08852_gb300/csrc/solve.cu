@@ -1009,7 +1009,12 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       s.iter = total_iter;
       s.max_iter = P.opts.max_iter;
       s.xa = P.xacc;  // Cauchy ratios of the iterate x_a + delta
-      s.delta_cap2 = P.opts.anchor_cap * P.opts.anchor_cap * xn;
+      // re-anchoring bound on ||delta|| / ||x_a||: anchor_cap, tightened to
+      // anchor_cap_tol times the stage tolerance (the FP32 error of a step
+      // scales with ||delta||, and late stages take steps of ~eps_k ||x||)
+      double cap = P.opts.anchor_cap;
+      if (P.opts.anchor_cap_tol > 0.0) cap = std::min(cap, P.opts.anchor_cap_tol * stage.eps_k);
+      s.delta_cap2 = cap * cap * xn;
       s.rate_floor = stage.mu == 0.0 ? rate_floor : 0.0;
       s.noise_guard = 1;
       s.boundary_stop = 1;
