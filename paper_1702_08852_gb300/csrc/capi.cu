@@ -116,8 +116,6 @@ static wf_status check_opts(const wf_opts &o) {
     return arg_error("wf: anchor_eps must be >= 0 and anchor_cap in (0, 1]");
   if (o.tail_exact != 0 && o.tail_exact != 1) return arg_error("wf: tail_exact must be 0 or 1");
   if (!(o.anchor_cap_tol >= 0.0)) return arg_error("wf: anchor_cap_tol must be >= 0");
-  if (!(o.decide_margin >= 0.0 && o.decide_margin <= 1.0))
-    return arg_error("wf: decide_margin must be in [0, 1]");
   return WF_OK;
 }
 
@@ -141,9 +139,10 @@ void wf_opts_default(wf_opts *o) {
   o->graph_chunk = 0;
   o->refine_max = 8;
   o->anchor = 1;
-  o->anchor_eps = 3e-5;
+  o->anchor_eps = 1.0;
   o->anchor_cap = 1e-2;
-  o->decide_margin = 0.0;
+  o->anchor_cap_tol = 100.0;
+  o->tail_exact = 1;
 }
 
 long wf_npix(int nside) { return 12L * nside * nside; }

@@ -120,17 +120,9 @@ __global__ void __launch_bounds__(CTRL_THREADS)
       st->since_min += 1;
     }
     const bool plateau = st->noise_guard && st->since_min >= PLATEAU_ITERS && c < 1e-3;
-    const double thr = st->mu == 0.0 ? st->eps_final : st->eps_k;
-    const bool near_window = anchored && st->near_factor > 1.0 && !st->near_done &&
-                             (st->mu != 0.0 || st->stop_rule == WF_STOP_CAUCHY) &&
-                             c >= thr && c < thr * st->near_factor;
     if (!isfinite(c) || !isfinite(num)) {
       st->numeric_error = 1;
       st->done = 1;
-    } else if (near_window) {
-      st->done = 1;
-      st->reanchor = 1;
-      st->near_hit = 1;
     } else if (st->mu == 0.0) {
       // arithmetic noise floor: the Cauchy ratio has stopped falling
       st->flat = (st->prev_c > 0.0 && c >= st->prev_c) ? st->flat + 1 : 0;
@@ -192,7 +184,6 @@ __global__ void __launch_bounds__(CTRL_THREADS)
                       ? st->eps_final
                       : fmin(st->eps_cap, st->eps_final * fmax(1.0, st->mu / st->alpha));
       st->lcur = st->lnext;
-      st->near_done = 0;
     }
     if (adv && st->mu == 0.0 && st->handoff) {
       st->done = 1;
@@ -989,10 +980,8 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       }
       const SolverState stage = h;  // stage parameters of this anchor
       double num = 0.0, xn = 0.0;
-      // a near-decision anchor runs in plain FP64: the stage test that
-      // follows needs the step to FP64 accuracy
       WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num, stage.xi, stage.mu, stage.lcur,
-                       P.opts.anchor == 1 && !stage.near_hit));
+                       P.opts.anchor == 1));
       WF_TRY(alm_dot(P, P.xacc, P.xacc, nullptr, &xn));
       ++P.nlaunch;
       k_make_source<<<P.lmax + 1, 128, 0, P.stream>>>(P.xtmp, P.xacc, P.cl_d, stage.xi,
@@ -1018,9 +1007,6 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       s.rate_floor = stage.mu == 0.0 ? rate_floor : 0.0;
       s.noise_guard = 1;
       s.boundary_stop = 1;
-      s.near_factor = 1.0 + P.opts.decide_margin;
-      s.near_done = stage.near_done || stage.near_hit;
-      s.near_hit = 0;
       h = s;
       WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
                               cudaMemcpyHostToDevice, P.stream));

@@ -95,12 +95,6 @@ struct SolverState {
   // ||x_a + delta||^2, the Cauchy denominator ||x||^2 of the iterate the
   // correction stands for); NULL otherwise
   const double2 *xa;
-  // anchored stage, near-decision re-anchoring: when the Cauchy ratio first
-  // falls below near_factor times the stage's threshold (but not below it),
-  // stop for a new anchor from a plain FP64 step (near_hit), so that the
-  // stage test runs on a fresh, small correction; once per stage (near_done)
-  double near_factor;
-  int near_hit, near_done;
   // the stage before the last advance (its xi, mu and band)
   double xi_prev, mu_prev;
   int lcur_prev;

@@ -37,8 +37,7 @@ class wf_opts(ctypes.Structure):
                 ("graph_chunk", ctypes.c_int), ("refine_max", ctypes.c_int),
                 ("timing", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("anchor", ctypes.c_int), ("anchor_eps", ctypes.c_double),
-                ("anchor_cap", ctypes.c_double), ("decide_margin", ctypes.c_double),
-                ("anchor_cap_tol", ctypes.c_double), ("tail_exact", ctypes.c_int)]
+                ("anchor_cap", ctypes.c_double), ("anchor_cap_tol", ctypes.c_double), ("tail_exact", ctypes.c_int)]
 
 
 class wf_stats(ctypes.Structure):

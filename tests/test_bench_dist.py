@@ -52,9 +52,12 @@ def test_single_rank_defaults():
     assert bench.aggregate_value(1, 2, 4000.0) == pytest.approx(0.5)
 
 
-def test_analysis_traffic_only_for_the_captured_variant():
+def test_analysis_traffic_only_for_the_captured_variant(monkeypatch):
     import bench
-    ref = bench.ANALYSIS_DRAM_FULL_BAND
+    if bench.ANALYSIS_DRAM_FULL_BAND["bytes"] is None:  # no capture of the current kernel
+        assert bench.analysis_traffic(1024, 22.0, 1) is None
+    ref = dict(bench.ANALYSIS_DRAM_FULL_BAND, bytes=2.0e8)
+    monkeypatch.setattr(bench, "ANALYSIS_DRAM_FULL_BAND", ref)
     tuning = {"ana_np": [4, ref["variant"]["ana_np"]], "ana_queue": ref["variant"]["ana_queue"],
               "ana_packed": ref["variant"]["ana_packed"],
               "ana_global_acc": ref["variant"]["ana_global_acc"]}

@@ -165,6 +165,9 @@ def test_cauchy_rule_matches_oracle_and_mixed(torch_cuda, osht, odm):
     assert rel_alm(osht, alm, xo, p.lmax) < 1e-8
     alm2, mp2, st2, tr2 = gpu_solve(torch, p, d, eps_final=1e-6, precision=1)
     assert st2["converged"] == 1 and tr2["cauchy"][-1] < 1e-6
+    # the mixed path reproduces the FP64 result under the same rule
+    assert np.linalg.norm(mp2 - mp) / np.linalg.norm(mp) < 1e-6
+    assert st2["iterations"] == st["iterations"]
 
 
 def test_deterministic(torch_cuda, osht):
@@ -259,8 +262,32 @@ def test_mixed_stage_lengths_match_fp64(torch_cuda, osht, nside, kind, seed):
     assert st32["refinements"] >= 1  # anchored stages were run
     n64 = np.bincount(np.asarray(tr64["stage"]))
     n32 = np.bincount(np.asarray(tr32["stage"]))
-    assert len(n32) == len(n64)
-    assert np.all(np.abs(n32.astype(int) - n64.astype(int)) <= 2), (n32, n64)
+    assert np.array_equal(n32, n64), (n32, n64)
+
+
+@pytest.mark.parametrize("nside,lsig", [(128, 256), (256, 128)])
+def test_mixed_matches_fp64_solve_at_scale(torch_cuda, osht, nside, lsig):
+    """The scan-noise workload (hits 1-100, 25 % mask: galactic band and 500
+    discs of 0.5 deg) at Nside 128 and 256 (lmax 2 Nside; the signal of the
+    data map band-limited to lsig so that the oracle synthesises it in
+    seconds): under the paper's Cauchy rule the mixed path takes the FP64
+    solve's stage lengths and its map is within 1e-6 relative L2 of the FP64
+    map."""
+    torch = torch_cuda
+    from paper_1702_08852_gb300 import inputs
+    p = inputs.scan_problem(nside, seed=11, mask_fraction=0.25, discs=500,
+                            disc_radius_deg=0.5)
+    ls, _ = inputs.lm_of_slots(p.lmax)
+    a = p.alm_true[ls <= lsig] if lsig < p.lmax else p.alm_true
+    d = p.data(osht.alm2map(a, p.nside, min(lsig, p.lmax)))
+    _, m64, st64, tr64 = gpu_solve(torch, p, d, precision=0, eps_final=1e-6)
+    _, m32, st32, tr32 = gpu_solve(torch, p, d, precision=1, eps_final=1e-6)
+    assert st64["converged"] == 1 and st32["converged"] == 1
+    n64 = np.bincount(np.asarray(tr64["stage"]))
+    n32 = np.bincount(np.asarray(tr32["stage"]))
+    assert np.array_equal(n32, n64), (n32, n64)
+    err = np.linalg.norm(m32 - m64) / np.linalg.norm(m64)
+    assert err < 1e-6, err
 
 
 def test_set_cl_equals_a_plan_made_with_it(torch_cuda, osht):
