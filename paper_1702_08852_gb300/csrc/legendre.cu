@@ -1072,12 +1072,67 @@ __device__ __forceinline__ void dd_acc(dd &acc, dd u, dd x) {
   acc.hi = s;
   acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
 }
-// u_l = c_l z u_{l-1} - u_{l-2}
+// u_l = c_l z u_{l-1} - u_{l-2}: t = c u_{l-1} in double-float, then the
+// product t z (two-product, unnormalised) and the difference with u_{l-2}
+// (two-sum) with one final normalisation
 __device__ __forceinline__ dd dd_rec(dd c, dd z, dd u1, dd u2) {
-  return dd_sub(dd_mul(dd_mul(c, u1), z), u2);
+  const dd t = dd_mul(c, u1);
+  const float p = __fmul_rn(t.hi, z.hi);
+  float e = fmaf(t.hi, z.hi, -p);
+  e = fmaf(t.hi, z.lo, fmaf(t.lo, z.hi, e));
+  const float s = __fsub_rn(p, u2.hi);
+  const float bb = __fsub_rn(s, p);
+  const float err = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(-u2.hi, bb));
+  return dd_quick(s, __fadd_rn(__fsub_rn(e, u2.lo), err));
 }
 
 constexpr int DD_NP_SYN = 2, DD_NP_ANA = 4;
+
+// (kh + kl) + (rh + rl) for unnormalised double-float sums: a two-sum of
+// the hi parts whose rounding error joins the lo parts
+__device__ __forceinline__ void dd_add_unnorm(float &kh, float &kl, float rh, float rl) {
+  const float t = __fadd_rn(kh, rh);
+  const float bb = __fsub_rn(t, kh);
+  const float e = __fadd_rn(__fsub_rn(kh, __fsub_rn(t, bb)), __fsub_rn(rh, bb));
+  kh = t;
+  kl = __fadd_rn(__fadd_rn(kl, rl), e);
+}
+
+// Cross-lane sum of NV double-float values per lane (vh + vl): the
+// transpose-reduce of transpose_reduce<T, NV> in double-float; lane i holds
+// the total of value index i / (32 / NV).  FP32 pipe only: this part's FP64
+// pipe runs at ~1/64 of the FP32 rate.
+template <int NV>
+__device__ __forceinline__ dd transpose_reduce_dd(float (&vh)[NV], float (&vl)[NV], int lane) {
+  constexpr int R = 32 / NV;
+#pragma unroll
+  for (int s = 16; s >= R; s >>= 1) {
+    const int h = s / R;
+    const bool upper = (lane & s) != 0;
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      const float sh = upper ? vh[j] : vh[j + h];
+      const float sl = upper ? vl[j] : vl[j + h];
+      float kh = upper ? vh[j + h] : vh[j];
+      float kl = upper ? vl[j + h] : vl[j];
+      dd_add_unnorm(kh, kl, __shfl_xor_sync(0xffffffffu, sh, s),
+                    __shfl_xor_sync(0xffffffffu, sl, s));
+      vh[j] = kh;
+      vl[j] = kl;
+    }
+  }
+#pragma unroll
+  for (int s = R / 2; s >= 1; s >>= 1)
+    dd_add_unnorm(vh[0], vl[0], __shfl_xor_sync(0xffffffffu, vh[0], s),
+                  __shfl_xor_sync(0xffffffffu, vl[0], s));
+  return {vh[0], vl[0]};
+}
+
+// l values per chunk of the double-float analysis: its chunk body (LC l x
+// DD_NP_ANA ring pairs of double-float arithmetic, fully unrolled) must fit
+// the instruction cache (16 l: ~3500 instructions, stalled on instruction
+// fetch)
+constexpr int DD_LC_ANA = 8;
 
 
 // synthesis: as k_legendre_synth (one CTA row per m, one thread per
@@ -1172,9 +1227,9 @@ __global__ void __launch_bounds__(SYN_THREADS)
 }
 
 // analysis: queue-scheduled like k_legendre_anal_q; per (m, tile of 32
-// DD_NP_ANA ring pairs) item, per chunk of LCHUNK l the lane's df64 sums are
-// rounded to FP64 and reduced across the warp in FP64 (measured faster than
-// a double-float reduction)
+// DD_NP_ANA ring pairs) item, per chunk of DD_LC_ANA l the lane's df64 sums
+// are reduced across the warp in double-float (transpose_reduce_dd) and
+// rounded to FP64 once per output
 __global__ void __launch_bounds__(ANA_THREADS)
     k_legendre_anal_dd(const RingPair *__restrict__ pairs, int npairs, int lmax, long nalm,
                        const double *__restrict__ rc, const int *__restrict__ seed_l,
@@ -1235,23 +1290,24 @@ __global__ void __launch_bounds__(ANA_THREADS)
     }
     lmin = warp_min(lmin);
     linj = warp_max(linj);
-    const int lc0 = lmin <= L ? m + ((lmin - m) / LCHUNK) * LCHUNK : L + 1;
+    constexpr int LC = DD_LC_ANA;
+    const int lc0 = lmin <= L ? m + ((lmin - m) / LC) * LC : L + 1;
     if (lane == 0) lstart[(long)m * ntiles + tile] = lc0;
     if (lmin > L) continue;
     __syncwarp();
     for (int j = lane; j <= L - m; j += 32) sc[j] = dd_of(rc[base + j]);
     __syncwarp();
     double *out = scratch + 2 * ((long)tile * nalm + base - m);  // out[2 l + re/im]
-    for (int lc = lc0; lc <= L; lc += LCHUNK) {
-      double v[32];
+    for (int lc = lc0; lc <= L; lc += LC) {
+      float vh[2 * LC], vl[2 * LC];
       const bool inj = lc <= linj;
 #pragma unroll
-      for (int jj = 0; jj < LCHUNK; ++jj) {
+      for (int jj = 0; jj < LC; ++jj) {
         const int l = lc + jj;
         dd ar = zero, ai = zero;
         if (l <= L) {
           const dd c = sc[l - m];
-          const bool even = (jj & 1) == 0;  // lc - m is a multiple of LCHUNK
+          const bool even = (jj & 1) == 0;  // lc - m is a multiple of LC (even)
 #pragma unroll
           for (int j = 0; j < NP; ++j) {
             dd u = dd_rec(c, z[j], u1[j], u2[j]);
@@ -1265,12 +1321,16 @@ __global__ void __launch_bounds__(ANA_THREADS)
             dd_acc(ai, u, even ? pim[j] : qim[j]);
           }
         }
-        v[2 * jj] = dd_val(ar);
-        v[2 * jj + 1] = dd_val(ai);
+        vh[2 * jj] = ar.hi;
+        vl[2 * jj] = ar.lo;
+        vh[2 * jj + 1] = ai.hi;
+        vl[2 * jj + 1] = ai.lo;
       }
-      const double tot = transpose_reduce32<double>(v, lane);
-      const int l = lc + (lane >> 1);
-      if (l <= L) out[2 * l + (lane & 1)] = tot;
+      const dd tot = transpose_reduce_dd<2 * LC>(vh, vl, lane);
+      constexpr int R = 16 / LC;  // lanes holding each total
+      const int idx = lane / R;
+      const int l = lc + (idx >> 1);
+      if (lane % R == 0 && l <= L) out[2 * l + (idx & 1)] = dd_val(tot);
     }
   }
 }
