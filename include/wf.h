@@ -55,6 +55,15 @@ typedef enum {
 typedef enum { WF_PREC_FP64 = 0, WF_PREC_MIXED = 1 } wf_precision;
 
 typedef enum {
+  WF_METHOD_DUAL = 0,      /* the hybrid dual messenger (Algorithm 2) */
+  WF_METHOD_MESSENGER = 1  /* the standard messenger (Algorithm 1, Sect. 2.1):
+                              lambda cooling from lambda0 by beta (eta),
+                              untruncated signal step C / (C + lambda alpha
+                              Omega), tolerances in three steps (100 eps for
+                              lambda >= 100, 10 eps for lambda >= 10, eps) */
+} wf_method;
+
+typedef enum {
   WF_STOP_CAUCHY = 0, /* last stage ends when ||x_i - x_{i-1}|| / ||x_i|| < eps_final */
   WF_STOP_ERROR = 1   /* last stage ends when the geometric error estimate
                          c_i r / (1 - r) is < eps_final, with r the larger of
@@ -112,8 +121,10 @@ typedef struct {
                         ||delta|| > anchor_cap ||x_a|| (default 1e-2). */
   double anchor_cap_tol; /* > 0 tightens anchor_cap to anchor_cap_tol times
                         the stage's tolerance (default 100). */
-  int tail_exact;    /* with WF_STOP_CAUCHY: 1 = the tail stages (mu <=
-                        alpha, each with tolerance eps_final) iterate in the
+  int method;        /* wf_method (default WF_METHOD_DUAL) */
+  double lambda0;    /* WF_METHOD_MESSENGER: initial lambda (default 1e4) */
+  int tail_exact;    /* with WF_STOP_CAUCHY: 1 = the tail stages (those
+                        whose tolerance is eps_final) iterate in the
                         anchor arithmetic instead of FP32, so that their
                         Cauchy tests see FP64-accurate steps (default 1). */
 } wf_opts;

@@ -259,12 +259,14 @@ def fixed_point_residual(alm, nside, lmax, cl, noise_var, mask, d, transforms,
 
 # ---------------------------------------------------------------- PCG (App. C)
 def pcg_wf(nside, lmax, cl, noise_var, mask, d, tol=1e-12, max_iter=20000,
-           restart=200, transforms=None):
+           restart=200, transforms=None, stop="residual"):
     """Exact Wiener filter by conjugate gradients on App. C's system
     (1 + C^1/2 Y^T N^-1 Y C^1/2) z = C^1/2 Y^T N^-1 d, preconditioned by the
     harmonic diagonal M^-1 = 1 + C_l sum_p N^-1_p / (4 pi) (App. C's
     preconditioner on the sphere), restarted every ``restart`` iterations.
-    Stops when ||A z - y|| / ||y|| < tol.  Returns complex alm x = C^1/2 z."""
+    Stops when ||A z - y|| / ||y|| < tol (``stop`` = "residual"), or on App.
+    C's own criterion ||z_{i+1} - z_i|| / ||z_{i+1}|| < tol ("cauchy").
+    Returns complex alm x = C^1/2 z."""
     T = transforms if transforms is not None else make_transforms(nside, lmax)
     ls, _ = sht.lm_arrays(lmax)
     c = np.asarray(cl, dtype=np.float64)[ls]
@@ -281,7 +283,7 @@ def pcg_wf(nside, lmax, cl, noise_var, mask, d, tol=1e-12, max_iter=20000,
     pdiag = 1.0 + c * float(np.sum(ninv)) / (4.0 * np.pi)
     z = np.zeros_like(y)
     it = 0
-    rel = 1.0
+    rel = cauchy = 1.0
     while it < max_iter:
         r = y - A(z)
         p = r / pdiag
@@ -293,12 +295,13 @@ def pcg_wf(nside, lmax, cl, noise_var, mask, d, tol=1e-12, max_iter=20000,
             r = r - alpha_k * Ap
             it += 1
             rel = np.sqrt(dot(r, r)) / ny
-            if rel < tol or it >= max_iter:
+            cauchy = abs(alpha_k) * np.sqrt(dot(p, p)) / np.sqrt(dot(z, z))
+            if (cauchy if stop == "cauchy" else rel) < tol or it >= max_iter:
                 break
             q = r / pdiag
             rz_new = dot(r, q)
             p = q + (rz_new / rz) * p
             rz = rz_new
-        if rel < tol:
+        if (cauchy if stop == "cauchy" else rel) < tol:
             break
-    return sq * z, {"iterations": it, "rel_residual": rel}
+    return sq * z, {"iterations": it, "rel_residual": rel, "cauchy": cauchy}

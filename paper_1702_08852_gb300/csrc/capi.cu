@@ -116,6 +116,10 @@ static wf_status check_opts(const wf_opts &o) {
     return arg_error("wf: anchor_eps must be >= 0 and anchor_cap in (0, 1]");
   if (o.tail_exact != 0 && o.tail_exact != 1) return arg_error("wf: tail_exact must be 0 or 1");
   if (!(o.anchor_cap_tol >= 0.0)) return arg_error("wf: anchor_cap_tol must be >= 0");
+  if (o.method != WF_METHOD_DUAL && o.method != WF_METHOD_MESSENGER)
+    return arg_error("wf: unknown method");
+  if (o.method == WF_METHOD_MESSENGER && !(o.lambda0 >= 1.0 && o.lambda0 < 1e300))
+    return arg_error("wf: lambda0 must be >= 1");
   return WF_OK;
 }
 
@@ -143,6 +147,8 @@ void wf_opts_default(wf_opts *o) {
   o->anchor_cap = 1e-2;
   o->anchor_cap_tol = 100.0;
   o->tail_exact = 1;
+  o->method = WF_METHOD_DUAL;
+  o->lambda0 = 1e4;
 }
 
 long wf_npix(int nside) { return 12L * nside * nside; }

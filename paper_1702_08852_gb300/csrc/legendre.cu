@@ -702,7 +702,7 @@ __device__ __forceinline__ void
     if (st->done) return;
     L = st->lcur;
     xi = st->xi;
-    mu = st->mu;
+    mu = filter_mu(*st, st->mu);  // the signal step's truncation
     xa = st->xa;
   }
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -979,7 +979,7 @@ __global__ void __launch_bounds__(ANA_THREADS)
     if (st->done) return;
     L = st->lcur;
     xi = st->xi;
-    mu = st->mu;
+    mu = filter_mu(*st, st->mu);  // the signal step's truncation
     xa = st->xa;
   }
   if (m == 0 && threadIdx.x == 0) *counter = 0;

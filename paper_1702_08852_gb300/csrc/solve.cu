@@ -180,9 +180,7 @@ __global__ void __launch_bounds__(CTRL_THREADS)
       st->flat = 0;
       st->cmin = -1.0;
       st->since_min = 0;
-      st->eps_k = st->mu == 0.0
-                      ? st->eps_final
-                      : fmin(st->eps_cap, st->eps_final * fmax(1.0, st->mu / st->alpha));
+      st->eps_k = stage_tolerance(*st, st->mu);
       st->lcur = st->lnext;
     }
     if (adv && st->mu == 0.0 && st->handoff) {
@@ -205,7 +203,8 @@ __global__ void __launch_bounds__(CTRL_THREADS)
     // band of the stage after the new one
     const double xi2 = fmax(st->alpha, st->beta * st->xi);
     const double mu2 = xi2 > st->alpha ? xi2 - st->alpha : 0.0;
-    const int b = st->band_limit ? band_of(cl, lmax, mu2, st->omega, sh) : lmax;
+    const int b =
+        st->band_limit ? band_of(cl, lmax, filter_mu(*st, mu2), st->omega, sh) : lmax;
     if (threadIdx.x == 0) st->lnext = b;
   }
 }
@@ -365,13 +364,17 @@ SolverState initial_state(const Plan &P) {
   s.alpha = P.alpha;
   s.beta = o.beta;
   s.omega = P.omega;
-  const double mu0 = o.mu0 < 0.0 ? o.beta * cmax / P.omega : o.mu0;
+  s.messenger = o.method == WF_METHOD_MESSENGER;
+  // start: Algorithm 2, mu0 Omega = beta max C_l (or opts.mu0); Algorithm 1,
+  // xi = lambda0 alpha
+  const double mu0 = s.messenger ? (o.lambda0 - 1.0) * P.alpha
+                     : o.mu0 < 0.0 ? o.beta * cmax / P.omega
+                                   : o.mu0;
   s.mu = mu0;
   s.xi = P.alpha + mu0;
   s.eps_final = o.eps_final;
   s.eps_cap = o.eps_cap;
-  s.eps_k = mu0 == 0.0 ? o.eps_final
-                       : std::min(o.eps_cap, o.eps_final * std::max(1.0, mu0 / P.alpha));
+  s.eps_k = stage_tolerance(s, mu0);
   s.prev_c = -1.0;
   s.last_c = 0.0;
   s.err_est = 0.0;
@@ -401,10 +404,10 @@ SolverState initial_state(const Plan &P) {
   s.delta_cap2 = 0.0;
   s.last_den = 0.0;
   if (o.band_limit) {
-    s.lcur = band_host(P.cl, mu0, P.omega);
+    s.lcur = band_host(P.cl, filter_mu(s, mu0), P.omega);
     const double xi2 = std::max(P.alpha, o.beta * s.xi);
     const double mu2 = xi2 > P.alpha ? xi2 - P.alpha : 0.0;
-    s.lnext = band_host(P.cl, mu2, P.omega);
+    s.lnext = band_host(P.cl, filter_mu(s, mu2), P.omega);
   } else {
     s.lcur = s.lnext = P.lmax;
   }
@@ -650,7 +653,8 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
     else
       WF_TRY(launch_legendre_anal<double2>(P, P.G64, U, nullptr, ANA_PLAIN, Lb));
     ++P.nlaunch;
-    k_filter_from_u<<<P.lmax + 1, 128, 0, P.stream>>>(U, x, P.cl_d, xi, mu, P.omega, L,
+    k_filter_from_u<<<P.lmax + 1, 128, 0, P.stream>>>(U, x, P.cl_d, xi, filter_mu(s, mu),
+                                                      P.omega, L,
                                                       P.lmax, gx, P.partials);
     WF_CUDA(cudaGetLastError());
   } else if (dd) {
@@ -760,7 +764,8 @@ static wf_status boundary_step(Plan &P, SolverState &hio, int *total_iter) {
     WF_TRY(fp64_step(P, P.xacc, P.xtmp, &num, h.xi_prev, h.mu_prev, h.lcur_prev,
                      P.opts.anchor == 1, P.uacc[0], h.lcur));
     ++P.nlaunch;
-    k_filter_from_u<<<P.lmax + 1, 128, 0, P.stream>>>(P.uacc[0], P.xacc, P.cl_d, h.xi, h.mu,
+    k_filter_from_u<<<P.lmax + 1, 128, 0, P.stream>>>(P.uacc[0], P.xacc, P.cl_d, h.xi,
+                                                      filter_mu(h, h.mu),
                                                       P.omega, h.lcur, P.lmax, P.xtmp,
                                                       P.partials);
     WF_CUDA(cudaGetLastError());
@@ -800,12 +805,11 @@ static wf_status boundary_step(Plan &P, SolverState &hio, int *total_iter) {
     h.xi = std::max(P.alpha, h.beta * h.xi);
     h.mu = h.xi > P.alpha ? h.xi - P.alpha : 0.0;
     h.stage += 1;
-    h.eps_k = h.mu == 0.0 ? h.eps_final
-                          : std::min(h.eps_cap, h.eps_final * std::max(1.0, h.mu / P.alpha));
+    h.eps_k = stage_tolerance(h, h.mu);
     h.lcur = h.lnext;
     const double xi2 = std::max(P.alpha, h.beta * h.xi);
     const double mu2 = xi2 > P.alpha ? xi2 - P.alpha : 0.0;
-    h.lnext = P.opts.band_limit ? band_host(P.cl, mu2, P.omega) : P.lmax;
+    h.lnext = P.opts.band_limit ? band_host(P.cl, filter_mu(h, mu2), P.omega) : P.lmax;
   }
 }
 
@@ -853,12 +857,11 @@ static wf_status tail_stage(Plan &P, SolverState &hio, int *total_iter, bool *la
       h.xi = std::max(P.alpha, h.beta * h.xi);
       h.mu = h.xi > P.alpha ? h.xi - P.alpha : 0.0;
       h.stage += 1;
-      h.eps_k = h.mu == 0.0 ? h.eps_final
-                            : std::min(h.eps_cap, h.eps_final * std::max(1.0, h.mu / P.alpha));
+      h.eps_k = stage_tolerance(h, h.mu);
       h.lcur = h.lnext;
       const double xi2 = std::max(P.alpha, h.beta * h.xi);
       const double mu2 = xi2 > P.alpha ? xi2 - P.alpha : 0.0;
-      h.lnext = P.opts.band_limit ? band_host(P.cl, mu2, P.omega) : P.lmax;
+      h.lnext = P.opts.band_limit ? band_host(P.cl, filter_mu(h, mu2), P.omega) : P.lmax;
       break;
     }
   }
@@ -951,8 +954,9 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
         WF_TRY(boundary_step(P, h, &total_iter));
         boundary = false;
       }
-      if (P.opts.tail_exact && h.mu <= P.alpha && P.opts.stop_rule == WF_STOP_CAUCHY) {
-        // the tail stages (mu <= alpha: each one's tolerance is eps_final)
+      if (P.opts.tail_exact && h.eps_k <= P.opts.eps_final &&
+          P.opts.stop_rule == WF_STOP_CAUCHY) {
+        // the tail stages (each one's tolerance is eps_final)
         // iterate in the anchor arithmetic, so that their Cauchy tests see
         // the step to FP64 accuracy
         bool last_done = false;
@@ -985,7 +989,8 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       WF_TRY(alm_dot(P, P.xacc, P.xacc, nullptr, &xn));
       ++P.nlaunch;
       k_make_source<<<P.lmax + 1, 128, 0, P.stream>>>(P.xtmp, P.xacc, P.cl_d, stage.xi,
-                                                      stage.mu, P.omega, P.lmax, P.src);
+                                                      filter_mu(stage, stage.mu), P.omega,
+                                                      P.lmax, P.src);
       WF_CUDA(cudaGetLastError());
       WF_CUDA(cudaMemsetAsync(P.x, 0, sizeof(double2) * P.nalm, P.stream));
       SolverState s = initial_state(P);

@@ -98,7 +98,28 @@ struct SolverState {
   // the stage before the last advance (its xi, mu and band)
   double xi_prev, mu_prev;
   int lcur_prev;
+  int messenger;  // 1: the standard messenger (Algorithm 1), xi = lambda alpha
 };
+
+// Tolerance of the stage at mu (pixel units): Algorithm 2 relaxes it as
+// min(eps_cap, eps_final max(1, mu / alpha)); Algorithm 1 in three steps of
+// lambda = xi / alpha = 1 + mu / alpha (100 eps from lambda 100, 10 eps from
+// lambda 10, eps below).  Both end on eps_final.
+__host__ __device__ inline double stage_tolerance(const SolverState &s, double mu) {
+  if (s.messenger) {
+    const double lam = 1.0 + mu / s.alpha;
+    if (lam >= 100.0) return fmin(s.eps_cap, 100.0 * s.eps_final);
+    if (lam >= 10.0) return fmin(s.eps_cap, 10.0 * s.eps_final);
+    return s.eps_final;
+  }
+  return mu == 0.0 ? s.eps_final : fmin(s.eps_cap, s.eps_final * fmax(1.0, mu / s.alpha));
+}
+
+// mu of the signal step's truncation Sbar = max(C - mu Omega, 0): Algorithm 2
+// truncates at the stage's mu; Algorithm 1 does not (Sbar = C)
+__host__ __device__ inline double filter_mu(const SolverState &s, double mu) {
+  return s.messenger ? 0.0 : mu;
+}
 
 struct TraceEntry {
   int stage, lcur;   // stage index and band limit of the iteration

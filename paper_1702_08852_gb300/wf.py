@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libwf.so")
 WF_OK, WF_ERR_ARG, WF_ERR_CUDA, WF_ERR_NOT_CONVERGED = 0, 1, 2, 3
 WF_ERR_NUMERIC, WF_ERR_TIMEOUT, WF_ERR_UNIMPLEMENTED, WF_ERR_STATE = 4, 5, 6, 7
 WF_PREC_FP64, WF_PREC_MIXED = 0, 1
+WF_METHOD_DUAL, WF_METHOD_MESSENGER = 0, 1
 WF_STOP_CAUCHY, WF_STOP_ERROR = 0, 1
 
 
@@ -37,7 +38,8 @@ class wf_opts(ctypes.Structure):
                 ("graph_chunk", ctypes.c_int), ("refine_max", ctypes.c_int),
                 ("timing", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("anchor", ctypes.c_int), ("anchor_eps", ctypes.c_double),
-                ("anchor_cap", ctypes.c_double), ("anchor_cap_tol", ctypes.c_double), ("tail_exact", ctypes.c_int)]
+                ("anchor_cap", ctypes.c_double), ("anchor_cap_tol", ctypes.c_double), ("method", ctypes.c_int),
+                ("lambda0", ctypes.c_double), ("tail_exact", ctypes.c_int)]
 
 
 class wf_stats(ctypes.Structure):

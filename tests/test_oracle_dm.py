@@ -183,3 +183,19 @@ def test_error_stop_rule_meets_its_tolerance(osht, odm):
                                   eps_final=tol, stop="error", transforms=T)
         err = np.linalg.norm(T.synth(x) - sd) / np.linalg.norm(sd)
         assert err < 3 * tol
+
+
+def test_pcg_cauchy_rule_of_app_c(osht, odm):
+    """App. C's stop rule ||z_{i+1} - z_i|| / ||z_{i+1}|| < eps: the step norm
+    it tests is |alpha| ||p|| (z_{i+1} = z_i + alpha p), and the solve it ends
+    is within the rule's reach of the exact Wiener filter."""
+    p, d = make(osht, "lognormal", 4, seed=19)
+    xa = odm.wf_exact_dense(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d)
+    x6, i6 = odm.pcg_wf(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d, tol=1e-6,
+                        stop="cauchy")
+    assert i6["cauchy"] < 1e-6
+    x12, i12 = odm.pcg_wf(p.nside, p.lmax, p.cl, p.noise_var, p.mask, d, tol=1e-12,
+                          stop="cauchy")
+    assert i12["iterations"] > i6["iterations"]
+    assert rel(osht, x12, xa, p.lmax) < 1e-9
+    assert rel(osht, x6, xa, p.lmax) < 1e-3
