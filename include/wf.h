@@ -196,6 +196,32 @@ wf_status wf_solve_batch(wf_plan_t *plans, int n, const double *const *d_dev,
                          double *const *alm_dev, double *const *map_dev, wf_stats *stats,
                          double *elapsed_ms);
 
+/* Stop rules of wf_pcg. */
+typedef enum {
+  WF_PCG_STOP_CAUCHY = 0,   /* ||z_{i+1} - z_i|| / ||z_{i+1}|| < tol (App. C) */
+  WF_PCG_STOP_RESIDUAL = 1  /* ||A z - y|| / ||y|| < tol (the residual of Fig. 5) */
+} wf_pcg_stop;
+
+/* The Wiener filter by preconditioned conjugate gradients, the paper's
+ * comparison method (App. C): A z = y with A = 1 + C^1/2 Y^T N^-1 Y C^1/2,
+ * y = C^1/2 Y^T N^-1 d, s_WF = C^1/2 z, preconditioned by the harmonic
+ * diagonal 1 + C_l sum_p N^-1_p / (4 pi), restarted every `restart`
+ * iterations (the paper: 200), FP64 transforms.  Unlike wf_solve, its fixed
+ * point is Eq. (2) itself (no messenger, so no quadrature gap).
+ *  d_dev      device double[Npix] data map (masked pixels ignored).
+ *  alm_dev    device double[2 Nalm] output s_WF coefficients, or NULL.
+ *  map_dev    device double[Npix] output s_WF = Y alm, or NULL.
+ *  tol        tolerance of the stop rule; stop_rule: wf_pcg_stop.
+ *  max_iter, restart  >= 1.
+ *  stats      optional: iterations, converged, final_cauchy (the last
+ *             step's Cauchy ratio), err_estimate = fp_residual (the last
+ *             relative residual), elapsed_ms, kernel_launches.
+ * Allocates its work vectors (8 alm-sized) for the call.  Returns WF_OK,
+ * WF_ERR_NOT_CONVERGED (outputs hold the last iterate), WF_ERR_STATE for a
+ * plan without noise, WF_ERR_NUMERIC, WF_ERR_ARG. */
+wf_status wf_pcg(wf_plan_t plan, const double *d_dev, double *alm_dev, double *map_dev,
+                 double tol, int stop_rule, int max_iter, int restart, wf_stats *stats);
+
 /* Same as wf_solve with host buffers: copies d in, solves, copies the
  * requested outputs back (both copies are part of the call). */
 wf_status wf_solve_host(wf_plan_t plan, const double *d_host, double *alm_host,

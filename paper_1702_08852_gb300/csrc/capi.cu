@@ -308,6 +308,17 @@ wf_status wf_residual(wf_plan_t plan, const double *d_dev, const double *alm_dev
   return residual(*plan, d_dev, alm_dev, rel_res_wf, rel_res_fp, chi2);
 }
 
+wf_status wf_pcg(wf_plan_t plan, const double *d_dev, double *alm_dev, double *map_dev,
+                 double tol, int stop_rule, int max_iter, int restart, wf_stats *stats) {
+  if (!plan) return arg_error("wf_pcg: plan is NULL");
+  if (!d_dev) return arg_error("wf_pcg: d_dev is NULL");
+  if (!(tol > 0.0)) return arg_error("wf_pcg: tol must be > 0");
+  if (stop_rule != WF_PCG_STOP_CAUCHY && stop_rule != WF_PCG_STOP_RESIDUAL)
+    return arg_error("wf_pcg: unknown stop_rule");
+  if (max_iter < 1 || restart < 1) return arg_error("wf_pcg: max_iter and restart must be >= 1");
+  return pcg(*plan, d_dev, alm_dev, map_dev, tol, stop_rule, max_iter, restart, stats);
+}
+
 wf_status wf_solve_batch(wf_plan_t *plans, int n, const double *const *d_dev,
                          double *const *alm_dev, double *const *map_dev, wf_stats *stats,
                          double *elapsed_ms) {

@@ -296,6 +296,10 @@ static wf_status alm_dot(Plan &P, const double2 *a, const double2 *b,
   return host_sum(P, P.red, RED_BLOCKS, res);
 }
 
+wf_status alm_dot_host(Plan &P, const double2 *a, const double2 *b, double *res) {
+  return alm_dot(P, a, b, nullptr, res);
+}
+
 // ---------------------------------------------------------------- transforms
 wf_status alm2map(Plan &P, const double *alm, double *map) {
   const double2 *a = reinterpret_cast<const double2 *>(alm);

@@ -321,6 +321,12 @@ wf_status legendre_terms(Plan &P, int L, double *terms);
 SolverState initial_state(const Plan &P);
 wf_status residual_static(Plan &P, const double *d, const double *alm, double *res_wf,
                           double *res_fp, double *chi2);
+// real-basis inner product of two alm (fixed-order reduction, host result)
+wf_status alm_dot_host(Plan &P, const double2 *a, const double2 *b, double *res);
+
+// pcg.cu
+wf_status pcg(Plan &P, const double *d, double *alm, double *map, double tol, int stop_rule,
+              int max_iter, int restart, wf_stats *stats);
 
 // helper kernels of solve.cu shared with noalloc.cu
 __global__ void k_mask_data(const double *d, const double *nvar, long npix, double *out);

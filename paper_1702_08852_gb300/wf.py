@@ -21,6 +21,7 @@ WF_OK, WF_ERR_ARG, WF_ERR_CUDA, WF_ERR_NOT_CONVERGED = 0, 1, 2, 3
 WF_ERR_NUMERIC, WF_ERR_TIMEOUT, WF_ERR_UNIMPLEMENTED, WF_ERR_STATE = 4, 5, 6, 7
 WF_PREC_FP64, WF_PREC_MIXED = 0, 1
 WF_METHOD_DUAL, WF_METHOD_MESSENGER = 0, 1
+WF_PCG_STOP_CAUCHY, WF_PCG_STOP_RESIDUAL = 0, 1
 WF_STOP_CAUCHY, WF_STOP_ERROR = 0, 1
 
 
@@ -101,6 +102,7 @@ def lib():
             "wf_kernel_stats": (I, [_P, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long),
                                     ctypes.POINTER(D), I]),
             "wf_legendre_terms": (I, [_P, I, ctypes.POINTER(D)]),
+            "wf_pcg": (I, [_P, _P, _P, _P, D, I, I, I, ctypes.POINTER(wf_stats)]),
             "wf_alu_peak": (I, [I, I, ctypes.POINTER(D), ctypes.POINTER(D),
                                 ctypes.POINTER(I)]),
             "wf_get_tuning": (I, [_P, ctypes.POINTER(_Tuning)]),
@@ -239,6 +241,24 @@ class Plan:
         if check and status not in (WF_OK,):
             _check(status)
         return alm, map, st.as_dict() | {"status": status}
+
+    def pcg(self, d, tol=1e-6, stop_rule=WF_PCG_STOP_CAUCHY, max_iter=20000, restart=200,
+            want_alm=True, want_map=True):
+        """wf_pcg: the Wiener filter by preconditioned conjugate gradients
+        (App. C).  Returns (alm or None, map or None, stats dict)."""
+        import torch
+        dev = d.device
+        alm = torch.empty(self.nalm, dtype=torch.complex128, device=dev) if want_alm else None
+        mp = torch.empty(self.npix, dtype=torch.float64, device=dev) if want_map else None
+        st = wf_stats()
+        status = lib().wf_pcg(self.handle, _dev_ptr(d, torch.float64, self.npix, "d"),
+                              _dev_ptr(alm, torch.complex128, self.nalm, "alm"),
+                              _dev_ptr(mp, torch.float64, self.npix, "map"),
+                              float(tol), int(stop_rule), int(max_iter), int(restart),
+                              ctypes.byref(st))
+        if status not in (WF_OK, WF_ERR_NOT_CONVERGED):
+            _check(status)
+        return alm, mp, st.as_dict() | {"status": status}
 
     def solve_host(self, d_host, want_alm=True, want_map=True):
         d = np.ascontiguousarray(d_host, dtype=np.float64)
