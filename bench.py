@@ -273,7 +273,7 @@ def run_ours(args, rank, world):
     # plain FP64 dual messenger on the same map (rank 0): the comparison the
     # speedup is quoted against, and the mixed result's distance from it;
     # beside it the mixed solver's fast configuration on the same map
-    fp64, fast, cfg2 = {}, {}, {}
+    fp64, fast, cfg2, methods = {}, {}, {}, {}
     if rank == 0 and not args.no_fp64:
         p64 = wf.Plan(p.nside, p.lmax, p.cl, nv, mk, precision=wf.WF_PREC_FP64,
                       eps_final=args.eps, timing=1, autotune=1)
@@ -297,6 +297,7 @@ def run_ours(args, rank, world):
         p64.close()
         fast = fast_mode(wf, p, nv, mk, d, m64, s64, args)
         cfg2 = config2(wf, args)
+        methods = methods_comparison(wf, args)
     plan.close()
     if dist:
         dist.barrier()
@@ -352,6 +353,7 @@ def run_ours(args, rank, world):
         "plain_fp64": fp64,
         "fast_mode": fast,
         "nside256": cfg2,
+        "methods_nside256": methods,
         "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "source": peak_src, "alu": alu},
     }
     out["gpu_launches"] = int(sum(s["kernel_launches"] for s in stats))
@@ -408,6 +410,34 @@ def config2(wf, args, reps=3):
                 "mixed_vs_fp64_rel_l2": float(torch.linalg.norm(mm - m64) /
                                               torch.linalg.norm(m64)),
                 "speedup_mixed_over_fp64": (s64["elapsed_ms"] / 1e3) / t})
+    return out
+
+
+def methods_comparison(wf, args):
+    """The paper's three-way comparison (Sect. 4) on the Nside 256 scan
+    workload, each method to its own Cauchy criterion eps (FP64 transforms):
+    the dual messenger (Algorithm 2), the standard messenger (Algorithm 1,
+    lambda from 1e4 by 3/4, three-step tolerances) and PCG with the
+    harmonic-diagonal preconditioner (App. C, restart 200); iterations, time
+    and the App. C residual of each result."""
+    p, nv, mk, d = make_workload(256, seed=3100)
+    out = {"workload": "Nside 256 lmax 512 scan-noise 25% mask, FP64 transforms"}
+    for name, kw in (("dual_messenger", {}),
+                     ("standard_messenger", {"method": wf.WF_METHOD_MESSENGER})):
+        pl = wf.Plan(p.nside, p.lmax, p.cl, nv, mk, precision=wf.WF_PREC_FP64,
+                     eps_final=args.eps, autotune=1, **kw)
+        alm, _, st = pl.solve(d, want_map=False)
+        res = pl.residual(d, alm)
+        out[name] = {"solve_s": st["elapsed_ms"] / 1e3, "iterations": st["iterations"],
+                     "stages": st["stages"], "rel_res_wf": res["rel_res_wf"]}
+        pl.close()
+    pl = wf.Plan(p.nside, p.lmax, p.cl, nv, mk, autotune=1)
+    alm, _, st = pl.pcg(d, tol=args.eps, stop_rule=wf.WF_PCG_STOP_CAUCHY, restart=200,
+                        want_map=False)
+    res = pl.residual(d, alm)
+    out["pcg"] = {"solve_s": st["elapsed_ms"] / 1e3, "iterations": st["iterations"],
+                  "converged": st["converged"], "rel_res_wf": res["rel_res_wf"]}
+    pl.close()
     return out
 
 
