@@ -397,6 +397,36 @@ wf_status wf_net_loss_grad(wf_net_t net, const double *d_dev,
 wf_status wf_net_adam_step(wf_net_t net, float lr, float beta1, float beta2, float eps);
 void wf_net_destroy(wf_net_t net);
 
+/* ---- the flat sky (the paper's own Sect. 3 set-up)
+ * Algorithm 2 on an n x n periodic grid with 2-D FFTs, FP64: the basis
+ * change is orthogonal, so the last stage's fixed point is the Wiener filter
+ * of Eq. (2) itself.  With the DFT in numpy's convention one iteration is
+ * s = ifft2(f_k fft2(t)), f_k = Sbar_k / (Sbar_k + xi Omega_pix),
+ * Sbar_k = max(C_k - mu Omega_pix, 0), then t = s + xi / (sigma^2 + mu)
+ * (d - s); cooling, start, tolerances and stop rules as wf_solve's.
+ *  n              grid side, a power of two, 8 <= n <= 2048.
+ *  pixel_area     Omega_pix = (L / n)^2 (sr): a pixel variance v has the
+ *                 power v Omega_pix of the signal power C_k.
+ *  ck_host        host double[n * n]: C at each DFT mode (row ky, column
+ *                 kx, DFT frequency order), >= 0; copied.
+ *  noise_var_dev  device double[n * n] sigma^2 > 0 per pixel (+inf masks a
+ *                 pixel); copied.
+ *  opts           NULL = defaults; beta, eps_final, eps_cap, mu0 (< 0:
+ *                 mu0 Omega_pix = beta max C_k), max_iter, stop_rule,
+ *                 graph_chunk are used.
+ * Errors: WF_ERR_ARG for a bad size, spectrum, noise or option. */
+typedef struct wf_flat_s *wf_flat_t;
+wf_status wf_flat_plan(wf_flat_t *out, int n, double pixel_area, const double *ck_host,
+                       const double *noise_var_dev, const wf_opts *opts, void *stream);
+/* d_dev: device double[n * n] data; s_dev: device double[n * n] output s_WF.
+ * Returns WF_OK, WF_ERR_NOT_CONVERGED (s_dev holds the last iterate) or an
+ * error; stats as wf_solve's. */
+wf_status wf_flat_solve(wf_flat_t plan, const double *d_dev, double *s_dev, wf_stats *stats);
+/* Stage index and Cauchy ratio of each iteration of the last solve (host
+ * arrays of length >= *count; *count in: capacity, out: entries). */
+wf_status wf_flat_trace(wf_flat_t plan, int *count, int *stage, double *cauchy);
+void wf_flat_destroy(wf_flat_t plan);
+
 void wf_destroy(wf_plan_t plan);
 const char *wf_status_str(wf_status s);
 const char *wf_last_error(void);

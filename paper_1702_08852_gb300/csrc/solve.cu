@@ -56,7 +56,7 @@ __device__ int band_of(const double *cl, int lmax, double mu, double omega,
   return r;
 }
 
-constexpr int CTRL_THREADS = 256;
+constexpr int CTRL_THREADS = CONTROL_THREADS;
 constexpr int PLATEAU_ITERS = 256;
 
 // mixed precision: bound on the re-anchorings of one solve

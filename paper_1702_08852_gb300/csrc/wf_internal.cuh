@@ -328,6 +328,15 @@ wf_status alm_dot_host(Plan &P, const double2 *a, const double2 *b, double *res)
 wf_status pcg(Plan &P, const double *d, double *alm, double *map, double tol, int stop_rule,
               int max_iter, int restart, wf_stats *stats);
 
+// the stage-control kernel of solve.cu (launch with CONTROL_THREADS threads):
+// Cauchy ratio from the per-slot partial sums partials[2 j], [2 j + 1],
+// j <= nslots - 1 (passed as lmax), stage test, cooling, trace; cl may be
+// NULL when the state's band_limit is 0
+constexpr int CONTROL_THREADS = 256;
+__global__ void __launch_bounds__(CONTROL_THREADS)
+    k_control(SolverState *st, const double *__restrict__ partials, int lmax,
+              const double *__restrict__ cl, TraceEntry *trace);
+
 // helper kernels of solve.cu shared with noalloc.cu
 __global__ void k_mask_data(const double *d, const double *nvar, long npix, double *out);
 __global__ void k_alm_dot(const double2 *a, const double2 *b, const double *fl, int lmax,

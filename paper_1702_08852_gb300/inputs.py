@@ -265,3 +265,45 @@ def batch_problems(count=64, seed_base=3000, nsides=(64, 128, 256)):
 
 def random_map(nside, seed):
     return np.random.default_rng(seed).standard_normal(npix(nside))
+
+
+# ---------------------------------------------------------------- flat sky
+# The paper's Sect. 3 workload: an n x n periodic grid of side L = 10 deg,
+# white noise of 64 muK^2 with a central 5 deg square at 10^6 times that;
+# an analytic spectrum stands in for CAMB.
+
+def flat_mode_ell(n, side):
+    """|l| = 2 pi |k| / L of every DFT mode (numpy fft2 order)."""
+    k = np.fft.fftfreq(n, d=1.0 / n)
+    kx, ky = np.meshgrid(k, k)
+    return 2.0 * np.pi * np.hypot(kx, ky) / side
+
+
+def flat_cl(ell, amplitude=5000.0, ell_damp=1500.0):
+    """Analytic stand-in for the paper's CAMB spectrum (muK^2 sr):
+    C_l = 2 pi A / (l (l + 1)) exp(-(l / l_d)^2), A the plateau of
+    l (l + 1) C_l / 2 pi; C_0 = 0 (no monopole)."""
+    ell = np.asarray(ell, dtype=np.float64)
+    c = np.zeros_like(ell)
+    pos = ell > 0
+    e = ell[pos]
+    c[pos] = 2.0 * np.pi * amplitude / (e * (e + 1.0)) * np.exp(-(e / ell_damp) ** 2)
+    return c
+
+
+def flat_paper_noise(n, side_deg=10.0, mask_deg=5.0, var=64.0, mask_factor=1e6):
+    """White noise of variance 64 muK^2, a central square of side 5 deg
+    with 10^6 times that (the Sect. 3 workload)."""
+    x = (np.arange(n) + 0.5) * side_deg / n - side_deg / 2.0
+    inside = np.abs(x) < mask_deg / 2.0
+    m = inside[:, None] & inside[None, :]
+    return np.where(m, var * mask_factor, var), m
+
+
+def flat_gaussian_field(rng, ck, pixel_area):
+    """A real Gaussian field whose DFT modes have power C_k / Omega_pix per
+    unit white variance (the filter's units): s = ifft2(sqrt(C_k / Omega) *
+    fft2(white)), white ~ N(0, 1) per pixel."""
+    n = ck.shape[0]
+    w = rng.standard_normal((n, n))
+    return np.real(np.fft.ifft2(np.sqrt(ck / pixel_area) * np.fft.fft2(w)))

@@ -103,6 +103,10 @@ def lib():
                                     ctypes.POINTER(D), I]),
             "wf_legendre_terms": (I, [_P, I, ctypes.POINTER(D)]),
             "wf_pcg": (I, [_P, _P, _P, _P, D, I, I, I, ctypes.POINTER(wf_stats)]),
+            "wf_flat_plan": (I, [ctypes.POINTER(_P), I, D, _P, _P, ctypes.POINTER(wf_opts), _P]),
+            "wf_flat_solve": (I, [_P, _P, _P, ctypes.POINTER(wf_stats)]),
+            "wf_flat_trace": (I, [_P, ctypes.POINTER(I), _P, _P]),
+            "wf_flat_destroy": (None, [_P]),
             "wf_alu_peak": (I, [I, I, ctypes.POINTER(D), ctypes.POINTER(D),
                                 ctypes.POINTER(I)]),
             "wf_get_tuning": (I, [_P, ctypes.POINTER(_Tuning)]),
@@ -564,6 +568,66 @@ def wf_trace(plan):
 
 def wf_kernel_stats(plan, kernel=0, reset=False):
     return plan.kernel_stats(kernel, reset)
+
+
+class FlatPlan:
+    """Algorithm 2 on the flat sky (wf_flat_plan / wf_flat_solve): an n x n
+    periodic grid with 2-D FFTs.  ck: host array (n, n) of C at each DFT
+    mode (numpy fft2 order); noise_var: CUDA float64 tensor (n, n) or n*n."""
+
+    def __init__(self, n, pixel_area, ck, noise_var, stream=None, **opt_overrides):
+        import torch
+        self.n = int(n)
+        self.opts = wf_opts_default(**opt_overrides)
+        ck = np.ascontiguousarray(np.asarray(ck, dtype=np.float64).reshape(-1))
+        if ck.size != self.n * self.n:
+            raise ValueError("ck: expected n*n values")
+        h = _P()
+        _check(lib().wf_flat_plan(ctypes.byref(h), self.n, float(pixel_area),
+                                  ck.ctypes.data_as(ctypes.c_void_p),
+                                  _dev_ptr(noise_var.reshape(-1), torch.float64,
+                                           self.n * self.n, "noise_var"),
+                                  ctypes.byref(self.opts), _stream(stream)))
+        self.handle = h
+
+    def solve(self, d, out=None, check=True):
+        import torch
+        n2 = self.n * self.n
+        if out is None:
+            out = torch.empty(n2, dtype=torch.float64, device=d.device)
+        st = wf_stats()
+        status = lib().wf_flat_solve(self.handle,
+                                     _dev_ptr(d.reshape(-1), torch.float64, n2, "d"),
+                                     _dev_ptr(out.reshape(-1), torch.float64, n2, "s"),
+                                     ctypes.byref(st))
+        if check and status != WF_OK:
+            _check(status)
+        return out.reshape(self.n, self.n), st.as_dict() | {"status": status}
+
+    def trace(self, cap=1 << 20):
+        n = ctypes.c_int(cap)
+        st, c = np.empty(cap, dtype=np.int32), np.empty(cap)
+        _check(lib().wf_flat_trace(self.handle, ctypes.byref(n),
+                                   st.ctypes.data_as(ctypes.c_void_p),
+                                   c.ctypes.data_as(ctypes.c_void_p)))
+        return {"stage": st[:n.value], "cauchy": c[:n.value]}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().wf_flat_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def wf_alu_peak(kind, reps=5):

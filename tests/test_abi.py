@@ -145,3 +145,17 @@ def test_alu_peak_rejects_bad_arguments_before_cuda(wflib):
     assert L.wf_alu_peak(3, 1, C.byref(t), None, None) == wflib.WF_ERR_ARG
     assert L.wf_alu_peak(1, 0, C.byref(t), None, None) == wflib.WF_ERR_ARG
     assert L.wf_alu_peak(1, 1, None, None, None) == wflib.WF_ERR_ARG
+
+
+def test_flat_plan_rejects_bad_sizes_before_cuda(wflib):
+    import ctypes as C
+    L = wflib.lib()
+    h = C.c_void_p()
+    ck = np.ones(100)
+    dummy = C.c_void_p(8)  # never dereferenced: the size check comes first
+    assert L.wf_flat_plan(C.byref(h), 10, 1e-6, ck.ctypes.data_as(C.c_void_p), dummy,
+                          None, None) == wflib.WF_ERR_ARG
+    assert L.wf_flat_plan(C.byref(h), 4096, 1e-6, ck.ctypes.data_as(C.c_void_p), dummy,
+                          None, None) == wflib.WF_ERR_ARG
+    assert L.wf_flat_plan(C.byref(h), 8, 0.0, ck.ctypes.data_as(C.c_void_p), dummy,
+                          None, None) == wflib.WF_ERR_ARG

@@ -5,6 +5,8 @@ itself, against a dense solve and a conjugate-gradient solve."""
 import numpy as np
 import pytest
 
+from paper_1702_08852_gb300 import inputs
+
 
 @pytest.fixture(scope="module")
 def ofs():
@@ -15,13 +17,13 @@ def ofs():
 def setup(ofs, n, seed, uniform=False):
     side = np.deg2rad(10.0) * n / 512 * 8 if n < 64 else np.deg2rad(10.0)
     om = (side / n) ** 2
-    ck = ofs.cl_flat(ofs.mode_ell(n, side))
+    ck = inputs.flat_cl(inputs.flat_mode_ell(n, side))
     rng = np.random.default_rng(seed)
     if uniform:
         nv, _ = np.full((n, n), 64.0), None
     else:
-        nv, _ = ofs.paper_noise(n, side_deg=np.rad2deg(side), mask_deg=np.rad2deg(side) / 2)
-    s = ofs.gaussian_field(rng, ck, om)
+        nv, _ = inputs.flat_paper_noise(n, side_deg=np.rad2deg(side), mask_deg=np.rad2deg(side) / 2)
+    s = inputs.flat_gaussian_field(rng, ck, om)
     d = s + np.sqrt(nv) * rng.standard_normal((n, n))
     return d, nv, ck, om
 
@@ -56,9 +58,9 @@ def test_cg_matches_dense(ofs):
 def test_paper_workload_shapes(ofs):
     """512^2, L = 10 deg, 64 muK^2, central 5 deg square at 10^6 N: a quarter
     of the map masked; l of the fundamental mode 2 pi / L."""
-    nv, m = ofs.paper_noise(512)
+    nv, m = inputs.flat_paper_noise(512)
     assert m.mean() == pytest.approx(0.25, abs=0.01)
     assert nv.min() == 64.0 and nv.max() == 64.0e6
-    ell = ofs.mode_ell(512, np.deg2rad(10.0))
+    ell = inputs.flat_mode_ell(512, np.deg2rad(10.0))
     assert ell[0, 1] == pytest.approx(2 * np.pi / np.deg2rad(10.0))
-    assert ofs.cl_flat(ell)[0, 0] == 0.0
+    assert inputs.flat_cl(ell)[0, 0] == 0.0
