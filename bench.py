@@ -168,6 +168,57 @@ def alu_peaks(wf):
             "source": "measured live: wf_alu_peak FMA chains on every SM, best of 5"}
 
 
+# FP32 flops of the double-float formulas per (l, m, ring pair) term: the
+# recurrence step (product c u, product by z, difference: 28 with an FMA
+# counted as 2) and two accumulations of a product (15 each)
+DD_FLOPS_PER_TERM = 58.0
+KERNEL_NAMES = ["legendre_analysis_f32", "legendre_synthesis_f32", "ring_step_f32",
+                "legendre_synthesis_dd", "legendre_analysis_dd", "ring_step_f64"]
+
+
+def kernel_rooflines(kern, alu, peaks, peak_src, args, ana_variant):
+    """Per-kernel rooflines of the timed solves (wf_kernel_stats, CUDA events
+    around every launch) and the dominant kernel's at the top level.
+    Legendre kernels: 7 algorithmic flops per term against the measured FP32
+    FMA peak (the double-float ones: the 58 FP32 flops of their formulas per
+    term against the same peak, and their FP64-equivalent 7 flops per term
+    beside the measured FP64 peak); ring steps: DRAM bytes they cannot avoid
+    against the measured copy bandwidth."""
+    total = sum(k["ms"] for k in kern) or 1.0
+    rows = []
+    for i, (k, name) in enumerate(zip(kern, KERNEL_NAMES)):
+        if not k["ms"]:
+            continue
+        ms = k["ms"] / max(1, k["launches"])
+        if i in (2, 5):
+            r = ring_roofline(k, peaks, peak_src)
+        else:
+            g = k["gflop"] * (DD_FLOPS_PER_TERM / 7.0 if i in (3, 4) else 1.0)
+            ach = g / (k["ms"] / 1e3) / 1e3
+            r = {"bound": "alu", "achieved": ach, "peak": alu["fp32_tflops"],
+                 "unit": "TFLOP/s", "frac": ach / alu["fp32_tflops"],
+                 "peak_source": alu["source"] + f" ({alu['num_sms']} SMs), FP32 FMA pipe",
+                 "avg_launch_ms": ms}
+            if i in (3, 4):
+                e = k["gflop"] / (k["ms"] / 1e3) / 1e3
+                r["flops_per_term"] = DD_FLOPS_PER_TERM
+                r["fp64_equivalent"] = {"achieved": e, "fp64_peak": alu["fp64_tflops"],
+                                        "ratio": e / alu["fp64_tflops"]}
+        r.update({"kernel": name, "launches": k["launches"], "time_share": k["ms"] / total})
+        rows.append(r)
+    top = dict(max(rows, key=lambda r: r["time_share"])) if rows else {}
+    if top.get("kernel") == "legendre_analysis_f32":
+        top["traffic"] = analysis_traffic(args.nside, kern[0]["gflop"], kern[0]["launches"],
+                                          ana_variant)
+        top["traffic_source"] = ANALYSIS_DRAM_FULL_BAND["source"]
+        top["variant"] = ana_variant
+    else:
+        top.setdefault("traffic", None)
+        top["traffic_source"] = "see profiles/ (one-kernel ncu captures)"
+    top["kernels"] = rows
+    return top
+
+
 def ring_roofline(k, peaks, peak_src):
     """HBM roofline of the ring step (fold, ring FFTs, t-update): algorithmic
     bytes (ring coefficients in and out, d and sigma^2) per timed launch pair
@@ -237,7 +288,7 @@ def run_ours(args, rank, world):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     for _ in range(args.warmup):
         alm, mp, st = plan.solve(d)
-    for k in (0, 1, 2):
+    for k in range(6):
         plan.kernel_stats(k, reset=True)
     torch.cuda.synchronize()
     if dist:
@@ -257,7 +308,7 @@ def run_ours(args, rank, world):
         stats.append(st)
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(step_ms), dist, dev)
-    kern = [plan.kernel_stats(k) for k in (0, 1, 2)]
+    kern = [plan.kernel_stats(k) for k in range(6)]
     ana_variant = analysis_variant(plan.tuning())
     ms_step_mean = sum(step_ms) / len(step_ms)
 
@@ -309,9 +360,6 @@ def run_ours(args, rank, world):
     ms_per_step = total_ms / args.steps
     value = aggregate_value(world, args.steps, total_ms)
     peaks, peak_src = measured_peaks()
-    peak32 = alu["fp32_tflops"]
-    k0 = kern[0]
-    achieved = (k0["gflop"] / (k0["ms"] / 1e3) / 1e3) if k0["ms"] > 0 else None
     iters = [s["iterations"] for s in stats]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -333,19 +381,7 @@ def run_ours(args, rank, world):
                           "bound 100 eps_k, tail stages (mu <= alpha) in double-float",
                   "fp64_cauchy_of_result": stats[-1]["fp_residual"],
                   "converged": stats[-1]["converged"]},
-        "roofline": {"bound": "alu", "kernel": "legendre_analysis_f32",
-                     "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
-                     "frac": (achieved / peak32) if achieved else None,
-                     "peak_source": alu["source"] + f" ({alu['num_sms']} SMs)",
-                     "traffic": analysis_traffic(args.nside, k0["gflop"], k0["launches"],
-                                                 ana_variant),
-                     "traffic_source": ANALYSIS_DRAM_FULL_BAND["source"],
-                     "variant": ana_variant,
-                     "launches": k0["launches"], "avg_launch_ms": k0["ms"] / max(1, k0["launches"]),
-                     "synthesis": {"achieved": (kern[1]["gflop"] / (kern[1]["ms"] / 1e3) / 1e3)
-                                   if kern[1]["ms"] > 0 else None,
-                                   "avg_launch_ms": kern[1]["ms"] / max(1, kern[1]["launches"])},
-                     "ring_step": ring_roofline(kern[2], peaks, peak_src)},
+        "roofline": kernel_rooflines(kern, alu, peaks, peak_src, args, ana_variant),
         "clocks": clk,
         "e2e": {"value": 1.0 / (sum(e2e_s) / len(e2e_s)), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * 12 * args.nside ** 2,

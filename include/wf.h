@@ -295,14 +295,18 @@ wf_status wf_trace(wf_plan_t plan, int *count, int *stage, double *xi,
  * opts.timing = 1 since plan creation or the last reset.
  *  kernel    0 = Legendre analysis (Omega Y^T with the fused filter),
  *            1 = Legendre synthesis, 2 = ring step (fold, inverse ring
- *            FFTs, the t-update of Eq. 14, forward ring FFTs; both launches).
+ *            FFTs, the t-update of Eq. 14, forward ring FFTs; both launches)
+ *            of the captured FP32 / FP64 iterations; 3 = double-float
+ *            Legendre synthesis, 4 = double-float Legendre analysis (with
+ *            its tile combine), 5 = FP64 ring step, of the mixed solver's
+ *            anchor-arithmetic steps (anchors, stage boundaries, tail).
  *  ms        summed CUDA-event time of the timed launches.
  *  launches  number of timed launches (iterations that did work).
- *  gflop     algorithmic work of those launches.  Kernels 0, 1: GFLOP, 7
+ *  gflop     algorithmic work of those launches.  Kernels 0, 1, 3, 4: GFLOP, 7
  *            flops (recurrence 3, complex accumulate 4) per (l, m, ring pair)
  *            with l <= the band limit of the launch and |lambda_lm| >=
  *            2^-100 (the terms the method needs; the skipped ones are below
- *            that).  Kernel 2: GB of DRAM traffic the step cannot avoid --
+ *            that).  Kernels 2, 5: GB of DRAM traffic the step cannot avoid --
  *            ring coefficients read and written for m <= the band limit
  *            (8 bytes each in FP32 stages, 16 in FP64) and d, sigma^2 read
  *            (16 bytes per pixel).

@@ -45,6 +45,8 @@ static void free_plan(wf_plan_s *P) {
   if (P->fork_ev) cudaEventDestroy(P->fork_ev);
   if (P->join_ev) cudaEventDestroy(P->join_ev);
   for (cudaEvent_t e : P->tev) cudaEventDestroy(e);
+  for (cudaEvent_t e : P->dd_ev)
+    if (e) cudaEventDestroy(e);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
   delete P;
@@ -411,7 +413,7 @@ wf_status wf_trace(wf_plan_t plan, int *count, int *stage, double *xi, double *m
 wf_status wf_kernel_stats(wf_plan_t plan, int kernel, double *ms, long *launches,
                           double *gflop, int reset) {
   if (!plan) return arg_error("wf_kernel_stats: plan is NULL");
-  if (kernel < 0 || kernel > 2) return arg_error("wf_kernel_stats: kernel must be 0, 1 or 2");
+  if (kernel < 0 || kernel > 5) return arg_error("wf_kernel_stats: kernel must be 0 .. 5");
   if (ms) *ms = plan->kern_ms[kernel];
   if (launches) *launches = plan->kern_launches[kernel];
   if (gflop) *gflop = plan->kern_flop[kernel] * 1e-9;

@@ -644,12 +644,21 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
   WF_CUDA(cudaMemcpyAsync(gx, x, sizeof(double2) * P.nalm, cudaMemcpyDeviceToDevice,
                           P.stream));
   WF_TRY(launch_prescale<double2>(P, x, P.xs64));
+  // opts.timing: events around the double-float synthesis, the ring step and
+  // the double-float analysis (kernels 3, 5, 4 of wf_kernel_stats)
+  const bool timed = dd && P.opts.timing;
+  if (timed && !P.dd_ev[0])
+    for (auto &e : P.dd_ev) WF_CUDA(cudaEventCreate(&e));
+  if (timed) WF_CUDA(cudaEventRecord(P.dd_ev[0], P.stream));
   if (dd)
     WF_TRY(launch_legendre_synth_dd(P, P.xs64, P.F64, nullptr, std::max(L, 0)));
   else
     WF_TRY(launch_legendre_synth<double2>(P, P.xs64, P.F64, nullptr, std::max(L, 0)));
+  if (timed) WF_CUDA(cudaEventRecord(P.dd_ev[1], P.stream));
   WF_TRY(launch_ring<double2>(P, RING_FUSED, P.F64, P.G64, P.dmap, nullptr, P.state,
                               P.lmax));
+  if (timed) WF_CUDA(cudaEventRecord(P.dd_ev[2], P.stream));
+  const int La = U ? std::max(L, Lu) : P.lmax;  // band of the analysis launch
   if (U) {
     const int Lb = std::max(L, Lu);
     if (dd)
@@ -666,10 +675,27 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
   } else {
     WF_TRY(launch_legendre_anal<double2>(P, P.G64, gx, P.state, ANA_FILTER, P.lmax));
   }
+  if (timed) WF_CUDA(cudaEventRecord(P.dd_ev[3], P.stream));
   std::vector<double> part(2 * (P.lmax + 1));
   WF_CUDA(cudaMemcpyAsync(part.data(), P.partials, sizeof(double) * part.size(),
                           cudaMemcpyDeviceToHost, P.stream));
   WF_CUDA(cudaStreamSynchronize(P.stream));
+  if (timed) {
+    float t[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < 3; ++k)
+      WF_CUDA(cudaEventElapsedTime(&t[k], P.dd_ev[k], P.dd_ev[k + 1]));
+    double ts = 0.0, ta = 0.0;
+    WF_TRY(legendre_terms(P, std::max(L, 0), &ts));
+    WF_TRY(legendre_terms(P, La, &ta));
+    P.kern_ms[3] += t[0];
+    P.kern_ms[5] += t[1];
+    P.kern_ms[4] += t[2];
+    P.kern_flop[3] += 7.0 * ts;
+    P.kern_flop[4] += 7.0 * ta;
+    // FP64 ring step: F read and G written for m <= its bands, d and sigma^2
+    P.kern_flop[5] += 16.0 * P.nring * (std::max(L, 0) + La + 2.0) + 16.0 * P.npix;
+    for (int k = 3; k < 6; ++k) P.kern_launches[k] += 1;
+  }
   double acc = 0.0, acd = 0.0;
   for (int m = 0; m <= P.lmax; ++m) {
     acc += part[2 * m];

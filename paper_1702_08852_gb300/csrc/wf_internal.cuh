@@ -240,10 +240,14 @@ struct Plan {
   // timed kernels: 0 analysis, 1 synthesis, 2 ring step (both launches)
   std::vector<cudaEvent_t> tev;     // [3 kernels][2 (start, stop)][chunk]
   int tev_chunk = 0;
-  double kern_ms[3] = {0.0, 0.0, 0.0};
-  long kern_launches[3] = {0, 0, 0};
+  // 3, 4: double-float Legendre synthesis / analysis and 5: FP64 ring step
+  // of the anchor-arithmetic steps (anchors, boundary steps, tail stages),
+  // timed with events around their launches
+  double kern_ms[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  long kern_launches[6] = {0, 0, 0, 0, 0, 0};
+  cudaEvent_t dd_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // algorithmic work of the timed launches: flops (0, 1), DRAM bytes (2)
-  double kern_flop[3] = {0.0, 0.0, 0.0};
+  double kern_flop[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   std::vector<double> work_cache;    // reduced (l, m, ring-pair) count per band
   std::vector<int> seed_l_h;         // host copy of seed_l
 };

@@ -373,7 +373,7 @@ class Plan:
         ms, n, gf = ctypes.c_double(), ctypes.c_long(), ctypes.c_double()
         _check(lib().wf_kernel_stats(self.handle, int(kernel), ctypes.byref(ms),
                                      ctypes.byref(n), ctypes.byref(gf), int(reset)))
-        key = "gbytes" if int(kernel) == 2 else "gflop"
+        key = "gbytes" if int(kernel) in (2, 5) else "gflop"
         return {"ms": ms.value, "launches": n.value, key: gf.value}
 
     def tuning(self):
