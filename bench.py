@@ -173,7 +173,7 @@ def alu_peaks(wf):
 # counted as 2) and two accumulations of a product (15 each)
 DD_FLOPS_PER_TERM = 58.0
 KERNEL_NAMES = ["legendre_analysis_f32", "legendre_synthesis_f32", "ring_step_f32",
-                "legendre_synthesis_dd", "legendre_analysis_dd", "ring_step_f64"]
+                "legendre_synthesis_dd", "legendre_analysis_dd", "ring_step_dd"]
 
 
 def kernel_rooflines(kern, alu, peaks, peak_src, args, ana_variant):
@@ -365,7 +365,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 transforms; anchors and tail stages: double-float Legendre, f64 ring",
+        "dtype": "f32 transforms; anchors and tail stages: double-float Legendre and ring FFTs",
         "data": "synthetic",
         "config": {"workload": f"Nside {args.nside} lmax {2 * args.nside} scan-noise "
                                f"25% mask, 1 map per GPU",
@@ -660,7 +660,7 @@ def run_batch(args, rank, world):
             "value": world * nmaps * args.steps / (total_ms / 1e3), "unit": "maps/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 transforms; anchors: double-float Legendre, f64 ring",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 transforms; anchors and tail stages: double-float Legendre and ring FFTs",
             "data": "synthetic",
             "config": {"workload": "64 maps, Nside in {64,128,256}, lmax = 2 Nside, "
                                    "scan noise, mask 5-40 %",

@@ -99,8 +99,8 @@ typedef struct {
                         fastest (cached per nside, lmax; default 0) */
   int anchor;        /* WF_PREC_MIXED: arithmetic of the anchor steps
                         r = G(x_a) - x_a.  1 (default): the Legendre
-                        transforms in double-float (pairs of FP32, ~48-bit
-                        significand) on the FP32 pipe, ring FFTs in FP64;
+                        transforms and ring FFTs in double-float (pairs of
+                        FP32, ~48-bit significand) on the FP32 pipe;
                         0: plain FP64.  The last stage's acceptance test
                         and fp_residual always use plain FP64. */
   /* WF_PREC_MIXED anchoring.  The defaults reproduce the FP64 solve's
@@ -274,10 +274,10 @@ wf_status wf_map2alm(wf_plan_t plan, const double *map_dev, double *alm_dev);
 wf_status wf_alm2map_f32(wf_plan_t plan, const double *alm_dev, double *map_dev);
 wf_status wf_map2alm_f32(wf_plan_t plan, const double *map_dev, double *alm_dev);
 
-/* The same transforms with the Legendre step in double-float (each value an
- * unevaluated sum of two FP32 numbers, ~48-bit significand, run on the FP32
- * pipe) and FP64 ring FFTs: the arithmetic of the mixed solver's anchor
- * steps (opts.anchor = 1).  FP64 in and out; errors as wf_alm2map_f32. */
+/* The same transforms in double-float (each value an unevaluated sum of two
+ * FP32 numbers, ~48-bit significand, run on the FP32 pipe), the Legendre
+ * steps and the ring FFTs: the arithmetic of the mixed solver's anchor steps
+ * (opts.anchor = 1).  FP64 in and out; errors as wf_alm2map_f32. */
 wf_status wf_alm2map_df64(wf_plan_t plan, const double *alm_dev, double *map_dev);
 wf_status wf_map2alm_df64(wf_plan_t plan, const double *map_dev, double *alm_dev);
 
@@ -296,9 +296,9 @@ wf_status wf_trace(wf_plan_t plan, int *count, int *stage, double *xi,
  *  kernel    0 = Legendre analysis (Omega Y^T with the fused filter),
  *            1 = Legendre synthesis, 2 = ring step (fold, inverse ring
  *            FFTs, the t-update of Eq. 14, forward ring FFTs; both launches)
- *            of the captured FP32 / FP64 iterations; 3 = double-float
- *            Legendre synthesis, 4 = double-float Legendre analysis (with
- *            its tile combine), 5 = FP64 ring step, of the mixed solver's
+ *            of the captured FP32 / FP64 iterations; 3 = Legendre
+ *            synthesis, 4 = Legendre analysis (with its tile combine),
+ *            5 = ring step, all three in double-float, of the mixed solver's
  *            anchor-arithmetic steps (anchors, stage boundaries, tail).
  *  ms        summed CUDA-event time of the timed launches.
  *  launches  number of timed launches (iterations that did work).

@@ -36,7 +36,7 @@ static void free_plan(wf_plan_s *P) {
                   P->state,  P->trace, P->xacc,  P->src, P->xs64, P->xs32,
                   P->nvar32, P->dmap32, P->ana_scratch, P->ana_lstart,
                   P->ana_counter, P->uacc[0], P->uacc[1],
-                  P->seed_s32, P->zs32, P->rg32, P->cl32};
+                  P->seed_s32, P->zs32, P->rg32, P->cl32, P->twdd, P->chirpdd, P->bhatdd};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (P->state_h) cudaFreeHost(P->state_h);

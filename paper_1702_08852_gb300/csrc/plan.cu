@@ -118,6 +118,19 @@ static int bitrev(int x, int bits) {
   return r;
 }
 
+// a complex FP64 table as double-float pairs (re hi, re lo, im hi, im lo)
+// for the double-float ring transforms
+static wf_status upload_dd(const std::vector<double2> &v, float4 **out) {
+  std::vector<float4> h(v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    const float rh = (float)v[i].x, ih = (float)v[i].y;
+    h[i] = make_float4(rh, (float)(v[i].x - (double)rh), ih, (float)(v[i].y - (double)ih));
+  }
+  WF_CUDA(cudaMalloc(out, sizeof(float4) * h.size()));
+  WF_CUDA(cudaMemcpy(*out, h.data(), sizeof(float4) * h.size(), cudaMemcpyHostToDevice));
+  return WF_OK;
+}
+
 static wf_status make_fft_tables(Plan &P) {
   int Mmax = 2;
   long chirp_total = 0, bhat_total = 0;
@@ -146,6 +159,7 @@ static wf_status make_fft_tables(Plan &P) {
                      cudaMemcpyHostToDevice));
   WF_CUDA(cudaMemcpy(P.tw32, tw32.data(), sizeof(float2) * tw.size(),
                      cudaMemcpyHostToDevice));
+  WF_TRY(upload_dd(tw, &P.twdd));
   P.chirp_total = chirp_total;
   P.bhat_total = bhat_total;
   if (chirp_total > 0) {
@@ -189,6 +203,8 @@ static wf_status make_fft_tables(Plan &P) {
                        cudaMemcpyHostToDevice));
     WF_CUDA(cudaMemcpy(P.bhat32, bh32.data(), sizeof(float2) * bhat_total,
                        cudaMemcpyHostToDevice));
+    WF_TRY(upload_dd(ch, &P.chirpdd));
+    WF_TRY(upload_dd(bh, &P.bhatdd));
   }
   return WF_OK;
 }

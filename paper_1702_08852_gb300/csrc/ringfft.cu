@@ -32,6 +32,11 @@ namespace wf {
 template <typename T2> struct CT;
 template <> struct CT<double2> {
   typedef double T;
+  typedef double2 G;  // element type of the global data arrays (F, G)
+  typedef double2 W;  // element type of the tables (twiddles, chirps)
+  static __device__ __forceinline__ double2 ld(const G *p) { return *p; }
+  static __device__ __forceinline__ double2 ldw(const W *p) { return *p; }
+  static __device__ __forceinline__ void st(G *p, double2 v) { *p = v; }
   static __device__ __forceinline__ double2 mk(double a, double b) {
     return make_double2(a, b);
   }
@@ -43,6 +48,11 @@ template <> struct CT<double2> {
 };
 template <> struct CT<float2> {
   typedef float T;
+  typedef float2 G;
+  typedef float2 W;
+  static __device__ __forceinline__ float2 ld(const G *p) { return *p; }
+  static __device__ __forceinline__ float2 ldw(const W *p) { return *p; }
+  static __device__ __forceinline__ void st(G *p, float2 v) { *p = v; }
   static __device__ __forceinline__ float2 mk(float a, float b) {
     return make_float2(a, b);
   }
@@ -119,6 +129,92 @@ template <> struct TwPass<double2> {
   }
 };
 
+// ---------------------------------------------------------- double-float
+// ddr: an unevaluated sum hi + lo of two floats (~48-bit significand) with
+// the operations the ring transforms use -- sums by two-sum, products by
+// the FMA two-product, one normalisation each (Dekker, Knuth); explicit _rn
+// intrinsics, so nothing is contracted or reassociated.  The mixed solver's
+// anchor steps run their ring FFTs in it on the FP32 pipe: this part's FP64
+// pipe runs at ~1/64 of the FP32 rate, and those FFTs were FP64-bound.
+// Global data stays FP64 (converted at load and store); the twiddle, chirp
+// and kernel-spectrum tables are kept as (hi, lo) float pairs.
+struct ddr {
+  float hi, lo;
+  __device__ __forceinline__ ddr() : hi(0.f), lo(0.f) {}
+  __device__ __forceinline__ ddr(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ ddr(int v) : hi((float)v), lo(0.f) {}
+  __device__ __forceinline__ ddr(double v) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+  }
+  __device__ __forceinline__ explicit operator double() const {
+    return (double)hi + (double)lo;
+  }
+};
+__device__ __forceinline__ ddr ddr_norm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return ddr(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ ddr operator+(ddr a, ddr b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return ddr_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ddr operator-(ddr a) { return ddr(-a.hi, -a.lo); }
+__device__ __forceinline__ ddr operator-(ddr a, ddr b) { return a + (-b); }
+__device__ __forceinline__ ddr operator*(ddr a, ddr b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  return ddr_norm(p, e);
+}
+__device__ __forceinline__ ddr &operator*=(ddr &a, ddr b) {
+  a = a * b;
+  return a;
+}
+__device__ __forceinline__ bool operator<(ddr a, ddr b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+
+struct ddc {
+  ddr x, y;
+};
+template <> struct CT<ddc> {
+  typedef ddr T;
+  typedef double2 G;  // F, G stay FP64
+  typedef float4 W;   // tables as (re hi, re lo, im hi, im lo)
+  static __device__ __forceinline__ ddc ld(const G *p) {
+    const double2 v = *p;
+    return {ddr(v.x), ddr(v.y)};
+  }
+  static __device__ __forceinline__ ddc ldw(const W *p) {
+    const float4 v = *p;
+    return {ddr(v.x, v.y), ddr(v.z, v.w)};
+  }
+  static __device__ __forceinline__ void st(G *p, ddc v) {
+    *p = make_double2((double)v.x, (double)v.y);
+  }
+  static __device__ __forceinline__ ddc mk(ddr a, ddr b) { return {a, b}; }
+  // sin, cos of pi r / den, rounded from FP64
+  static __device__ __forceinline__ void sincospi_(int r, int den, ddr *s, ddr *c) {
+    double sd, cd;
+    sincospi((double)r / (double)den, &sd, &cd);
+    *s = ddr(sd);
+    *c = ddr(cd);
+  }
+};
+template <> struct TwPass<ddc> {
+  const float4 *tw;
+  int ts;
+  __device__ __forceinline__ TwPass(int h, const float4 *t, int Mmax)
+      : tw(t), ts(Mmax / (2 * h)) {}
+  __device__ __forceinline__ void pair(int j, ddc &w2h, ddc &wh) const {
+    w2h = CT<ddc>::ldw(tw + j * ts);
+    wh = CT<ddc>::ldw(tw + 2 * j * ts);
+  }
+};
+
 // natural -> bit-reversed; INV uses e^{+2 pi i jk/M}.  Two radix-2 stages
 // (spans h and h/2) per pass over shared memory ("radix-2^2"): the output
 // order stays bit-reversed, and the barriers and shared-memory round trips
@@ -126,7 +222,7 @@ template <> struct TwPass<double2> {
 // Where the twiddle index j = b mod q is the same for all of a thread's
 // butterflies (q <= blockDim), the twiddles are computed once per pass.
 template <typename T2, bool INV>
-__device__ void fft_dif(T2 *buf, int M, const T2 *__restrict__ tw, int Mmax) {
+__device__ void fft_dif(T2 *buf, int M, const typename CT<T2>::W *__restrict__ tw, int Mmax) {
   int h = M >> 1;
   for (; h >= 2; h >>= 2) {
     const int q = h >> 1;
@@ -164,7 +260,7 @@ __device__ void fft_dif(T2 *buf, int M, const T2 *__restrict__ tw, int Mmax) {
 // bit-reversed -> natural; an odd number of stages starts with one radix-2
 // pass of span 1, then pairs of stages (spans h and 2h) per pass
 template <typename T2, bool INV>
-__device__ void fft_dit(T2 *buf, int M, const T2 *__restrict__ tw, int Mmax) {
+__device__ void fft_dit(T2 *buf, int M, const typename CT<T2>::W *__restrict__ tw, int Mmax) {
   int h = 1;
   int bits = 0;
   while ((1 << bits) < M) ++bits;
@@ -207,16 +303,18 @@ __device__ void fft_dit(T2 *buf, int M, const T2 *__restrict__ tw, int Mmax) {
 // In place: buf[0..n) holds a_j = x_j conj(w_j) and buf[n..M) zeros on entry;
 // on exit buf[0..n) holds X = DFT_n(x).
 template <typename T2>
-__device__ void bluestein(T2 *buf, int n, int M, const T2 *__restrict__ tw,
-                          int Mmax, const T2 *__restrict__ chirp,
-                          const T2 *__restrict__ bhat) {
+__device__ void bluestein(T2 *buf, int n, int M, const typename CT<T2>::W *__restrict__ tw,
+                          int Mmax, const typename CT<T2>::W *__restrict__ chirp,
+                          const typename CT<T2>::W *__restrict__ bhat) {
   fft_dif<T2, false>(buf, M, tw, Mmax);
   #pragma unroll 8
-  for (int q = threadIdx.x; q < M; q += blockDim.x) buf[sw(q)] = cmul(buf[sw(q)], bhat[q]);
+  for (int q = threadIdx.x; q < M; q += blockDim.x)
+    buf[sw(q)] = cmul(buf[sw(q)], CT<T2>::ldw(bhat + q));
   __syncthreads();
   fft_dit<T2, true>(buf, M, tw, Mmax);
   #pragma unroll 8
-  for (int k = threadIdx.x; k < n; k += blockDim.x) buf[sw(k)] = cmulc(buf[sw(k)], chirp[k]);
+  for (int k = threadIdx.x; k < n; k += blockDim.x)
+    buf[sw(k)] = cmulc(buf[sw(k)], CT<T2>::ldw(chirp + k));
   __syncthreads();
 }
 
@@ -235,10 +333,10 @@ __device__ __forceinline__ int bitrev_n(int x, int bits) {
 // sincospi with the exact rational argument k / den.
 template <typename T2>
 __device__ __forceinline__ T2 ring_phase(int k, int num, int den, int tstep,
-                                         const T2 *__restrict__ tw) {
+                                         const typename CT<T2>::W *__restrict__ tw) {
   typedef typename CT<T2>::T T;
   if (num == 0) return CT<T2>::mk((T)1, (T)0);
-  if (tstep > 0) return cconj(tw[k * tstep]);
+  if (tstep > 0) return cconj(CT<T2>::ldw(tw + k * tstep));
   T s, c;
   CT<T2>::sincospi_(k, den, &s, &c);
   return CT<T2>::mk(c, s);
@@ -249,28 +347,28 @@ __device__ __forceinline__ T2 ring_phase(int k, int num, int den, int tstep,
 // When n > L each sum has at most one term (every equatorial ring, the outer
 // polar rings): the two loads are issued together, not in dependent loops.
 template <typename T2>
-__device__ __forceinline__ T2 fold(const T2 *__restrict__ Fr, int k, int n, int L,
-                                   typename CT<T2>::T sgn, T2 ph) {
+__device__ __forceinline__ T2 fold(const typename CT<T2>::G *__restrict__ Fr, int k, int n,
+                                   int L, typename CT<T2>::T sgn, T2 ph) {
   typedef typename CT<T2>::T T;
   T2 acc = CT<T2>::mk((T)0, (T)0);
   if (n > L) {
     const T2 zero = CT<T2>::mk((T)0, (T)0);
-    const T2 a = k <= L ? Fr[k] : zero;
-    const T2 b = n - k <= L ? Fr[n - k] : zero;
+    const T2 a = k <= L ? CT<T2>::ld(Fr + k) : zero;
+    const T2 b = n - k <= L ? CT<T2>::ld(Fr + (n - k)) : zero;
     acc = CT<T2>::mk(a.x + sgn * b.x, a.y - sgn * b.y);
     return cmul(acc, ph);
   }
   T s = (T)1;
 #pragma unroll 4
   for (int m = k; m <= L; m += n) {
-    const T2 f = Fr[m];
+    const T2 f = CT<T2>::ld(Fr + m);
     acc = CT<T2>::mk(acc.x + s * f.x, acc.y + s * f.y);
     s *= sgn;
   }
   s = sgn;
 #pragma unroll 4
   for (int m = n - k; m <= L; m += n) {  // m >= 1 since k < n
-    const T2 f = Fr[m];
+    const T2 f = CT<T2>::ld(Fr + m);
     acc = CT<T2>::mk(acc.x + s * f.x, acc.y - s * f.y);
     s *= sgn;
   }
@@ -286,13 +384,16 @@ constexpr int RING_THREADS_BIG = 512;
 template <typename T2, int MODE>
 __global__ void __launch_bounds__(RING_THREADS_BIG)
     k_ring(const RingPair *__restrict__ pairs, int pair_base, int lmax,
-           const T2 *__restrict__ F, T2 *__restrict__ G,
+           const typename CT<T2>::G *__restrict__ F, typename CT<T2>::G *__restrict__ G,
            const double *__restrict__ in_map, double *__restrict__ out_map,
-           const double *__restrict__ nvar, const T2 *__restrict__ tw, int Mmax,
-           const T2 *__restrict__ chirp_all, const T2 *__restrict__ bhat_all,
+           const double *__restrict__ nvar, const typename CT<T2>::W *__restrict__ tw,
+           int Mmax, const typename CT<T2>::W *__restrict__ chirp_all,
+           const typename CT<T2>::W *__restrict__ bhat_all,
            const SolverState *__restrict__ st, int lstatic, int reverse,
            const float *__restrict__ in32, const float *__restrict__ nv32, int red_ofs) {
   typedef typename CT<T2>::T T;
+  typedef typename CT<T2>::G GT;
+  typedef typename CT<T2>::W WT;
   // reverse: the polar rings grow with the pair index; taking the largest
   // first keeps the small ones for the tail of the launch
   const int blk = reverse ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
@@ -327,8 +428,8 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
   const bool blue = M != n;
   int bits = 0;
   while ((1 << bits) < M) ++bits;
-  const T2 *chirp = blue ? chirp_all + rp.chirp_ofs : nullptr;
-  const T2 *bhat = blue ? bhat_all + rp.bhat_ofs : nullptr;
+  const WT *chirp = blue ? chirp_all + rp.chirp_ofs : nullptr;
+  const WT *bhat = blue ? bhat_all + rp.bhat_ofs : nullptr;
   const long stride = lmax + 1;
   const bool south = rp.ringS >= 0;
   const T2 zero = CT<T2>::mk((T)0, (T)0);
@@ -336,8 +437,8 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
   const int tstep = (rp.phi_num && Mmax % (2 * rp.phi_den) == 0) ? Mmax / (2 * rp.phi_den) : 0;
 
   if (MODE != RING_ANALYSIS) {
-    const T2 *FN = F + rp.ringN * stride;
-    const T2 *FS = south ? F + rp.ringS * stride : nullptr;
+    const GT *FN = F + rp.ringN * stride;
+    const GT *FS = south ? F + rp.ringS * stride : nullptr;
     if (n < (int)blockDim.x) {
       // small rings (n < threads): each k's sums over j are split across
       // P = threads / n threads (j = part mod P), whose partials are added
@@ -349,19 +450,19 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
         if (Lf >= 0) {
           for (int j = part; k + j * n <= Lf; j += P) {  // m = k + j n
             const T s = (sgn < (T)0 && (j & 1)) ? (T)-1 : (T)1;
-            const T2 f = FN[k + j * n];
+            const T2 f = CT<T2>::ld(FN + (k + j * n));
             pN = CT<T2>::mk(pN.x + s * f.x, pN.y + s * f.y);
             if (south) {
-              const T2 g = FS[k + j * n];
+              const T2 g = CT<T2>::ld(FS + (k + j * n));
               pS = CT<T2>::mk(pS.x + s * g.x, pS.y + s * g.y);
             }
           }
           for (int j = 1 + part; j * n - k <= Lf; j += P) {  // m = j n - k, conj
             const T s = (sgn < (T)0 && (j & 1)) ? (T)-1 : (T)1;
-            const T2 f = FN[j * n - k];
+            const T2 f = CT<T2>::ld(FN + (j * n - k));
             pN = CT<T2>::mk(pN.x + s * f.x, pN.y - s * f.y);
             if (south) {
-              const T2 g = FS[j * n - k];
+              const T2 g = CT<T2>::ld(FS + (j * n - k));
               pS = CT<T2>::mk(pS.x + s * g.x, pS.y - s * g.y);
             }
           }
@@ -380,7 +481,7 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
         cN = cmul(cN, ph);
         cS = cmul(cS, ph);
         const T2 Zk = CT<T2>::mk(cN.x - cS.y, cN.y + cS.x);  // cN + i cS
-        buf[sw(k)] = blue ? cmulc(cconj(Zk), chirp[k]) : Zk;
+        buf[sw(k)] = blue ? cmulc(cconj(Zk), CT<T2>::ldw(chirp + k)) : Zk;
       }
     } else {
       #pragma unroll 4
@@ -392,7 +493,7 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
           if (south) cS = fold(FS, k, n, Lf, sgn, ph);
         }
         const T2 Zk = CT<T2>::mk(cN.x - cS.y, cN.y + cS.x);  // cN + i cS
-        buf[sw(k)] = blue ? cmulc(cconj(Zk), chirp[k]) : Zk;
+        buf[sw(k)] = blue ? cmulc(cconj(Zk), CT<T2>::ldw(chirp + k)) : Zk;
       }
     }
     if (blue)
@@ -441,7 +542,7 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
           }
           tt = CT<T2>::mk((T)tN, (T)tS);
         }
-        buf[sw(q)] = blue ? cmulc(tt, chirp[q]) : tt;
+        buf[sw(q)] = blue ? cmulc(tt, CT<T2>::ldw(chirp + q)) : tt;
       }
     }
     if (MODE == RING_SYNTH) return;
@@ -455,7 +556,7 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
       const double tS = south ? in_map[rp.ofsS + j] : 0.0;
       const T2 tt = CT<T2>::mk((T)tN, (T)tS);
       if (blue)
-        buf[sw(j)] = cmulc(tt, chirp[j]);
+        buf[sw(j)] = cmulc(tt, CT<T2>::ldw(chirp + j));
       else
         buf[sw(bitrev_n(j, bits))] = tt;
     }
@@ -470,8 +571,8 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
     fft_dit<T2, false>(buf, M, tw, Mmax);
   // split the two real rings and apply e^{-i m phi0}: for m = k + j n,
   // G[m] = sgn^j e^{-i k phi0} X_k (X^N or X^S)
-  T2 *GN = G + rp.ringN * stride;
-  T2 *GS = south ? G + rp.ringS * stride : nullptr;
+  GT *GN = G + rp.ringN * stride;
+  GT *GS = south ? G + rp.ringS * stride : nullptr;
   const T half = (T)0.5;
   const int kmax = min(n - 1, Lg);
   // small rings: the copies m = k + j n of each k are split across
@@ -493,8 +594,8 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
       for (int j = part; k + j * n <= Lg; j += P) {
         const int m = k + j * n;
         const T s = (sgn < (T)0 && (j & 1)) ? (T)-1 : (T)1;
-        GN[m] = CT<T2>::mk(s * tN.x, s * tN.y);
-        if (south) GS[m] = CT<T2>::mk(s * tS.x, s * tS.y);
+        CT<T2>::st(GN + m, CT<T2>::mk(s * tN.x, s * tN.y));
+        if (south) CT<T2>::st(GS + m, CT<T2>::mk(s * tS.x, s * tS.y));
       }
     }
   }
@@ -511,11 +612,17 @@ template <> struct Tables<float2> {
   static const float2 *ch(const Plan &P) { return P.chirp32; }
   static const float2 *bh(const Plan &P) { return P.bhat32; }
 };
+template <> struct Tables<ddc> {
+  static const float4 *tw(const Plan &P) { return P.twdd; }
+  static const float4 *ch(const Plan &P) { return P.chirpdd; }
+  static const float4 *bh(const Plan &P) { return P.bhatdd; }
+};
 
 template <typename T2, int MODE>
-static wf_status launch_ring_mode(const Plan &P, const T2 *F, T2 *G,
-                                  const double *in_map, double *out_map,
-                                  const SolverState *st, int lstatic, const float *in32) {
+static wf_status launch_ring_mode(const Plan &P, const typename CT<T2>::G *F,
+                                  typename CT<T2>::G *G, const double *in_map,
+                                  double *out_map, const SolverState *st, int lstatic,
+                                  const float *in32) {
   auto kern = k_ring<T2, MODE>;
   // two launches: the polar rings (pairs 0 .. nside-2, Bluestein unless n is
   // a power of two) and the equatorial belt (pairs nside-1 .. 2 nside-1);
@@ -574,6 +681,22 @@ wf_status launch_ring(const Plan &P, int mode, const T2 *F, T2 *G,
   }
 }
 
+wf_status launch_ring_dd(const Plan &P, int mode, const double2 *F, double2 *G,
+                         const double *in_map, double *out_map, const SolverState *st,
+                         int lstatic) {
+  switch (mode) {
+    case RING_SYNTH:
+      return launch_ring_mode<ddc, RING_SYNTH>(P, F, G, in_map, out_map, st, lstatic,
+                                               nullptr);
+    case RING_ANALYSIS:
+      return launch_ring_mode<ddc, RING_ANALYSIS>(P, F, G, in_map, out_map, st, lstatic,
+                                                  nullptr);
+    default:
+      return launch_ring_mode<ddc, RING_FUSED>(P, F, G, in_map, out_map, st, lstatic,
+                                               nullptr);
+  }
+}
+
 wf_status init_ring_attributes() {
   const int big = 220 * 1024;
   WF_CUDA(cudaFuncSetAttribute(k_ring<double2, RING_SYNTH>,
@@ -587,6 +710,12 @@ wf_status init_ring_attributes() {
   WF_CUDA(cudaFuncSetAttribute(k_ring<float2, RING_ANALYSIS>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   WF_CUDA(cudaFuncSetAttribute(k_ring<float2, RING_FUSED>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  WF_CUDA(cudaFuncSetAttribute(k_ring<ddc, RING_SYNTH>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  WF_CUDA(cudaFuncSetAttribute(k_ring<ddc, RING_ANALYSIS>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  WF_CUDA(cudaFuncSetAttribute(k_ring<ddc, RING_FUSED>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   return WF_OK;
 }

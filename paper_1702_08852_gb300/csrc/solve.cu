@@ -339,14 +339,12 @@ wf_status alm2map_df64(Plan &P, const double *alm, double *map) {
   const double2 *a = reinterpret_cast<const double2 *>(alm);
   WF_TRY(launch_prescale<double2>(P, a, P.xs64));
   WF_TRY(launch_legendre_synth_dd(P, P.xs64, P.F64, nullptr, P.lmax));
-  WF_TRY(launch_ring<double2>(P, RING_SYNTH, P.F64, nullptr, nullptr, map, nullptr,
-                              P.lmax));
+  WF_TRY(launch_ring_dd(P, RING_SYNTH, P.F64, nullptr, nullptr, map, nullptr, P.lmax));
   return WF_OK;
 }
 
 wf_status map2alm_df64(Plan &P, const double *map, double *alm) {
-  WF_TRY(launch_ring<double2>(P, RING_ANALYSIS, nullptr, P.G64, map, nullptr, nullptr,
-                              P.lmax));
+  WF_TRY(launch_ring_dd(P, RING_ANALYSIS, nullptr, P.G64, map, nullptr, nullptr, P.lmax));
   WF_TRY(launch_legendre_anal_dd(P, P.G64, reinterpret_cast<double2 *>(alm), nullptr,
                                  ANA_PLAIN, P.lmax));
   return WF_OK;
@@ -644,8 +642,8 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
   WF_CUDA(cudaMemcpyAsync(gx, x, sizeof(double2) * P.nalm, cudaMemcpyDeviceToDevice,
                           P.stream));
   WF_TRY(launch_prescale<double2>(P, x, P.xs64));
-  // opts.timing: events around the double-float synthesis, the ring step and
-  // the double-float analysis (kernels 3, 5, 4 of wf_kernel_stats)
+  // opts.timing: events around the double-float synthesis, ring step and
+  // analysis (kernels 3, 5, 4 of wf_kernel_stats)
   const bool timed = dd && P.opts.timing;
   if (timed && !P.dd_ev[0])
     for (auto &e : P.dd_ev) WF_CUDA(cudaEventCreate(&e));
@@ -655,8 +653,11 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
   else
     WF_TRY(launch_legendre_synth<double2>(P, P.xs64, P.F64, nullptr, std::max(L, 0)));
   if (timed) WF_CUDA(cudaEventRecord(P.dd_ev[1], P.stream));
-  WF_TRY(launch_ring<double2>(P, RING_FUSED, P.F64, P.G64, P.dmap, nullptr, P.state,
-                              P.lmax));
+  if (dd)
+    WF_TRY(launch_ring_dd(P, RING_FUSED, P.F64, P.G64, P.dmap, nullptr, P.state, P.lmax));
+  else
+    WF_TRY(launch_ring<double2>(P, RING_FUSED, P.F64, P.G64, P.dmap, nullptr, P.state,
+                                P.lmax));
   if (timed) WF_CUDA(cudaEventRecord(P.dd_ev[2], P.stream));
   const int La = U ? std::max(L, Lu) : P.lmax;  // band of the analysis launch
   if (U) {
@@ -692,7 +693,7 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
     P.kern_ms[4] += t[2];
     P.kern_flop[3] += 7.0 * ts;
     P.kern_flop[4] += 7.0 * ta;
-    // FP64 ring step: F read and G written for m <= its bands, d and sigma^2
+    // ring step: F read and G written (FP64) for m <= its bands, d and sigma^2
     P.kern_flop[5] += 16.0 * P.nring * (std::max(L, 0) + La + 2.0) + 16.0 * P.npix;
     for (int k = 3; k < 6; ++k) P.kern_launches[k] += 1;
   }

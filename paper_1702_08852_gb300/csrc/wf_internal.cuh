@@ -189,6 +189,9 @@ struct Plan {
   float2 *chirp32 = nullptr;
   double2 *bhat64 = nullptr;     // FFT_M of the chirp kernel, bit-reversed order
   float2 *bhat32 = nullptr;
+  // the same three tables as double-float pairs (re hi, re lo, im hi, im lo)
+  // for the double-float ring transforms of the anchor steps
+  float4 *twdd = nullptr, *chirpdd = nullptr, *bhatdd = nullptr;
   long chirp_total = 0, bhat_total = 0;
 
   // noise
@@ -294,6 +297,11 @@ wf_status launch_ring(const Plan &P, int mode, const T2 *F, T2 *G,
                       const double *in_map, double *out_map,
                       const SolverState *st, int lstatic,
                       const float *in32 = nullptr);
+// The FP64 ring transforms (FP64 F, G, maps) computed in double-float
+// arithmetic on the FP32 pipe (the anchor steps' arithmetic).
+wf_status launch_ring_dd(const Plan &P, int mode, const double2 *F, double2 *G,
+                         const double *in_map, double *out_map, const SolverState *st,
+                         int lstatic);
 
 // once per plan (kernel attributes; allowed outside stream capture only)
 wf_status init_legendre_attributes();
