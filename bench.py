@@ -57,7 +57,10 @@ def parse():
     ap.add_argument("--train-maps", type=int, default=64)
     ap.add_argument("--eval-maps", type=int, default=8)
     ap.add_argument("--epochs", type=int, default=20)
-    ap.add_argument("--workload", choices=["nside1024", "batch64", "learned"],
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="one warm-up solve, then one solve inside the NVTX range "
+                         "'solve' (for a bounded profiler launch list) and exit")
+    ap.add_argument("--workload", choices=["nside1024", "batch64", "learned", "flat512"],
                     default="nside1024",
                     help="batch64: 64 maps, Nside drawn from {64, 128, 256}, solved "
                          "together (maps/s)")
@@ -818,10 +821,40 @@ def run_kernel_case(args):
     print(json.dumps({"kernel_case": args.kernel_case, "nside": ns, **out}))
 
 
+def run_profile_solve(args):
+    """The timed configuration's solve, once untimed, then once inside the
+    NVTX range 'solve' (profilers select its launches with --nvtx-include
+    "solve/")."""
+    import torch
+    from paper_1702_08852_gb300 import wf
+    p, nv, mk, d = make_workload(args.nside, seed=3000)
+    plan = wf.Plan(p.nside, p.lmax, p.cl, nv, mk, precision=wf.WF_PREC_MIXED,
+                   eps_final=args.eps, autotune=1)
+    plan.solve(d)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("solve")
+    _, _, st = plan.solve(d)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    plan.close()
+    print(json.dumps({"profile_solve": args.nside, "iterations": st["iterations"],
+                      "kernel_launches": st["kernel_launches"],
+                      "solve_ms": st["elapsed_ms"]}))
+
+
 def main():
     args = parse()
     if args.kernel_case:
         run_kernel_case(args)
+        return
+    if args.profile_solve:
+        run_profile_solve(args)
+        return
+    if args.workload == "flat512" and args.impl != "reference":
+        import torch
+        from paper_1702_08852_gb300 import wf
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        print(json.dumps(flat_sky(wf, args)))
         return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
