@@ -36,7 +36,8 @@ static void free_plan(wf_plan_s *P) {
                   P->state,  P->trace, P->xacc,  P->src, P->xs64, P->xs32,
                   P->nvar32, P->dmap32, P->ana_scratch, P->ana_lstart,
                   P->ana_counter, P->uacc[0], P->uacc[1],
-                  P->seed_s32, P->zs32, P->rg32, P->cl32, P->twdd, P->chirpdd, P->bhatdd};
+                  P->seed_s32, P->zs32, P->rg32, P->cl32, P->twdd, P->chirpdd, P->bhatdd,
+                  P->phasedd, P->rcdd, P->nvardd, P->dmapdd};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (P->state_h) cudaFreeHost(P->state_h);
@@ -69,6 +70,7 @@ static wf_status alloc_work(Plan &P) {
   WF_CUDA(cudaMalloc(&P.src, sizeof(double2) * P.nalm));
   WF_CUDA(cudaMalloc(&P.dmap, sizeof(double) * P.npix));
   WF_CUDA(cudaMalloc(&P.dmap32, sizeof(float) * P.npix));
+  WF_CUDA(cudaMalloc(&P.dmapdd, sizeof(float2) * P.npix));
   {
     // queue-scheduled FP32 analysis: partial sums of tiles of 128 ring pairs
     // (the smallest tile of its variants)

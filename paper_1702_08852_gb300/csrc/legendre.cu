@@ -1139,9 +1139,9 @@ constexpr int DD_LC_ANA = 8;
 // DD_NP_SYN ring pairs), E/O parity sums in df64
 __global__ void __launch_bounds__(SYN_THREADS)
     k_legendre_synth_dd(const RingPair *__restrict__ pairs, int npairs, int lmax,
-                        const double *__restrict__ rc, const int *__restrict__ seed_l,
-                        const double2 *__restrict__ seed_u, const double2 *__restrict__ xs,
-                        double2 *__restrict__ F, const SolverState *__restrict__ st,
+                        const float2 *__restrict__ rcdd, const int *__restrict__ seed_l,
+                        const double2 *__restrict__ seed_u, const float4 *__restrict__ xs,
+                        float4 *__restrict__ F, const SolverState *__restrict__ st,
                         int lstatic) {
   constexpr int NP = DD_NP_SYN;
   const int m = blockIdx.y;
@@ -1158,10 +1158,11 @@ __global__ void __launch_bounds__(SYN_THREADS)
   dd *sc = sxi + nl;
   const long base = lm_index(lmax, m, m);
   for (int j = threadIdx.x; j < nl; j += blockDim.x) {
-    const double2 xv = xs[base + j];
-    sxr[j] = dd_of(xv.x);
-    sxi[j] = dd_of(xv.y);
-    sc[j] = dd_of(rc[base + j]);
+    const float4 xv = xs[base + j];
+    const float2 cv = rcdd[base + j];
+    sxr[j] = {xv.x, xv.y};
+    sxi[j] = {xv.z, xv.w};
+    sc[j] = {cv.x, cv.y};
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1219,10 +1220,14 @@ __global__ void __launch_bounds__(SYN_THREADS)
     const int k = pair0 + lane + 32 * j;
     if (k >= npairs) continue;
     const RingPair &rp = pairs[k];
-    const double e_r = dd_val(er[j]), e_i = dd_val(ei[j]);
-    const double o_r = dd_val(orr[j]), o_i = dd_val(oi[j]);
-    F[rp.ringN * stride + m] = make_double2(e_r + o_r, e_i + o_i);
-    if (rp.ringS >= 0) F[rp.ringS * stride + m] = make_double2(e_r - o_r, e_i - o_i);
+    // north = E + O, south = E - O, as double-float pairs (re hi, re lo,
+    // im hi, im lo): the double-float ring transform reads them unconverted
+    const dd nr = dd_add(er[j], orr[j]), ni = dd_add(ei[j], oi[j]);
+    F[rp.ringN * stride + m] = make_float4(nr.hi, nr.lo, ni.hi, ni.lo);
+    if (rp.ringS >= 0) {
+      const dd sr = dd_sub(er[j], orr[j]), si = dd_sub(ei[j], oi[j]);
+      F[rp.ringS * stride + m] = make_float4(sr.hi, sr.lo, si.hi, si.lo);
+    }
   }
 }
 
@@ -1232,8 +1237,8 @@ __global__ void __launch_bounds__(SYN_THREADS)
 // rounded to FP64 once per output
 __global__ void __launch_bounds__(ANA_THREADS)
     k_legendre_anal_dd(const RingPair *__restrict__ pairs, int npairs, int lmax, long nalm,
-                       const double *__restrict__ rc, const int *__restrict__ seed_l,
-                       const double2 *__restrict__ seed_u, const double2 *__restrict__ G,
+                       const float2 *__restrict__ rcdd, const int *__restrict__ seed_l,
+                       const double2 *__restrict__ seed_u, const float4 *__restrict__ G,
                        double *__restrict__ scratch, int *__restrict__ lstart,
                        int *__restrict__ counter, const SolverState *__restrict__ st,
                        int lstatic) {
@@ -1275,13 +1280,16 @@ __global__ void __launch_bounds__(ANA_THREADS)
         const double2 su = seed_u[(long)m * npairs + k];
         s0[j] = dd_of(su.x);
         s1[j] = dd_of(su.y);
-        const double2 gn = G[rp.ringN * stride + m];
-        double2 gs = make_double2(0.0, 0.0);
+        // ring coefficients as double-float pairs (re hi, re lo, im hi, im lo)
+        const float4 gn = G[rp.ringN * stride + m];
+        float4 gs = make_float4(0.f, 0.f, 0.f, 0.f);
         if (rp.ringS >= 0) gs = G[rp.ringS * stride + m];
-        pr[j] = dd_of(gn.x + gs.x);
-        pim[j] = dd_of(gn.y + gs.y);
-        qr[j] = dd_of(gn.x - gs.x);
-        qim[j] = dd_of(gn.y - gs.y);
+        const dd nre = {gn.x, gn.y}, nim = {gn.z, gn.w};
+        const dd sre = {gs.x, gs.y}, sim = {gs.z, gs.w};
+        pr[j] = dd_add(nre, sre);
+        pim[j] = dd_add(nim, sim);
+        qr[j] = dd_sub(nre, sre);
+        qim[j] = dd_sub(nim, sim);
       }
       if (ls[j] <= L) {
         lmin = min(lmin, ls[j]);
@@ -1295,7 +1303,10 @@ __global__ void __launch_bounds__(ANA_THREADS)
     if (lane == 0) lstart[(long)m * ntiles + tile] = lc0;
     if (lmin > L) continue;
     __syncwarp();
-    for (int j = lane; j <= L - m; j += 32) sc[j] = dd_of(rc[base + j]);
+    for (int j = lane; j <= L - m; j += 32) {
+      const float2 cv = rcdd[base + j];
+      sc[j] = {cv.x, cv.y};
+    }
     __syncwarp();
     double *out = scratch + 2 * ((long)tile * nalm + base - m);  // out[2 l + re/im]
     for (int lc = lc0; lc <= L; lc += LC) {
@@ -1510,19 +1521,19 @@ wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
 
 // double-float transforms for the anchors of the mixed solver (FP64 in and
 // out; see the kernels above)
-wf_status launch_legendre_synth_dd(const Plan &P, const double2 *xs, double2 *F,
+wf_status launch_legendre_synth_dd(const Plan &P, const float4 *xs, float4 *F,
                                    const SolverState *st, int lstatic) {
   const size_t smem = 3 * sizeof(dd) * (P.lmax + 1);
   const int pairs_per_cta = SYN_THREADS * DD_NP_SYN;
   dim3 grid((P.npairs + pairs_per_cta - 1) / pairs_per_cta, P.lmax + 1);
   ++P.nlaunch;
   k_legendre_synth_dd<<<grid, SYN_THREADS, smem, P.stream>>>(
-      P.pairs, P.npairs, P.lmax, P.rc, P.seed_l, P.seed_u, xs, F, st, lstatic);
+      P.pairs, P.npairs, P.lmax, P.rcdd, P.seed_l, P.seed_u, xs, F, st, lstatic);
   WF_CUDA(cudaGetLastError());
   return WF_OK;
 }
 
-wf_status launch_legendre_anal_dd(const Plan &P, const double2 *G, double2 *x,
+wf_status launch_legendre_anal_dd(const Plan &P, const float4 *G, double2 *x,
                                   const SolverState *st, int mode, int lstatic,
                                   const double2 *src, double2 *xs_out) {
   const size_t smem = sizeof(dd) * (P.lmax + 1) * ANA_WARPS;
@@ -1541,7 +1552,7 @@ wf_status launch_legendre_anal_dd(const Plan &P, const double2 *G, double2 *x,
   double *scratch = reinterpret_cast<double *>(P.ana_scratch);
   ++P.nlaunch;
   k_legendre_anal_dd<<<P.num_sms * per_sm, ANA_THREADS, smem, P.stream>>>(
-      P.pairs, P.npairs, P.lmax, P.nalm, P.rc, P.seed_l, P.seed_u, G, scratch,
+      P.pairs, P.npairs, P.lmax, P.nalm, P.rcdd, P.seed_l, P.seed_u, G, scratch,
       P.ana_lstart, P.ana_counter, st, lstatic);
   WF_CUDA(cudaGetLastError());
   ++P.nlaunch;
@@ -1622,6 +1633,26 @@ template <typename T2>
 wf_status launch_prescale(const Plan &P, const double2 *x, T2 *xs) {
   ++P.nlaunch;
   k_prescale<T2><<<P.lmax + 1, 128, 0, P.stream>>>(x, P.rg, P.lmax, xs);
+  WF_CUDA(cudaGetLastError());
+  return WF_OK;
+}
+
+// the synthesis input of the double-float transforms: g_lm x_lm (FP64
+// product) as double-float pairs (re hi, re lo, im hi, im lo)
+__global__ void k_prescale_dd(const double2 *__restrict__ x, const double *__restrict__ rg,
+                              int lmax, float4 *__restrict__ xs) {
+  const int m = blockIdx.x;
+  const long base = lm_index(lmax, m, m) - m;
+  for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
+    const long i = base + l;
+    const dd re = dd_of(rg[i] * x[i].x), im = dd_of(rg[i] * x[i].y);
+    xs[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+  }
+}
+
+wf_status launch_prescale_dd(const Plan &P, const double2 *x, float4 *xs) {
+  ++P.nlaunch;
+  k_prescale_dd<<<P.lmax + 1, 128, 0, P.stream>>>(x, P.rg, P.lmax, xs);
   WF_CUDA(cudaGetLastError());
   return WF_OK;
 }

@@ -205,6 +205,22 @@ static wf_status make_fft_tables(Plan &P) {
                        cudaMemcpyHostToDevice));
     WF_TRY(upload_dd(ch, &P.chirpdd));
     WF_TRY(upload_dd(bh, &P.bhatdd));
+    // e^{i pi num k / den} (phi0 = pi num / den) of the Bluestein rings, for
+    // the double-float ring transforms (FP64 sincospi costs more there)
+    std::vector<double2> ph(chirp_total);
+    for (auto &rp : P.pairs_h) {
+      if (rp.chirp_ofs < 0) continue;
+      for (int k = 0; k < rp.nphi; ++k) {
+        if (rp.phi_num == 0) {
+          ph[rp.chirp_ofs + k] = make_double2(1.0, 0.0);
+        } else {
+          const long long q = ((long long)k * rp.phi_num) % (2LL * rp.phi_den);
+          const double ang = M_PI * (double)q / (double)rp.phi_den;
+          ph[rp.chirp_ofs + k] = make_double2(cos(ang), sin(ang));
+        }
+      }
+    }
+    WF_TRY(upload_dd(ph, &P.phasedd));
   }
   return WF_OK;
 }
@@ -247,6 +263,16 @@ static wf_status make_recurrence_tables(Plan &P) {
   WF_CUDA(cudaMalloc(&P.rc, sizeof(double) * P.nalm));
   WF_CUDA(cudaMalloc(&P.rg, sizeof(double) * P.nalm));
   WF_CUDA(cudaMalloc(&P.rc32, sizeof(float) * P.nalm));
+  {
+    // the double-float Legendre kernels' coefficient table (hi, lo)
+    std::vector<float2> cdd(P.nalm);
+    for (long i = 0; i < P.nalm; ++i) {
+      const float h = (float)c[i];
+      cdd[i] = make_float2(h, (float)(c[i] - (double)h));
+    }
+    WF_CUDA(cudaMalloc(&P.rcdd, sizeof(float2) * P.nalm));
+    WF_CUDA(cudaMemcpy(P.rcdd, cdd.data(), sizeof(float2) * P.nalm, cudaMemcpyHostToDevice));
+  }
   WF_CUDA(cudaMalloc(&P.rg32, sizeof(float) * P.nalm));
   WF_CUDA(cudaMemcpy(P.rg32, g32.data(), sizeof(float) * P.nalm, cudaMemcpyHostToDevice));
   WF_CUDA(cudaMemcpy(P.rc, c.data(), sizeof(double) * P.nalm,
@@ -475,6 +501,8 @@ wf_status upload_noise(Plan &P, const double *nvar_dev, const uint8_t *mask_dev)
   if (!P.nvar32) WF_CUDA(cudaMalloc(&P.nvar32, sizeof(float) * P.npix));
   k_noise_f32<<<nb, 256, 0, P.stream>>>(P.nvar, P.npix, 1.0 / mn, P.nvar32);
   WF_CUDA(cudaGetLastError());
+  if (!P.nvardd) WF_CUDA(cudaMalloc(&P.nvardd, sizeof(float2) * P.npix));
+  WF_TRY(launch_to_dd(P, P.nvar, P.nvardd, P.npix));
   P.has_noise = true;
   return WF_OK;
 }

@@ -25,6 +25,8 @@
 // product with the kernel spectrum (stored bit-reversed) -> inverse DIT.
 #include <limits.h>
 
+#include <type_traits>
+
 #include "wf_internal.cuh"
 
 namespace wf {
@@ -136,8 +138,10 @@ template <> struct TwPass<double2> {
 // intrinsics, so nothing is contracted or reassociated.  The mixed solver's
 // anchor steps run their ring FFTs in it on the FP32 pipe: this part's FP64
 // pipe runs at ~1/64 of the FP32 rate, and those FFTs were FP64-bound.
-// Global data stays FP64 (converted at load and store); the twiddle, chirp
-// and kernel-spectrum tables are kept as (hi, lo) float pairs.
+// The ring coefficients F, G (written and read by the double-float Legendre
+// kernels), the twiddle, chirp, kernel-spectrum and phase tables and the
+// pixel step's d and sigma^2 are kept as (hi, lo) float pairs, so no FP64
+// arithmetic is left but the maps of the API's own FP64 input and output.
 struct ddr {
   float hi, lo;
   __device__ __forceinline__ ddr() : hi(0.f), lo(0.f) {}
@@ -173,6 +177,13 @@ __device__ __forceinline__ ddr &operator*=(ddr &a, ddr b) {
   a = a * b;
   return a;
 }
+// a / b: the quotient of the hi parts, corrected by the remainder a - q b
+// (finite b only)
+__device__ __forceinline__ ddr operator/(ddr a, ddr b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const ddr r = a - ddr(q1, 0.f) * b;
+  return ddr_norm(q1, __fdiv_rn(r.hi, b.hi));
+}
 __device__ __forceinline__ bool operator<(ddr a, ddr b) {
   return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
 }
@@ -182,18 +193,18 @@ struct ddc {
 };
 template <> struct CT<ddc> {
   typedef ddr T;
-  typedef double2 G;  // F, G stay FP64
-  typedef float4 W;   // tables as (re hi, re lo, im hi, im lo)
+  typedef float4 G;  // F, G as double-float pairs (re hi, re lo, im hi, im lo)
+  typedef float4 W;  // tables in the same form
   static __device__ __forceinline__ ddc ld(const G *p) {
-    const double2 v = *p;
-    return {ddr(v.x), ddr(v.y)};
+    const float4 v = *p;
+    return {ddr(v.x, v.y), ddr(v.z, v.w)};
   }
   static __device__ __forceinline__ ddc ldw(const W *p) {
     const float4 v = *p;
     return {ddr(v.x, v.y), ddr(v.z, v.w)};
   }
   static __device__ __forceinline__ void st(G *p, ddc v) {
-    *p = make_double2((double)v.x, (double)v.y);
+    *p = make_float4(v.x.hi, v.x.lo, v.y.hi, v.y.lo);
   }
   static __device__ __forceinline__ ddc mk(ddr a, ddr b) { return {a, b}; }
   // sin, cos of pi r / den, rounded from FP64
@@ -333,10 +344,12 @@ __device__ __forceinline__ int bitrev_n(int x, int bits) {
 // sincospi with the exact rational argument k / den.
 template <typename T2>
 __device__ __forceinline__ T2 ring_phase(int k, int num, int den, int tstep,
-                                         const typename CT<T2>::W *__restrict__ tw) {
+                                         const typename CT<T2>::W *__restrict__ tw,
+                                         const typename CT<T2>::W *__restrict__ ph) {
   typedef typename CT<T2>::T T;
   if (num == 0) return CT<T2>::mk((T)1, (T)0);
   if (tstep > 0) return cconj(CT<T2>::ldw(tw + k * tstep));
+  if (ph) return CT<T2>::ldw(ph + k);  // the ring's own phase table
   T s, c;
   CT<T2>::sincospi_(k, den, &s, &c);
   return CT<T2>::mk(c, s);
@@ -390,7 +403,9 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
            int Mmax, const typename CT<T2>::W *__restrict__ chirp_all,
            const typename CT<T2>::W *__restrict__ bhat_all,
            const SolverState *__restrict__ st, int lstatic, int reverse,
-           const float *__restrict__ in32, const float *__restrict__ nv32, int red_ofs) {
+           const float *__restrict__ in32, const float *__restrict__ nv32, int red_ofs,
+           const typename CT<T2>::W *__restrict__ phase_all,
+           const float2 *__restrict__ in_dd, const float2 *__restrict__ nv_dd) {
   typedef typename CT<T2>::T T;
   typedef typename CT<T2>::G GT;
   typedef typename CT<T2>::W WT;
@@ -422,6 +437,12 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
     xia = __shfl_sync(0xffffffffu, xia, 0);
     mua = __shfl_sync(0xffffffffu, mua, 0);
   }
+  // the double-float step's xi and mu (converted once)
+  ddr xd(0), md(0);
+  if constexpr (std::is_same<T2, ddc>::value && MODE == RING_FUSED) {
+    xd = ddr(xi);
+    md = ddr(mu);
+  }
   extern __shared__ __align__(16) unsigned char smraw[];
   T2 *buf = reinterpret_cast<T2 *>(smraw);
   const int n = rp.nphi, M = rp.fftM;
@@ -430,6 +451,7 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
   while ((1 << bits) < M) ++bits;
   const WT *chirp = blue ? chirp_all + rp.chirp_ofs : nullptr;
   const WT *bhat = blue ? bhat_all + rp.bhat_ofs : nullptr;
+  const WT *phs = (blue && phase_all) ? phase_all + rp.chirp_ofs : nullptr;
   const long stride = lmax + 1;
   const bool south = rp.ringS >= 0;
   const T2 zero = CT<T2>::mk((T)0, (T)0);
@@ -477,7 +499,7 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
           cN = cadd(cN, red[q * n + k]);
           cS = cadd(cS, red[blockDim.x + q * n + k]);
         }
-        const T2 ph = ring_phase<T2>(k, rp.phi_num, rp.phi_den, tstep, tw);
+        const T2 ph = ring_phase<T2>(k, rp.phi_num, rp.phi_den, tstep, tw, phs);
         cN = cmul(cN, ph);
         cS = cmul(cS, ph);
         const T2 Zk = CT<T2>::mk(cN.x - cS.y, cN.y + cS.x);  // cN + i cS
@@ -488,7 +510,7 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
       for (int k = threadIdx.x; k < n; k += blockDim.x) {
         T2 cN = zero, cS = zero;
         if (Lf >= 0 && (k <= Lf || n - k <= Lf)) {
-          const T2 ph = ring_phase<T2>(k, rp.phi_num, rp.phi_den, tstep, tw);
+          const T2 ph = ring_phase<T2>(k, rp.phi_num, rp.phi_den, tstep, tw, phs);
           cN = fold(FN, k, n, Lf, sgn, ph);
           if (south) cS = fold(FS, k, n, Lf, sgn, ph);
         }
@@ -521,7 +543,21 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
           if (south) out_map[pS] = sS;
         }
         T2 tt;
-        if constexpr (F32STEP) {
+        if constexpr (std::is_same<T2, ddc>::value) {
+          // double-float step on double-float copies of d and sigma^2
+          const float2 vN = nv_dd[pN];
+          const ddr wN = isinf(vN.x) ? ddr(0) : xd / (ddr(vN.x, vN.y) + md);
+          const ddr dN = in_dd ? ddr(in_dd[pN].x, in_dd[pN].y) : ddr(0);
+          const ddr tN = zz.x + wN * (dN - zz.x);
+          ddr tS(0);
+          if (south) {
+            const float2 vS = nv_dd[pS];
+            const ddr wS = isinf(vS.x) ? ddr(0) : xd / (ddr(vS.x, vS.y) + md);
+            const ddr dS = in_dd ? ddr(in_dd[pS].x, in_dd[pS].y) : ddr(0);
+            tS = zz.y + wS * (dS - zz.y);
+          }
+          tt = CT<T2>::mk(tN, tS);
+        } else if constexpr (F32STEP) {
           // 0 on masked pixels (sigma^2 / alpha = +inf)
           const float sNf = zz.x, sSf = zz.y;
           float tN = sNf + xia / (nv32[pN] + mua) * ((in32 ? in32[pN] : 0.f) - sNf);
@@ -586,7 +622,7 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
          k <= kmax; k += kstep) {
       const int kk = k == 0 ? 0 : n - k;
       const T2 X = buf[sw(k)], Xc = cconj(buf[sw(kk)]);
-      const T2 ph = cconj(ring_phase<T2>(k, rp.phi_num, rp.phi_den, tstep, tw));
+      const T2 ph = cconj(ring_phase<T2>(k, rp.phi_num, rp.phi_den, tstep, tw, phs));
       const T2 tN = cmul(CT<T2>::mk(half * (X.x + Xc.x), half * (X.y + Xc.y)), ph);
       // (X - Xc) / (2i)
       const T2 dlt = csub(X, Xc);
@@ -603,16 +639,19 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
 
 template <typename T2> struct Tables;
 template <> struct Tables<double2> {
+  static const double2 *ph(const Plan &) { return nullptr; }
   static const double2 *tw(const Plan &P) { return P.tw64; }
   static const double2 *ch(const Plan &P) { return P.chirp64; }
   static const double2 *bh(const Plan &P) { return P.bhat64; }
 };
 template <> struct Tables<float2> {
+  static const float2 *ph(const Plan &) { return nullptr; }
   static const float2 *tw(const Plan &P) { return P.tw32; }
   static const float2 *ch(const Plan &P) { return P.chirp32; }
   static const float2 *bh(const Plan &P) { return P.bhat32; }
 };
 template <> struct Tables<ddc> {
+  static const float4 *ph(const Plan &P) { return P.phasedd; }
   static const float4 *tw(const Plan &P) { return P.twdd; }
   static const float4 *ch(const Plan &P) { return P.chirpdd; }
   static const float4 *bh(const Plan &P) { return P.bhatdd; }
@@ -622,7 +661,7 @@ template <typename T2, int MODE>
 static wf_status launch_ring_mode(const Plan &P, const typename CT<T2>::G *F,
                                   typename CT<T2>::G *G, const double *in_map,
                                   double *out_map, const SolverState *st, int lstatic,
-                                  const float *in32) {
+                                  const float *in32, const float2 *in_dd = nullptr) {
   auto kern = k_ring<T2, MODE>;
   // two launches: the polar rings (pairs 0 .. nside-2, Bluestein unless n is
   // a power of two) and the equatorial belt (pairs nside-1 .. 2 nside-1);
@@ -652,7 +691,7 @@ static wf_status launch_ring_mode(const Plan &P, const typename CT<T2>::G *F,
     kern<<<e - b, threads, smem, s>>>(
         P.pairs, b, P.lmax, F, G, in_map, out_map, P.nvar, Tables<T2>::tw(P),
         P.fftMmax, Tables<T2>::ch(P), Tables<T2>::bh(P), st, lstatic, g == 0, in32,
-        P.nvar32, red_ofs);
+        P.nvar32, red_ofs, Tables<T2>::ph(P), in_dd, P.nvardd);
     WF_CUDA(cudaGetLastError());
   }
   if (fork) {
@@ -681,9 +720,9 @@ wf_status launch_ring(const Plan &P, int mode, const T2 *F, T2 *G,
   }
 }
 
-wf_status launch_ring_dd(const Plan &P, int mode, const double2 *F, double2 *G,
+wf_status launch_ring_dd(const Plan &P, int mode, const float4 *F, float4 *G,
                          const double *in_map, double *out_map, const SolverState *st,
-                         int lstatic) {
+                         int lstatic, const float2 *in_dd) {
   switch (mode) {
     case RING_SYNTH:
       return launch_ring_mode<ddc, RING_SYNTH>(P, F, G, in_map, out_map, st, lstatic,
@@ -692,9 +731,29 @@ wf_status launch_ring_dd(const Plan &P, int mode, const double2 *F, double2 *G,
       return launch_ring_mode<ddc, RING_ANALYSIS>(P, F, G, in_map, out_map, st, lstatic,
                                                   nullptr);
     default:
+      if (!P.nvardd) {
+        set_error("ring step: the plan has no noise variance");
+        return WF_ERR_STATE;
+      }
       return launch_ring_mode<ddc, RING_FUSED>(P, F, G, in_map, out_map, st, lstatic,
-                                               nullptr);
+                                               nullptr, in_dd);
   }
+}
+
+__global__ void k_to_dd(const double *__restrict__ in, float2 *__restrict__ out, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    const double v = in[i];
+    const float h = (float)v;
+    out[i] = make_float2(h, isinf(v) ? 0.f : (float)(v - (double)h));
+  }
+}
+
+wf_status launch_to_dd(const Plan &P, const double *in, float2 *out, long n) {
+  ++P.nlaunch;
+  k_to_dd<<<304, 256, 0, P.stream>>>(in, out, n);
+  WF_CUDA(cudaGetLastError());
+  return WF_OK;
 }
 
 wf_status init_ring_attributes() {

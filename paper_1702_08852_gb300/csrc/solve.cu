@@ -335,17 +335,24 @@ wf_status map2alm_f32(Plan &P, const double *map, double *alm) {
   return WF_OK;
 }
 
+// The double-float transforms keep their synthesis input and ring
+// coefficients as double-float pairs in the plan's FP64 buffers (16 bytes
+// per complex value either way).
+static float4 *dd_view(double2 *p) { return reinterpret_cast<float4 *>(p); }
+
 wf_status alm2map_df64(Plan &P, const double *alm, double *map) {
   const double2 *a = reinterpret_cast<const double2 *>(alm);
-  WF_TRY(launch_prescale<double2>(P, a, P.xs64));
-  WF_TRY(launch_legendre_synth_dd(P, P.xs64, P.F64, nullptr, P.lmax));
-  WF_TRY(launch_ring_dd(P, RING_SYNTH, P.F64, nullptr, nullptr, map, nullptr, P.lmax));
+  WF_TRY(launch_prescale_dd(P, a, dd_view(P.xs64)));
+  WF_TRY(launch_legendre_synth_dd(P, dd_view(P.xs64), dd_view(P.F64), nullptr, P.lmax));
+  WF_TRY(launch_ring_dd(P, RING_SYNTH, dd_view(P.F64), nullptr, nullptr, map, nullptr,
+                        P.lmax));
   return WF_OK;
 }
 
 wf_status map2alm_df64(Plan &P, const double *map, double *alm) {
-  WF_TRY(launch_ring_dd(P, RING_ANALYSIS, nullptr, P.G64, map, nullptr, nullptr, P.lmax));
-  WF_TRY(launch_legendre_anal_dd(P, P.G64, reinterpret_cast<double2 *>(alm), nullptr,
+  WF_TRY(launch_ring_dd(P, RING_ANALYSIS, nullptr, dd_view(P.G64), map, nullptr, nullptr,
+                        P.lmax));
+  WF_TRY(launch_legendre_anal_dd(P, dd_view(P.G64), reinterpret_cast<double2 *>(alm), nullptr,
                                  ANA_PLAIN, P.lmax));
   return WF_OK;
 }
@@ -641,7 +648,10 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
                           cudaMemcpyHostToDevice, P.stream));
   WF_CUDA(cudaMemcpyAsync(gx, x, sizeof(double2) * P.nalm, cudaMemcpyDeviceToDevice,
                           P.stream));
-  WF_TRY(launch_prescale<double2>(P, x, P.xs64));
+  if (dd)
+    WF_TRY(launch_prescale_dd(P, x, dd_view(P.xs64)));
+  else
+    WF_TRY(launch_prescale<double2>(P, x, P.xs64));
   // opts.timing: events around the double-float synthesis, ring step and
   // analysis (kernels 3, 5, 4 of wf_kernel_stats)
   const bool timed = dd && P.opts.timing;
@@ -649,12 +659,14 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
     for (auto &e : P.dd_ev) WF_CUDA(cudaEventCreate(&e));
   if (timed) WF_CUDA(cudaEventRecord(P.dd_ev[0], P.stream));
   if (dd)
-    WF_TRY(launch_legendre_synth_dd(P, P.xs64, P.F64, nullptr, std::max(L, 0)));
+    WF_TRY(launch_legendre_synth_dd(P, dd_view(P.xs64), dd_view(P.F64), nullptr,
+                                    std::max(L, 0)));
   else
     WF_TRY(launch_legendre_synth<double2>(P, P.xs64, P.F64, nullptr, std::max(L, 0)));
   if (timed) WF_CUDA(cudaEventRecord(P.dd_ev[1], P.stream));
   if (dd)
-    WF_TRY(launch_ring_dd(P, RING_FUSED, P.F64, P.G64, P.dmap, nullptr, P.state, P.lmax));
+    WF_TRY(launch_ring_dd(P, RING_FUSED, dd_view(P.F64), dd_view(P.G64), nullptr, nullptr,
+                          P.state, P.lmax, P.dmapdd));
   else
     WF_TRY(launch_ring<double2>(P, RING_FUSED, P.F64, P.G64, P.dmap, nullptr, P.state,
                                 P.lmax));
@@ -663,7 +675,7 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
   if (U) {
     const int Lb = std::max(L, Lu);
     if (dd)
-      WF_TRY(launch_legendre_anal_dd(P, P.G64, U, nullptr, ANA_PLAIN, Lb));
+      WF_TRY(launch_legendre_anal_dd(P, dd_view(P.G64), U, nullptr, ANA_PLAIN, Lb));
     else
       WF_TRY(launch_legendre_anal<double2>(P, P.G64, U, nullptr, ANA_PLAIN, Lb));
     ++P.nlaunch;
@@ -672,7 +684,7 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
                                                       P.lmax, gx, P.partials);
     WF_CUDA(cudaGetLastError());
   } else if (dd) {
-    WF_TRY(launch_legendre_anal_dd(P, P.G64, gx, P.state, ANA_FILTER, P.lmax));
+    WF_TRY(launch_legendre_anal_dd(P, dd_view(P.G64), gx, P.state, ANA_FILTER, P.lmax));
   } else {
     WF_TRY(launch_legendre_anal<double2>(P, P.G64, gx, P.state, ANA_FILTER, P.lmax));
   }
@@ -912,6 +924,7 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
   ++P.nlaunch;
   k_mask_data<<<304, 256, 0, P.stream>>>(d, P.nvar, P.npix, P.dmap);
   WF_CUDA(cudaGetLastError());
+  WF_TRY(launch_to_dd(P, P.dmap, P.dmapdd, P.npix));  // the double-float ring steps' d
   if (init_alm)
     WF_CUDA(cudaMemcpyAsync(P.x, init_alm, sizeof(double2) * P.nalm,
                             cudaMemcpyDeviceToDevice, P.stream));

@@ -148,6 +148,7 @@ struct Plan {
   double *rc = nullptr;          // [nalm] recurrence coefficient c_lm
   double *rg = nullptr;          // [nalm] scale g_lm (lambda = g u)
   float *rc32 = nullptr;         // [nalm] FP32 copy of rc
+  float2 *rcdd = nullptr;        // [nalm] rc as double-float pairs (hi, lo)
   int *seed_l = nullptr;         // [lmax+1][npairs] first l with |lambda| >= 2^-100
   double2 *seed_u = nullptr;     // [lmax+1][npairs] (u_ls, u_ls+1)
   // FP32 kernels' tables (no FP64 arithmetic left in their tile loads and
@@ -192,6 +193,8 @@ struct Plan {
   // the same three tables as double-float pairs (re hi, re lo, im hi, im lo)
   // for the double-float ring transforms of the anchor steps
   float4 *twdd = nullptr, *chirpdd = nullptr, *bhatdd = nullptr;
+  // e^{i pi k / n} of every Bluestein ring (phi0 = pi / n), chirp layout
+  float4 *phasedd = nullptr;
   long chirp_total = 0, bhat_total = 0;
 
   // noise
@@ -199,6 +202,7 @@ struct Plan {
   double alpha = 0.0;
   double *nvar = nullptr;        // [npix] sigma^2, +inf on masked pixels
   float *nvar32 = nullptr;       // [npix] sigma^2 / alpha in FP32 (FP32 ring step)
+  float2 *nvardd = nullptr;      // [npix] sigma^2 as double-float (hi, lo); (+inf, 0) masked
 
   // work buffers
   double2 *F64 = nullptr, *G64 = nullptr;   // [nring][lmax+1]
@@ -216,6 +220,7 @@ struct Plan {
   std::vector<int> untimed;      // iterations run outside the timed graphs
   double *dmap = nullptr;        // [npix] data with masked pixels zeroed
   float *dmap32 = nullptr;       // [npix] FP32 copy of dmap (FP32 ring step)
+  float2 *dmapdd = nullptr;      // [npix] dmap as double-float (double-float ring step)
   int data_iters = 0;            // iterations of the last solve that read d
   double *mtmp = nullptr;        // [npix]
   double *partials = nullptr;    // [lmax+1][2]
@@ -277,9 +282,14 @@ wf_status launch_legendre_anal(const Plan &P, const T2 *G, double2 *x,
 // Double-float (pairs of FP32) Legendre transforms with FP64 inputs and
 // outputs, for the anchor steps of the mixed solver (legendre.cu): the same
 // contracts as launch_legendre_synth<double2> / launch_legendre_anal<double2>.
-wf_status launch_legendre_synth_dd(const Plan &P, const double2 *xs, double2 *F,
+// Their ring coefficients F, G and the synthesis input are double-float
+// pairs (re hi, re lo, im hi, im lo), 16 bytes like an FP64 complex (the
+// plan's F64 / G64 / xs64 buffers hold them in this form), the format of the
+// double-float ring transforms.
+wf_status launch_prescale_dd(const Plan &P, const double2 *x, float4 *xs);
+wf_status launch_legendre_synth_dd(const Plan &P, const float4 *xs, float4 *F,
                                    const SolverState *st, int lstatic);
-wf_status launch_legendre_anal_dd(const Plan &P, const double2 *G, double2 *x,
+wf_status launch_legendre_anal_dd(const Plan &P, const float4 *G, double2 *x,
                                   const SolverState *st, int mode, int lstatic,
                                   const double2 *src = nullptr, double2 *xs_out = nullptr);
 
@@ -299,9 +309,11 @@ wf_status launch_ring(const Plan &P, int mode, const T2 *F, T2 *G,
                       const float *in32 = nullptr);
 // The FP64 ring transforms (FP64 F, G, maps) computed in double-float
 // arithmetic on the FP32 pipe (the anchor steps' arithmetic).
-wf_status launch_ring_dd(const Plan &P, int mode, const double2 *F, double2 *G,
+wf_status launch_ring_dd(const Plan &P, int mode, const float4 *F, float4 *G,
                          const double *in_map, double *out_map, const SolverState *st,
-                         int lstatic);
+                         int lstatic, const float2 *in_dd = nullptr);
+// FP64 map -> double-float pairs (hi, lo); +inf -> (+inf, 0)
+wf_status launch_to_dd(const Plan &P, const double *in, float2 *out, long n);
 
 // once per plan (kernel attributes; allowed outside stream capture only)
 wf_status init_legendre_attributes();
