@@ -120,9 +120,13 @@ __global__ void __launch_bounds__(CTRL_THREADS)
       st->since_min += 1;
     }
     const bool plateau = st->noise_guard && st->since_min >= PLATEAU_ITERS && c < 1e-3;
+    const double thr = st->mu == 0.0 ? st->eps_final : st->eps_k;
     if (!isfinite(c) || !isfinite(num)) {
       st->numeric_error = 1;
       st->done = 1;
+    } else if (anchored && st->window_factor > 0.0 && c < thr * st->window_factor) {
+      st->done = 1;  // near the stage's decision: the anchor arithmetic decides
+      st->at_window = 1;
     } else if (st->mu == 0.0) {
       // arithmetic noise floor: the Cauchy ratio has stopped falling
       st->flat = (st->prev_c > 0.0 && c >= st->prev_c) ? st->flat + 1 : 0;
@@ -993,13 +997,16 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
     // taken here in the anchor arithmetic (boundary_step), from the
     // accumulated iterate x_a + delta; the new stage then anchors at it.
     bool boundary = h.at_boundary != 0;
+    bool tail_dd = false;  // the tail stage's decision is being taken in the anchor arithmetic
     while (anchored && reanchors <= MAX_REANCHORS && cycles <= P.opts.refine_max) {
       if (boundary) {
         WF_TRY(boundary_step(P, h, &total_iter));
         boundary = false;
+        tail_dd = false;
       }
-      if (P.opts.tail_exact && h.eps_k <= P.opts.eps_final &&
-          P.opts.stop_rule == WF_STOP_CAUCHY) {
+      const bool tail = P.opts.tail_exact && h.eps_k <= P.opts.eps_final &&
+                        P.opts.stop_rule == WF_STOP_CAUCHY;
+      if (tail && (tail_dd || !(P.opts.tail_window > 0.0))) {
         // the tail stages (each one's tolerance is eps_final)
         // iterate in the anchor arithmetic, so that their Cauchy tests see
         // the step to FP64 accuracy
@@ -1056,6 +1063,9 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       s.rate_floor = stage.mu == 0.0 ? rate_floor : 0.0;
       s.noise_guard = 1;
       s.boundary_stop = 1;
+      // a tail stage runs FP32 corrections until its Cauchy ratio is within
+      // tail_window of the threshold; the anchor arithmetic takes the decision
+      s.window_factor = tail ? 1.0 + P.opts.tail_window : 0.0;
       h = s;
       WF_CUDA(cudaMemcpyAsync(P.state, P.state_h, sizeof(SolverState),
                               cudaMemcpyHostToDevice, P.stream));
@@ -1071,6 +1081,11 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       k_alm_add<<<304, 256, 0, P.stream>>>(P.xacc, P.x, P.nalm);
       WF_CUDA(cudaGetLastError());
       ++refinements;
+      if (h.at_window) {  // same stage: iterate it in the anchor arithmetic
+        h.at_window = 0;
+        tail_dd = true;
+        continue;
+      }
       boundary = h.at_boundary != 0;
       if (h.at_boundary) continue;  // next stage: h holds its parameters
       if (h.reanchor || (h.stagnated && h.mu == 0.0)) {

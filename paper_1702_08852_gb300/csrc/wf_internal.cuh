@@ -99,6 +99,11 @@ struct SolverState {
   double xi_prev, mu_prev;
   int lcur_prev;
   int messenger;  // 1: the standard messenger (Algorithm 1), xi = lambda alpha
+  // anchored tail stage: stop (at_window) once the Cauchy ratio falls below
+  // window_factor times the stage's threshold, without a stage decision
+  // (the anchor arithmetic takes over for it); 0 = off
+  double window_factor;
+  int at_window;
 };
 
 // Tolerance of the stage at mu (pixel units): Algorithm 2 relaxes it as
