@@ -133,6 +133,10 @@ typedef struct {
                         iterations to its decision; <= 0: the whole tail in
                         the anchor arithmetic (default 0.08, above the FP32
                         ratio's measured error of 2.4 % there). */
+  double tail_cap_tol; /* with tail_window > 0: the re-anchoring bound of the
+                        tail stages' FP32 corrections, tail_cap_tol times
+                        the stage tolerance (default 10): their trajectory
+                        error moves the late steps the decisions read */
 } wf_opts;
 
 /* Per-solve statistics. */

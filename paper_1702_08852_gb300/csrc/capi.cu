@@ -120,6 +120,7 @@ static wf_status check_opts(const wf_opts &o) {
     return arg_error("wf: anchor_eps must be >= 0 and anchor_cap in (0, 1]");
   if (o.tail_exact != 0 && o.tail_exact != 1) return arg_error("wf: tail_exact must be 0 or 1");
   if (!(o.tail_window < 10.0)) return arg_error("wf: tail_window must be < 10");
+  if (!(o.tail_cap_tol >= 0.0)) return arg_error("wf: tail_cap_tol must be >= 0");
   if (!(o.anchor_cap_tol >= 0.0)) return arg_error("wf: anchor_cap_tol must be >= 0");
   if (o.method != WF_METHOD_DUAL && o.method != WF_METHOD_MESSENGER)
     return arg_error("wf: unknown method");
@@ -153,6 +154,7 @@ void wf_opts_default(wf_opts *o) {
   o->anchor_cap_tol = 100.0;
   o->tail_exact = 1;
   o->tail_window = 0.08;
+  o->tail_cap_tol = 10.0;
   o->method = WF_METHOD_DUAL;
   o->lambda0 = 1e4;
 }

@@ -1059,6 +1059,8 @@ wf_status solve(Plan &P, const double *d, double *alm, double *map,
       // scales with ||delta||, and late stages take steps of ~eps_k ||x||)
       double cap = P.opts.anchor_cap;
       if (P.opts.anchor_cap_tol > 0.0) cap = std::min(cap, P.opts.anchor_cap_tol * stage.eps_k);
+      if (tail && P.opts.tail_cap_tol > 0.0)
+        cap = std::min(cap, P.opts.tail_cap_tol * stage.eps_k);
       s.delta_cap2 = cap * cap * xn;
       s.rate_floor = stage.mu == 0.0 ? rate_floor : 0.0;
       s.noise_guard = 1;

@@ -41,7 +41,7 @@ class wf_opts(ctypes.Structure):
                 ("anchor", ctypes.c_int), ("anchor_eps", ctypes.c_double),
                 ("anchor_cap", ctypes.c_double), ("anchor_cap_tol", ctypes.c_double), ("method", ctypes.c_int),
                 ("lambda0", ctypes.c_double), ("tail_exact", ctypes.c_int),
-                ("tail_window", ctypes.c_double)]
+                ("tail_window", ctypes.c_double), ("tail_cap_tol", ctypes.c_double)]
 
 
 class wf_stats(ctypes.Structure):
