@@ -104,15 +104,16 @@ typedef struct {
                         0: plain FP64.  The last stage's acceptance test
                         and fp_residual always use plain FP64. */
   /* WF_PREC_MIXED anchoring.  The defaults reproduce the FP64 solve's
-     result (same stage lengths; ~5e-8 relative L2 at nside 1024, lmax 2048):
-     every stage anchored, a re-anchoring bound tied to the stage tolerance,
-     tail stages in the anchor arithmetic.  FP32 transforms err by ~1e-5 of
-     their input's norm, while late-stage steps are ~1e-3 of the correction
-     they act on; without these the late stages' Cauchy tests, whose
-     thresholds the FP64 ratios cross within 1e-4, can end a stage one or
-     two iterations off.  anchor_eps = 3e-5, anchor_cap_tol = 0,
-     tail_exact = 0 is ~2x faster with ~1e-5 distance from the FP64 result
-     (both sit ~1e-2 from the fixed point under the paper's criterion). */
+     result (same stage lengths; 1.9e-7 relative L2 at nside 1024, lmax
+     2048; 5.7e-8 at nside 256): every stage anchored, re-anchoring bounds
+     tied to the stage tolerance, the tail stages' decisions taken in the
+     anchor arithmetic.  FP32 transforms err by ~1e-5 of their input's norm,
+     while late-stage steps are ~1e-3 of the correction they act on; without
+     these the late stages' Cauchy tests, whose thresholds the FP64 ratios
+     cross within 1e-4, can end a stage one or two iterations off.
+     anchor_eps = 3e-5, anchor_cap_tol = 0, tail_exact = 0 is ~1.3x faster
+     with ~1e-5 distance from the FP64 result (both sit ~1e-2 from the
+     fixed point under the paper's criterion). */
   double anchor_eps; /* stages whose tolerance is below anchor_eps run
                         anchored (correction form around an FP64 anchor);
                         the others run plain FP32 iterations.  >= eps_cap
