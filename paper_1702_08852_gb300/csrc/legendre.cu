@@ -416,6 +416,36 @@ __device__ __forceinline__ T transpose_reduce32(T (&v)[32], int lane) {
   return v[0];
 }
 
+// Cross-lane sum of NV FP32 values per lane through shared memory, the same
+// totals as transpose_reduce<float, NV> (lane holds the total of value index
+// lane / (32 / NV)): each lane stores its NV values as one row (16-byte
+// stores; the row stride NV + 4 floats keeps them conflict-free), then sums
+// one column over its share of the rows (the lanes sharing a column start at
+// rotated rows, so they read different banks), then the shares by shuffles.
+// 4 stores, NV loads and NV adds per lane per chunk, against the shuffle
+// transpose's NV shuffles, NV adds and ~2 NV selects.  sb: this warp's
+// 32 x (NV + 4) floats.
+constexpr bool ANA_SMEM_REDUCE = true;
+template <int NV>
+__device__ __forceinline__ float smem_reduce(const float (&v)[NV], int lane, float *sb) {
+  constexpr int STR = NV + 4;
+  constexpr int R = 32 / NV;  // lanes per total
+  constexpr int S = NV;       // rows each of them sums (32 / R)
+  __syncwarp();               // the previous chunk's reads are done
+  float4 *row = reinterpret_cast<float4 *>(sb + lane * STR);
+#pragma unroll
+  for (int q = 0; q < NV / 4; ++q)
+    row[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  __syncwarp();
+  const int o = lane / R, sub = lane % R;
+  float acc = 0.f;
+#pragma unroll
+  for (int k = 0; k < S; ++k) acc += sb[(sub * S + ((k + sub) % S)) * STR + o];
+#pragma unroll
+  for (int sh = R / 2; sh >= 1; sh >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sh);
+  return acc;
+}
+
 // One chunk of LCHUNK consecutive l for NP ring pairs per lane: v[2 jj] and
 // v[2 jj + 1] receive this lane's contribution (re, im) to a_{lc+jj, m}.
 // INJ: some lane of the warp still has its seed (ls, ls + 1) in or after this
@@ -793,7 +823,13 @@ __device__ __forceinline__ void
         else
           anal_chunk<T, NP, false, false, X2, LC, SS>(v, lc, L, m, sc, zh, zl, u1, u2, s0,
                                                       s1, ls, pr, pim, qr, qim, ssm);
-        const T tot = transpose_reduce<T, 2 * LC>(v, lane);
+        T tot;
+        if constexpr (sizeof(T) == 4 && ANA_SMEM_REDUCE) {
+          __shared__ __align__(16) float red_sm[ANA_WARPS][32 * (2 * LC + 4)];
+          tot = smem_reduce<2 * LC>(v, lane, red_sm[warp]);
+        } else {
+          tot = transpose_reduce<T, 2 * LC>(v, lane);
+        }
         if (writer && lmine <= L) {
           if constexpr (GACC)
             *mine = old + tot;
