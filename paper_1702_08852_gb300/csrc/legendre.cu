@@ -1606,8 +1606,20 @@ static cudaError_t set_big_smem_synth(int big) {
 }
 template <typename T, int NP, bool X2 = false, bool GACC = false, int LC = LCHUNK>
 static cudaError_t set_big_smem_anal(int big) {
+  // the dynamic share leaves room for the kernel's static shared memory
+  // (the FP32 kernels' reduction buffer) under the per-block limit
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, k_legendre_anal<T, NP, X2, GACC, LC>);
+  if (e != cudaSuccess) return e;
+  int dev = 0, optin = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
+      cudaSuccess)
+    return e;
+  const int room = optin - (int)fa.sharedSizeBytes;
   return cudaFuncSetAttribute(k_legendre_anal<T, NP, X2, GACC, LC>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              big < room ? big : room);
 }
 
 wf_status init_legendre_attributes() {
