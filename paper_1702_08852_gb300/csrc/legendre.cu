@@ -1599,17 +1599,13 @@ wf_status launch_legendre_anal_dd(const Plan &P, const float4 *G, double2 *x,
   return WF_OK;
 }
 
-template <typename T, int NP, bool X2 = false, bool DUP = false>
-static cudaError_t set_big_smem_synth(int big) {
-  return cudaFuncSetAttribute(k_legendre_synth<T, NP, X2, DUP>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-}
-template <typename T, int NP, bool X2 = false, bool GACC = false, int LC = LCHUNK>
-static cudaError_t set_big_smem_anal(int big) {
-  // the dynamic share leaves room for the kernel's static shared memory
-  // (the FP32 kernels' reduction buffer) under the per-block limit
+// Dynamic shared memory limit of a kernel: `big`, less what its own static
+// shared memory (the FP32 analysis kernels' reduction buffer) takes of the
+// per-block limit.
+template <typename K>
+static cudaError_t set_dyn_smem(K kern, int big) {
   cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, k_legendre_anal<T, NP, X2, GACC, LC>);
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
   if (e != cudaSuccess) return e;
   int dev = 0, optin = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -1617,9 +1613,18 @@ static cudaError_t set_big_smem_anal(int big) {
       cudaSuccess)
     return e;
   const int room = optin - (int)fa.sharedSizeBytes;
-  return cudaFuncSetAttribute(k_legendre_anal<T, NP, X2, GACC, LC>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               big < room ? big : room);
+}
+
+template <typename T, int NP, bool X2 = false, bool DUP = false>
+static cudaError_t set_big_smem_synth(int big) {
+  return set_dyn_smem(k_legendre_synth<T, NP, X2, DUP>, big);
+}
+
+template <typename T, int NP, bool X2 = false, bool GACC = false, int LC = LCHUNK>
+static cudaError_t set_big_smem_anal(int big) {
+  return set_dyn_smem(k_legendre_anal<T, NP, X2, GACC, LC>, big);
 }
 
 wf_status init_legendre_attributes() {
@@ -1649,16 +1654,11 @@ wf_status init_legendre_attributes() {
   WF_CUDA((set_big_smem_anal<float, 8, true, true, 8>(big)));
   WF_CUDA((set_big_smem_anal<float, 6, true, true, 8>(big)));
   WF_CUDA((set_big_smem_anal<float, 4, true, true, 8>(big)));
-  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_ss<8>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  WF_CUDA(cudaFuncSetAttribute(k_legendre_synth_dd,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_dd,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_q<float, 4>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  WF_CUDA(cudaFuncSetAttribute(k_legendre_anal_q<float, 8>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  WF_CUDA(set_dyn_smem(k_legendre_anal_ss<8>, big));
+  WF_CUDA(set_dyn_smem(k_legendre_synth_dd, big));
+  WF_CUDA(set_dyn_smem(k_legendre_anal_dd, big));
+  WF_CUDA(set_dyn_smem(k_legendre_anal_q<float, 4>, big));
+  WF_CUDA(set_dyn_smem(k_legendre_anal_q<float, 8>, big));
   return WF_OK;
 }
 
