@@ -649,9 +649,20 @@ def run_batch(args, rank, world):
     times, stats = [], None
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        _, _, stats, ms = wf.wf_solve_batch(plans, ds, want_alm=True)
+        alms, _, stats, ms = wf.wf_solve_batch(plans, ds, want_alm=True)
         times.append(ms)
     clk = clocks.stop()
+    # each map's distance from its own plain FP64 solve (untimed)
+    rels = []
+    if not args.no_fp64:
+        for p, plan, d, a in zip(probs, plans, ds, alms):
+            nv = torch.from_numpy(p.noise_var).to(dev)
+            mk = torch.from_numpy(p.mask.astype(np.uint8)).to(dev)
+            with wf.Plan(p.nside, p.lmax, p.cl, nv, mk, precision=wf.WF_PREC_FP64,
+                         eps_final=args.eps, autotune=1) as p64:
+                _, m64, _ = p64.solve(d)
+                mm = plan.alm2map(a)
+            rels.append(float(torch.linalg.norm(mm - m64) / torch.linalg.norm(m64)))
     for p in plans:
         p.close()
     total_ms = max_over_ranks(sum(times))
@@ -671,7 +682,9 @@ def run_batch(args, rank, world):
             "per_map": {"iterations_max": max(s["iterations"] for s in stats),
                         "iterations_mean": sum(s["iterations"] for s in stats) / nmaps,
                         "fp64_cauchy_max": max(s["fp_residual"] for s in stats),
-                        "converged": sum(s["converged"] for s in stats)},
+                        "converged": sum(s["converged"] for s in stats),
+                        "vs_fp64_rel_l2_max": max(rels) if rels else None,
+                        "vs_fp64_rel_l2_mean": sum(rels) / len(rels) if rels else None},
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
             "clocks": clk}
 
