@@ -292,6 +292,46 @@ wf_status wf_map2alm_f32(wf_plan_t plan, const double *map_dev, double *alm_dev)
 wf_status wf_alm2map_df64(wf_plan_t plan, const double *alm_dev, double *map_dev);
 wf_status wf_map2alm_df64(wf_plan_t plan, const double *map_dev, double *alm_dev);
 
+/* Grouped transforms: the same two transforms (Sect. 2.2's Y and Omega Y^T)
+ * of nmaps maps that share the plan's geometry, in one pass of the Legendre
+ * step.  For each m, the Legendre step of all maps is one dense product of
+ * a table lambda_lm(z_ring) with the maps' ring coefficients (2 columns per
+ * map, real and imaginary parts).  It runs on the tensor cores (tcgen05,
+ * TF32 operands split hi + lo, three products per term, FP32 accumulation),
+ * so the accuracy is about that of wf_alm2map_f32 / wf_map2alm_f32.  The
+ * ring FFTs are the FP32 ones of those two calls.
+ *  maps_dev  nmaps x Npix doubles, map b at offset b * Npix.
+ *  alm_dev   nmaps x Nalm complex (2 doubles each), map b at offset
+ *            b * 2 * Nalm doubles, layout as for wf_solve.
+ *  nmaps     >= 0; up to 128 maps go into one product, and more are done
+ *            in groups of 128.  0 does nothing.
+ * The first call builds the table on the device: about 16 bytes per
+ * (l, m, ring pair), twice (one copy laid out for each direction; ~1.1 GB
+ * at Nside 256, lmax 512).  Its operand buffers are sized for the largest
+ * group seen.  Both stay until wf_destroy.  Host-synchronous.  Errors:
+ * WF_ERR_ARG for nmaps < 0 or a NULL buffer with nmaps > 0; WF_ERR_CUDA
+ * (e.g. out of device memory); WF_ERR_TIMEOUT if a device barrier wait gave
+ * up. */
+wf_status wf_map2alm_group(wf_plan_t plan, int nmaps, const double *maps_dev,
+                           double *alm_dev);
+wf_status wf_alm2map_group(wf_plan_t plan, int nmaps, const double *alm_dev,
+                           double *maps_dev);
+
+/* Device time and work of the grouped transforms' tensor-core
+ * contractions since plan creation or the last reset.
+ *  ms        summed CUDA-event time of the contraction launches.
+ *  launches  number of contraction launches.
+ *  gflop     algorithmic work: 2 flops per (l, m, ring pair, column) of
+ *            the plain product.  This is before the 3x of the split
+ *            products.
+ *  gbyte     bytes the launches must move: both tables' hi and lo parts of
+ *            the rows the tiles hold, the maps' operands once, the results
+ *            once.
+ * Any output pointer may be NULL; reset != 0 zeroes the counters after
+ * reading. */
+wf_status wf_group_stats(wf_plan_t plan, double *ms, long *launches, double *gflop,
+                         double *gbyte, int reset);
+
 /* Sizes of a plan. */
 long wf_npix(int nside);
 long wf_nalm(int lmax);

@@ -14,8 +14,8 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libwf.so")
-SOURCES = ["plan.cu", "legendre.cu", "ringfft.cu", "solve.cu", "capi.cu", "noalloc.cu", "autotune.cu", "batch.cu", "nn.cu", "peak.cu", "pcg.cu", "flatsky.cu"]
-HEADERS = ["wf_internal.cuh"]
+SOURCES = ["plan.cu", "legendre.cu", "ringfft.cu", "solve.cu", "capi.cu", "noalloc.cu", "autotune.cu", "batch.cu", "nn.cu", "peak.cu", "pcg.cu", "flatsky.cu", "group.cu"]
+HEADERS = ["wf_internal.cuh", "tc05.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

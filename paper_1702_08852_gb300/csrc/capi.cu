@@ -27,6 +27,7 @@ static wf_status arg_error(const char *msg) {
 
 static void free_plan(wf_plan_s *P) {
   if (!P) return;
+  free_group(*P);
   for (int i = 0; i < 3; ++i)
     if (P->graph[i]) cudaGraphExecDestroy(P->graph[i]);
   void *bufs[] = {P->pairs, P->cl_d,   P->rc,      P->rg,     P->rc32,   P->seed_l,
@@ -379,6 +380,40 @@ wf_status wf_map2alm_f32(wf_plan_t plan, const double *map_dev, double *alm_dev)
   if (!alm_dev || !map_dev) return arg_error("wf_map2alm_f32: NULL buffer");
   WF_TRY(map2alm_f32(*plan, map_dev, alm_dev));
   WF_CUDA(cudaStreamSynchronize(plan->stream));
+  return WF_OK;
+}
+
+wf_status wf_map2alm_group(wf_plan_t plan, int nmaps, const double *maps_dev,
+                           double *alm_dev) {
+  if (!plan) return arg_error("wf_map2alm_group: plan is NULL");
+  if (nmaps < 0) return arg_error("wf_map2alm_group: nmaps must be >= 0");
+  if (nmaps > 0 && (!maps_dev || !alm_dev)) return arg_error("wf_map2alm_group: NULL buffer");
+  WF_TRY(map2alm_group(*plan, nmaps, maps_dev, alm_dev));
+  WF_CUDA(cudaStreamSynchronize(plan->stream));
+  return WF_OK;
+}
+
+wf_status wf_alm2map_group(wf_plan_t plan, int nmaps, const double *alm_dev,
+                           double *maps_dev) {
+  if (!plan) return arg_error("wf_alm2map_group: plan is NULL");
+  if (nmaps < 0) return arg_error("wf_alm2map_group: nmaps must be >= 0");
+  if (nmaps > 0 && (!maps_dev || !alm_dev)) return arg_error("wf_alm2map_group: NULL buffer");
+  WF_TRY(alm2map_group(*plan, nmaps, alm_dev, maps_dev));
+  WF_CUDA(cudaStreamSynchronize(plan->stream));
+  return WF_OK;
+}
+
+wf_status wf_group_stats(wf_plan_t plan, double *ms, long *launches, double *gflop,
+                         double *gbyte, int reset) {
+  if (!plan) return arg_error("wf_group_stats: plan is NULL");
+  if (ms) *ms = plan->group_ms;
+  if (launches) *launches = plan->group_launches;
+  if (gflop) *gflop = plan->group_flop * 1e-9;
+  if (gbyte) *gbyte = plan->group_bytes * 1e-9;
+  if (reset) {
+    plan->group_ms = plan->group_flop = plan->group_bytes = 0.0;
+    plan->group_launches = 0;
+  }
   return WF_OK;
 }
 

@@ -262,6 +262,12 @@ struct Plan {
   // algorithmic work of the timed launches: flops (0, 1), DRAM bytes (2)
   double kern_flop[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   std::vector<double> work_cache;    // reduced (l, m, ring-pair) count per band
+
+  // grouped transforms (group.cu): tables and operands, built by the first
+  // call; time, algorithmic flops and operand bytes of their contractions
+  struct GroupState *group = nullptr;
+  double group_ms = 0.0, group_flop = 0.0, group_bytes = 0.0;
+  long group_launches = 0;
   std::vector<int> seed_l_h;         // host copy of seed_l
 };
 
@@ -352,6 +358,13 @@ wf_status residual_static(Plan &P, const double *d, const double *alm, double *r
                           double *res_fp, double *chi2);
 // real-basis inner product of two alm (fixed-order reduction, host result)
 wf_status alm_dot_host(Plan &P, const double2 *a, const double2 *b, double *res);
+
+// group.cu: Legendre transforms of nmaps maps of this geometry at once
+// (maps [nmaps][npix], alm [nmaps][nalm] complex), contracted on the
+// tensor cores; free_group releases their tables
+wf_status map2alm_group(Plan &P, int nmaps, const double *maps, double *alm);
+wf_status alm2map_group(Plan &P, int nmaps, const double *alm, double *maps);
+void free_group(Plan &P);
 
 // pcg.cu
 wf_status pcg(Plan &P, const double *d, double *alm, double *map, double tol, int stop_rule,

@@ -97,6 +97,10 @@ def lib():
             "wf_map2alm_f32": (I, [_P, _P, _P]),
             "wf_alm2map_df64": (I, [_P, _P, _P]),
             "wf_map2alm_df64": (I, [_P, _P, _P]),
+            "wf_map2alm_group": (I, [_P, I, _P, _P]),
+            "wf_alm2map_group": (I, [_P, I, _P, _P]),
+            "wf_group_stats": (I, [_P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_long),
+                                   ctypes.POINTER(D), ctypes.POINTER(D), I]),
             "wf_npix": (ctypes.c_long, [I]),
             "wf_nalm": (ctypes.c_long, [I]),
             "wf_trace": (I, [_P, ctypes.POINTER(I), _P, _P, _P, _P]),
@@ -358,6 +362,37 @@ class Plan:
                                      _dev_ptr(out, torch.complex128, self.nalm, "alm")))
         return out
 
+    def map2alm_group(self, maps, out=None):
+        """alm of each row of maps ([nmaps, npix] float64) in one grouped
+        pass (tensor-core Legendre contraction); returns [nmaps, nalm]."""
+        import torch
+        nm = maps.shape[0]
+        if out is None:
+            out = torch.empty((nm, self.nalm), dtype=torch.complex128, device=maps.device)
+        _check(lib().wf_map2alm_group(self.handle, int(nm),
+                                      _dev_ptr(maps, torch.float64, nm * self.npix, "maps"),
+                                      _dev_ptr(out, torch.complex128, nm * self.nalm, "alm")))
+        return out
+
+    def alm2map_group(self, alm, out=None):
+        """maps of each row of alm ([nmaps, nalm] complex128) in one grouped
+        pass; returns [nmaps, npix]."""
+        import torch
+        nm = alm.shape[0]
+        if out is None:
+            out = torch.empty((nm, self.npix), dtype=torch.float64, device=alm.device)
+        _check(lib().wf_alm2map_group(self.handle, int(nm),
+                                      _dev_ptr(alm, torch.complex128, nm * self.nalm, "alm"),
+                                      _dev_ptr(out, torch.float64, nm * self.npix, "maps")))
+        return out
+
+    def group_stats(self, reset=False):
+        ms, n = ctypes.c_double(), ctypes.c_long()
+        gf, gb = ctypes.c_double(), ctypes.c_double()
+        _check(lib().wf_group_stats(self.handle, ctypes.byref(ms), ctypes.byref(n),
+                                    ctypes.byref(gf), ctypes.byref(gb), int(reset)))
+        return {"ms": ms.value, "launches": n.value, "gflop": gf.value, "gbytes": gb.value}
+
     def trace(self, cap=1 << 20):
         n = ctypes.c_int(cap)
         st = np.empty(cap, dtype=np.int32)
@@ -545,6 +580,18 @@ def wf_alm2map_f32(plan, alm, out=None):
 
 def wf_map2alm_f32(plan, m, out=None):
     return plan.map2alm_f32(m, out)
+
+
+def wf_map2alm_group(plan, maps, out=None):
+    return plan.map2alm_group(maps, out)
+
+
+def wf_alm2map_group(plan, alm, out=None):
+    return plan.alm2map_group(alm, out)
+
+
+def wf_group_stats(plan, reset=False):
+    return plan.group_stats(reset)
 
 
 def wf_alm2map_df64(plan, alm, out=None):
