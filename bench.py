@@ -60,10 +60,14 @@ def parse():
     ap.add_argument("--profile-solve", action="store_true",
                     help="one warm-up solve, then one solve inside the NVTX range "
                          "'solve' (for a bounded profiler launch list) and exit")
-    ap.add_argument("--workload", choices=["nside1024", "batch64", "learned", "flat512"],
+    ap.add_argument("--group-maps", type=int, default=64,
+                    help="group_sht: maps per grouped transform pair")
+    ap.add_argument("--workload", choices=["nside1024", "batch64", "learned", "flat512",
+                                           "group_sht"],
                     default="nside1024",
                     help="batch64: 64 maps, Nside drawn from {64, 128, 256}, solved "
-                         "together (maps/s)")
+                         "together (maps/s); group_sht: the grouped tensor-core "
+                         "transforms of --group-maps maps at --nside (256 unless given)")
     return ap.parse_args()
 
 
@@ -793,6 +797,102 @@ def run_learned(args, rank, world):
                      "per_map": rows}}
 
 
+def run_group(args, rank, world):
+    """The grouped transforms: --group-maps maps of one geometry (Nside 256,
+    lmax 512 unless --nside is given), one step = alm2map_group then
+    map2alm_group of the whole group; beside it the per-map FP32 transforms
+    of the same maps, and the tensor-core contraction's own roofline."""
+    import numpy as np
+    import torch
+    from paper_1702_08852_gb300 import inputs, wf
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    ns = args.nside if args.nside != 1024 else 256
+    lm, nm = 2 * ns, args.group_maps
+    cl = inputs.cl_spectrum(lm, ns)
+    rng = np.random.default_rng(4000 + rank)
+    a = np.stack([inputs.random_alm(rng, np.maximum(cl, 1e-30)) for _ in range(nm)])
+    a *= rng.uniform(0.5, 2.0, nm)[:, None]
+    peaks, peak_src = measured_peaks()
+    with wf.Plan(ns, lm, cl, autotune=1) as p:
+        ad = torch.from_numpy(a).to(dev)
+        t0 = time.perf_counter()
+        mg = p.alm2map_group(ad)          # builds the tables
+        build_s = time.perf_counter() - t0
+        ag = p.map2alm_group(mg)
+        for _ in range(args.warmup):
+            p.alm2map_group(ad, mg)
+            p.map2alm_group(mg, ag)
+        p.group_stats(reset=True)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(dev.index)
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            p.alm2map_group(ad, mg)
+            p.map2alm_group(mg, ag)
+        e1.record()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        gs = p.group_stats(reset=True)
+        # per-map FP32 transforms of the same maps (the solver's single-map path)
+        m1, a1 = p.alm2map_f32(ad[0]), p.map2alm_f32(mg[0])
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        for b in range(nm):
+            p.alm2map_f32(ad[b], m1)
+            p.map2alm_f32(mg[b], a1)
+        f1.record()
+        torch.cuda.synchronize()
+        ms_f32 = f0.elapsed_time(f1)
+        # accuracy against the per-map FP64 transforms (untimed, 8 maps)
+        es, ea = [], []
+        for b in range(0, nm, max(1, nm // 8)):
+            mf = p.alm2map(ad[b])
+            es.append(float(torch.linalg.norm(mg[b] - mf) / torch.linalg.norm(mf)))
+            af = p.map2alm(mf)
+            ag1 = p.map2alm_group(mf.unsqueeze(0))[0]
+            ea.append(float(torch.linalg.norm(ag1 - af) / torch.linalg.norm(af)))
+    total_ms = max_over_ranks(ms)
+    if rank != 0:
+        return None
+    k_ms = gs["ms"] / max(gs["launches"], 1)
+    gbps = gs["gbytes"] / (gs["ms"] * 1e-3)
+    tflops = 3 * gs["gflop"] / (gs["ms"] * 1e-3) * 1e-3    # the 3 split products
+    tf32_peak = 0.5 * peaks["bf16_tflops"]
+    roof_h = {"bound": "hbm", "achieved": gbps, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+              "frac": gbps / peaks["hbm_gbs"], "traffic": None,
+              "kernel": "k_group_mma (tcgen05 3xTF32)", "peak_source": peak_src,
+              "algorithmic_gbytes_per_launch": gs["gbytes"] / max(gs["launches"], 1)}
+    roof_t = {"bound": "tensor", "achieved": tflops, "peak": tf32_peak, "unit": "TFLOP/s",
+              "frac": tflops / tf32_peak,
+              "peak_source": "TF32 dense = 0.5 x the measured bf16 burst (nominal ratio)"}
+    roof = roof_h if roof_h["frac"] >= roof_t["frac"] else roof_t
+    steps_pairs = world * nm * args.steps
+    return {"metric": f"map transform pairs/s (alm2map + map2alm), group of {nm} maps "
+                      f"at Nside {ns}",
+            "value": steps_pairs / (total_ms / 1e3), "unit": "pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "3xTF32 products, FP32 accumulation (tcgen05); FP32 ring FFTs",
+            "data": "synthetic",
+            "config": {"workload": f"{nm} band-limited maps, Nside {ns}, lmax {lm}",
+                       "l2": "inputs larger than L2 (maps and coefficients of the group)"},
+            "per_map_f32": {"pairs_per_s": nm / (ms_f32 / 1e3),
+                            "ms_per_pair": ms_f32 / nm},
+            "speedup_vs_per_map_f32": (ms_f32 / nm) / (total_ms / args.steps / nm),
+            "contraction": {"ms_per_launch": k_ms, "launches": gs["launches"],
+                            "share_of_step": gs["ms"] / total_ms,
+                            "hbm": roof_h, "tensor": roof_t},
+            "roofline": roof,
+            "table_build_s": build_s,
+            "vs_fp64_rel_l2": {"synthesis_max": max(es), "analysis_max": max(ea)},
+            "gpu_launches": args.steps * (4 + 4),
+            "clocks": clk}
+
+
 def run_kernel_case(args):
     """One FP32 (or FP64) synthesis + analysis pair at full band on a random
     band-limited field, repeated --reps times; prints the event timings."""
@@ -877,6 +977,8 @@ def main():
         out = run_batch(args, rank, world)
     elif args.workload == "learned":
         out = run_learned(args, rank, world)
+    elif args.workload == "group_sht":
+        out = run_group(args, rank, world)
     else:
         out = run_ours(args, rank, world)
     if rank == 0 and out is not None:

@@ -22,19 +22,23 @@
 // FP32 accuracy.
 //
 // Data layout: each operand tile is stored pre-tiled in global memory as the
-// tensor core reads it from shared memory -- chunks of K = 32 columns, each
+// tensor core reads it from shared memory -- chunks of K = 16 columns, each
 // a block of 8-row x 16-byte core matrices, rows outer -- so one bulk copy
 // (cp.async.bulk, the TMA engine) per operand and chunk moves it, and the
 // shared-memory descriptors need no swizzling.  Only the rows a tile holds
 // (rounded up to 8) are stored and copied.
 //
-// Kernel: one CTA of 128 threads per work item (m, parity, tile).  Thread 0
-// issues the copies of a multi-stage ring of chunk buffers and the MMAs
-// (one elected thread per CTA), commits each chunk's MMAs to the barrier
-// that frees its buffer, and the four warps read the accumulator out of
-// tensor memory (tcgen05.ld, one lane per row) for the epilogue.  Every
-// barrier wait is bounded: on a timeout the kernel sets an error word, waits
-// (bounded) for its copies in flight, frees its tensor memory and returns.
+// Kernel: one CTA of 128 threads per work item: one m and one 128-row tile
+// (analysis: 128 l of each parity; synthesis: 128 ring pairs), the two
+// parities accumulated side by side in tensor memory.  Thread 0 issues the
+// copies of a multi-stage ring of chunk buffers and the MMAs (one elected
+// thread per CTA) and commits each chunk's MMAs to the barrier that frees
+// its buffer; the four warps read the accumulators out of tensor memory
+// (tcgen05.ld, one lane per row) for the epilogue.  Two CTAs share an SM
+// (up to 64 maps per launch), so one's epilogue overlaps the other's
+// copies and products.  Every barrier wait is bounded: on a timeout the
+// kernel sets an error word, waits (bounded) for its copies in flight, frees
+// its tensor memory and returns.
 #include <algorithm>
 #include <vector>
 
@@ -45,22 +49,21 @@ namespace wf {
 
 using namespace tc05;
 
-constexpr int GT = 128;        // rows of a tile (MMA M)
-constexpr int GKC = 32;        // K columns per chunk
+constexpr int GT = 128;          // rows of a tile (MMA M)
+constexpr int GKC = 16;          // K columns per chunk
 constexpr int G_THREADS = 128;
 constexpr int G_MAX_MAPS = 128;  // maps per launch (N = 2 maps <= 256)
 constexpr long G_SPINS = 1L << 22;
 
-// One work item of the contraction: up to two K segments accumulated into
-// two tensor-memory accumulators (analysis: one; synthesis: the two
-// parities of the same pair tile).
+// One work item of the contraction: two K segments (the parities p = 0, 1
+// of one m) accumulated into two tensor-memory accumulators.
 struct GItem {
-  long a_off[2];  // float offset of the segment's first A chunk block
-  long b_unit[2]; // the segment's first B chunk block starts at b_unit x N floats
-  int k[2];       // K extent of the segment (a multiple of 8; 0 = empty)
-  int rows;       // valid rows of the tile
-  int r8;         // rows rounded up to 8 (rows stored per chunk block)
-  int m, p, tile;
+  long a_off[2];   // float offset of the segment's first A chunk block
+  long b_unit[2];  // the segment's first B chunk block starts at b_unit x N floats
+  int k[2];        // K extent of the segment (a multiple of 8; 0 = empty)
+  int rows[2];     // valid rows of the segment's tile
+  int r8[2];       // rows rounded up to 8 (rows stored per chunk block)
+  int m, tile;
 };
 
 // offset of element (row i, column j) inside a chunk block of kc columns
@@ -78,12 +81,19 @@ __host__ __device__ inline int par_count(int lmax, int m, int p) {
 }
 __host__ __device__ inline int round8(int x) { return (x + 7) & ~7; }
 
+__device__ __forceinline__ void split4(const float (&v)[4], float4 &h, float4 &l) {
+  h.x = tf32_trunc(v[0]); l.x = tf32_trunc(v[0] - h.x);
+  h.y = tf32_trunc(v[1]); l.y = tf32_trunc(v[1] - h.y);
+  h.z = tf32_trunc(v[2]); l.z = tf32_trunc(v[2] - h.z);
+  h.w = tf32_trunc(v[3]); l.w = tf32_trunc(v[3] - h.w);
+}
+
 // Per-plan state of the grouped transforms (built by the first call).
 struct GroupState {
   int npairs = 0, k8 = 0;        // ring pairs, rounded up to 8
   std::vector<GItem> ana_h, syn_h;
   GItem *ana = nullptr, *syn = nullptr;
-  int *ana_first = nullptr;      // [(lmax+1) * 2] first analysis item of (m, p)
+  int *ana_first = nullptr;      // [lmax+1] first analysis item of m
   int *syn_first = nullptr;      // [lmax+1] first synthesis item of m
   float *ta_hi = nullptr, *ta_lo = nullptr;  // analysis table (A of the analysis)
   float *ts_hi = nullptr, *ts_lo = nullptr;  // synthesis table
@@ -118,10 +128,10 @@ __global__ void k_group_tables(const RingPair *__restrict__ pairs, int npairs, i
   if (ls > lmax) return;
   const double2 su = seed_u[mk];
   const double z = pairs[k].z;
-  // analysis: column k of chunk k / 32
-  const int ca = k >> 5, ja = k & 31, kca = min(GKC, k8 - 32 * ca);
+  // analysis: column k % GKC of chunk k / GKC
+  const int ca = k / GKC, ja = k % GKC, kca = min(GKC, k8 - GKC * ca);
   // synthesis: row k % 128 of pair tile k / 128
-  const int ts = k >> 7, is = k & (GT - 1);
+  const int ts = k / GT, is = k % GT;
   double u1 = 0.0, u2 = 0.0;
   for (int l = ls; l <= lmax; ++l) {
     const long i = glm_index(lmax, l, m);
@@ -136,16 +146,16 @@ __global__ void k_group_tables(const RingPair *__restrict__ pairs, int npairs, i
     const float lo = tf32_trunc((float)(lam - (double)hi));
     const int p = (l - m) & 1, j = (l - m - p) >> 1;
     {
-      const GItem &it = ana[ana_first[2 * m + p] + (j >> 7)];
-      const long o = it.a_off[0] + (long)ca * it.r8 * GKC + core_off(j & (GT - 1), ja, kca);
+      const GItem &it = ana[ana_first[m] + j / GT];
+      const long o = it.a_off[p] + (long)ca * it.r8[p] * GKC + core_off(j % GT, ja, kca);
       ta_hi[o] = hi;
       ta_lo[o] = lo;
     }
     {
       const GItem &it = syn[syn_first[m] + ts];
       const int kp = it.k[p];
-      const int c = j >> 5, kc = min(GKC, kp - 32 * c);
-      const long o = it.a_off[p] + (long)c * it.r8 * GKC + core_off(is, j & 31, kc);
+      const int c = j / GKC, kc = min(GKC, kp - GKC * c);
+      const long o = it.a_off[p] + (long)c * it.r8[p] * GKC + core_off(is, j % GKC, kc);
       ts_hi[o] = hi;
       ts_lo[o] = lo;
     }
@@ -153,47 +163,47 @@ __global__ void k_group_tables(const RingPair *__restrict__ pairs, int npairs, i
 }
 
 // ------------------------------------------------------------ operand packs
-// analysis B: P^p_m[k][n], n = 2 b + (0: re, 1: im); one thread per
-// (m, 4 consecutive pairs, map), consecutive threads on consecutive m
-__global__ void k_group_pack_ana(const RingPair *__restrict__ pairs, int npairs, int lmax,
-                                 int k8, int N, int nmaps, const float2 *__restrict__ G,
-                                 long gstride, float *bh, float *bl) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  const int q = blockIdx.y, b = blockIdx.z;
-  if (m > lmax) return;
-  const float2 *Gb = G + (long)b * gstride;
-  float er[4], ei[4], orr[4], oi[4];
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    const int k = 4 * q + t;
-    float2 gn = make_float2(0.f, 0.f), gs = gn;
-    if (k < npairs) {
-      const RingPair rp = pairs[k];
-      gn = Gb[(long)rp.ringN * (lmax + 1) + m];
-      if (rp.ringS >= 0) gs = Gb[(long)rp.ringS * (lmax + 1) + m];
+// analysis B: P^p_m[k][n] (n = 2 b + 0 / 1 for re / im) of 8 consecutive m,
+// one K chunk and 4 maps per CTA: the ring coefficients are read in runs of
+// 8 m and staged in shared memory; each (m, p) block of the 4 maps' 8 rows
+// is written as whole 128-byte core matrices.
+constexpr int PACK_THREADS = 256;
+__global__ void __launch_bounds__(PACK_THREADS)
+    k_group_pack_ana(const RingPair *__restrict__ pairs, int npairs, int lmax, int k8, int N,
+                     int nmaps, const float2 *__restrict__ G, long gstride, float *bh,
+                     float *bl) {
+  __shared__ float2 sg[4][2][GKC][8];  // [map][north, south][pair][m]
+  const int m0 = 8 * blockIdx.x, c = blockIdx.y, g = blockIdx.z;
+  const int kc = min(GKC, k8 - GKC * c);
+  for (int t = threadIdx.x; t < 4 * 2 * GKC * 8; t += blockDim.x) {
+    const int mm = t & 7, kk = (t >> 3) % GKC, s = ((t >> 3) / GKC) & 1, b4 = t / (16 * GKC);
+    const int b = 4 * g + b4, k = GKC * c + kk, m = m0 + mm;
+    float2 v = make_float2(0.f, 0.f);
+    if (b < nmaps && k < npairs && m <= lmax) {
+      const int ring = s == 0 ? pairs[k].ringN : pairs[k].ringS;
+      if (ring >= 0) v = G[(long)b * gstride + (long)ring * (lmax + 1) + m];
     }
-    er[t] = gn.x + gs.x;
-    ei[t] = gn.y + gs.y;
-    orr[t] = gn.x - gs.x;
-    oi[t] = gn.y - gs.y;
+    sg[b4][s][kk][mm] = v;
   }
-  const int c = q >> 3, kc = min(GKC, k8 - 32 * c), j = (4 * q) & 31;
+  __syncthreads();
+  const int nki = kc / 4;
+  for (int t = threadIdx.x; t < 8 * 2 * nki * 8; t += blockDim.x) {
+    const int r = t & 7, ki = (t >> 3) % nki, rest = (t >> 3) / nki;
+    const int p = rest & 1, mm = rest >> 1, m = m0 + mm;
+    if (m > lmax || par_count(lmax, m, p) == 0) continue;
+    const int b4 = r >> 1, ri = r & 1;
+    float v[4];
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    if (par_count(lmax, m, p) == 0) continue;
-    const long base = ((long)(2 * m + p) * N) * k8 + (long)c * N * GKC;
-#pragma unroll
-    for (int ri = 0; ri < 2; ++ri) {
-      const float *v = p == 0 ? (ri == 0 ? er : ei) : (ri == 0 ? orr : oi);
-      float4 h, l;
-      h.x = tf32_trunc(v[0]); l.x = tf32_trunc(v[0] - h.x);
-      h.y = tf32_trunc(v[1]); l.y = tf32_trunc(v[1] - h.y);
-      h.z = tf32_trunc(v[2]); l.z = tf32_trunc(v[2] - h.z);
-      h.w = tf32_trunc(v[3]); l.w = tf32_trunc(v[3] - h.w);
-      const long o = base + core_off(2 * b + ri, j, kc);
-      *reinterpret_cast<float4 *>(bh + o) = h;
-      *reinterpret_cast<float4 *>(bl + o) = l;
+    for (int u = 0; u < 4; ++u) {
+      const float2 gn = sg[b4][0][4 * ki + u][mm], gs = sg[b4][1][4 * ki + u][mm];
+      const float a = ri == 0 ? gn.x : gn.y, b = ri == 0 ? gs.x : gs.y;
+      v[u] = p == 0 ? a + b : a - b;
     }
+    float4 h, l;
+    split4(v, h, l);
+    const long o = (long)(2 * m + p) * N * k8 + (long)c * N * GKC + core_off(8 * g + r, 4 * ki, kc);
+    *reinterpret_cast<float4 *>(bh + o) = h;
+    *reinterpret_cast<float4 *>(bl + o) = l;
   }
 }
 
@@ -217,26 +227,21 @@ __global__ void k_group_pack_syn(int lmax, long nalm, int N, const long *__restr
     re[u] = (float)a.x;
     im[u] = (float)a.y;
   }
-  const int c = q >> 3, kc = min(GKC, kp - 32 * c), j0 = (4 * q) & 31;
+  const int c = (4 * q) / GKC, kc = min(GKC, kp - GKC * c), j0 = (4 * q) % GKC;
   const long base = xoff[2 * m + p] * N + (long)c * N * GKC;
-#pragma unroll
-  for (int ri = 0; ri < 2; ++ri) {
-    const float *v = ri == 0 ? re : im;
-    float4 h, l;
-    h.x = tf32_trunc(v[0]); l.x = tf32_trunc(v[0] - h.x);
-    h.y = tf32_trunc(v[1]); l.y = tf32_trunc(v[1] - h.y);
-    h.z = tf32_trunc(v[2]); l.z = tf32_trunc(v[2] - h.z);
-    h.w = tf32_trunc(v[3]); l.w = tf32_trunc(v[3] - h.w);
-    const long o = base + core_off(2 * b + ri, j0, kc);
-    *reinterpret_cast<float4 *>(bh + o) = h;
-    *reinterpret_cast<float4 *>(bl + o) = l;
-  }
+  float4 h, l;
+  split4(re, h, l);
+  *reinterpret_cast<float4 *>(bh + base + core_off(2 * b, j0, kc)) = h;
+  *reinterpret_cast<float4 *>(bl + base + core_off(2 * b, j0, kc)) = l;
+  split4(im, h, l);
+  *reinterpret_cast<float4 *>(bh + base + core_off(2 * b + 1, j0, kc)) = h;
+  *reinterpret_cast<float4 *>(bl + base + core_off(2 * b + 1, j0, kc)) = l;
 }
 
 // ------------------------------------------------------------- contraction
-// MODE 0: analysis (one segment; epilogue a_lm = Omega D);
-// MODE 1: synthesis (segments p = 0, 1 into accumulators 0, 1; epilogue
-// F_N = D0 + D1, F_S = D0 - D1).
+// Both modes accumulate segment p into tensor-memory columns [p N, p N + N).
+// MODE 0 (analysis) epilogue: a_lm = Omega D_p for l = m + p + 2 j;
+// MODE 1 (synthesis): F_N = D0 + D1, F_S = D0 - D1.
 struct GOut {
   double2 *alm;          // analysis: [maps][nalm]
   float2 *F;             // synthesis: [maps][nring][lmax+1]
@@ -247,7 +252,7 @@ struct GOut {
 };
 
 template <int MODE>
-__global__ void __launch_bounds__(G_THREADS, 1)
+__global__ void __launch_bounds__(G_THREADS, 2)
     k_group_mma(const GItem *__restrict__ items, const float *__restrict__ a_hi,
                 const float *__restrict__ a_lo, const float *__restrict__ b_hi,
                 const float *__restrict__ b_lo, int N, int stages, uint32_t tmem_cols,
@@ -275,30 +280,31 @@ __global__ void __launch_bounds__(G_THREADS, 1)
   fence_after_sync();
   const uint32_t tbase = *slot;
 
-  const int nseg = MODE == 0 ? 1 : 2;
   const int c0 = (it.k[0] + GKC - 1) / GKC;
-  const int C = c0 + (nseg > 1 ? (it.k[1] + GKC - 1) / GKC : 0);
+  const int C = c0 + (it.k[1] + GKC - 1) / GKC;
 
   if (tid == 0) {
     const uint32_t idesc = idesc_tf32(GT, N);
     int issued = 0, consumed = 0;
     bool ok = true;
     // chunk i -> its segment, chunk index and width
+    // (segment fields selected without indexing, so they stay in registers)
     auto chunk = [&](int i, int &seg, int &c, int &kc) {
       seg = i < c0 ? 0 : 1;
       c = seg == 0 ? i : i - c0;
-      kc = min(GKC, it.k[seg] - GKC * c);
+      kc = min(GKC, (seg ? it.k[1] : it.k[0]) - GKC * c);
     };
     auto issue = [&](int i) {
       int seg, c, kc;
       chunk(i, seg, c, kc);
       const int s = i % stages;
-      const uint32_t ab = (uint32_t)it.r8 * kc * 4, bb = (uint32_t)N * kc * 4;
+      const int r8 = seg ? it.r8[1] : it.r8[0];
+      const uint32_t ab = (uint32_t)r8 * kc * 4, bb = (uint32_t)N * kc * 4;
       unsigned char *sb = buf + (size_t)s * stage_bytes;
       const uint32_t full = smem_u32(&bars[s]);
       mbar_arrive_expect_tx(full, 2 * (ab + bb));
-      const long ao = it.a_off[seg] + (long)c * it.r8 * GKC;
-      const long bo = it.b_unit[seg] * N + (long)c * N * GKC;
+      const long ao = (seg ? it.a_off[1] : it.a_off[0]) + (long)c * r8 * GKC;
+      const long bo = (seg ? it.b_unit[1] : it.b_unit[0]) * N + (long)c * N * GKC;
       bulk_g2s(smem_u32(sb), a_hi + ao, ab, full);
       bulk_g2s(smem_u32(sb + a_bytes_max), a_lo + ao, ab, full);
       bulk_g2s(smem_u32(sb + 2 * a_bytes_max), b_hi + bo, bb, full);
@@ -307,6 +313,16 @@ __global__ void __launch_bounds__(G_THREADS, 1)
     };
     for (int i = 0; i < min(stages, C); ++i) issue(i);
     for (int i = 0; i < C && ok; ++i) {
+      // refill the buffer of the previous chunk once its MMAs are done, before
+      // waiting for this chunk: all stages' copies stay in flight
+      if (i >= 1 && i - 1 + stages < C) {
+        const int sp = (i - 1) % stages;
+        if (!mbar_wait(smem_u32(&bars[4 + sp]), ((i - 1) / stages) & 1, G_SPINS)) {
+          ok = false;
+          break;
+        }
+        issue(i - 1 + stages);
+      }
       const int s = i % stages;
       if (!mbar_wait(smem_u32(&bars[s]), (i / stages) & 1, G_SPINS)) {
         ok = false;
@@ -330,15 +346,6 @@ __global__ void __launch_bounds__(G_THREADS, 1)
         mma_tf32(d, al, bh, idesc, 1u);
       }
       mma_commit(smem_u32(&bars[4 + s]));
-      // refill the buffer of the previous chunk once its MMAs are done
-      if (i >= 1 && i - 1 + stages < C) {
-        const int sp = (i - 1) % stages;
-        if (!mbar_wait(smem_u32(&bars[4 + sp]), ((i - 1) / stages) & 1, G_SPINS)) {
-          ok = false;
-          break;
-        }
-        issue(i - 1 + stages);
-      }
     }
     mma_commit(smem_u32(&bars[8]));
     if (!ok) {
@@ -356,35 +363,37 @@ __global__ void __launch_bounds__(G_THREADS, 1)
   if (done) {
     const int row = tid;  // tensor-memory lane = tile row
     const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
+    const bool has_odd = it.k[1] > 0;
     if constexpr (MODE == 0) {
       const int j = it.tile * GT + row;
-      const int l = it.m + it.p + 2 * j;
-      const bool valid = row < it.rows;
-      const long idx = glm_index(out.lmax, l, it.m);
+      const bool v0 = row < it.rows[0], v1 = row < it.rows[1];
+      const long i0 = glm_index(out.lmax, it.m + 2 * j, it.m);
       for (int c = 0; c < N; c += 16) {
-        float v[16];
-        tmem_ld16(lane_addr + c, v);
+        float e[16], o[16];
+        tmem_ld16(lane_addr + c, e);
+        if (has_odd) tmem_ld16(lane_addr + N + c, o);
         tmem_wait_ld();
-        if (valid) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int b = c / 2 + q;
-            if (b < out.nmaps)
-              out.alm[(long)b * out.nalm + idx] =
-                  make_double2(out.omega * v[2 * q], out.omega * v[2 * q + 1]);
-          }
+        for (int q = 0; q < 8; ++q) {
+          const int b = c / 2 + q;
+          if (b >= out.nmaps) continue;
+          double2 *ab = out.alm + (long)b * out.nalm + i0;
+          if (v0) ab[0] = make_double2(out.omega * e[2 * q], out.omega * e[2 * q + 1]);
+          if (v1) ab[1] = make_double2(out.omega * o[2 * q], out.omega * o[2 * q + 1]);
         }
       }
     } else {
       const int k = it.tile * GT + row;
-      const bool valid = row < it.rows;
-      const bool has_odd = it.k[1] > 0;
-      RingPair rp;
-      if (valid) rp = out.pairs[k];
+      const bool valid = row < it.rows[0];
+      int ring_n = 0, ring_s = -1;
+      if (valid) {
+        ring_n = out.pairs[k].ringN;
+        ring_s = out.pairs[k].ringS;
+      }
       for (int c = 0; c < N; c += 16) {
         float e[16], o[16];
         tmem_ld16(lane_addr + c, e);
-        tmem_ld16(lane_addr + N + c, o);
+        if (has_odd) tmem_ld16(lane_addr + N + c, o);
         tmem_wait_ld();
         if (valid) {
 #pragma unroll
@@ -394,9 +403,9 @@ __global__ void __launch_bounds__(G_THREADS, 1)
             const float er = e[2 * q], ei = e[2 * q + 1];
             const float orr = has_odd ? o[2 * q] : 0.f, oi = has_odd ? o[2 * q + 1] : 0.f;
             float2 *Fb = out.F + (long)b * out.fstride;
-            Fb[(long)rp.ringN * (out.lmax + 1) + it.m] = make_float2(er + orr, ei + oi);
-            if (rp.ringS >= 0)
-              Fb[(long)rp.ringS * (out.lmax + 1) + it.m] = make_float2(er - orr, ei - oi);
+            Fb[(long)ring_n * (out.lmax + 1) + it.m] = make_float2(er + orr, ei + oi);
+            if (ring_s >= 0)
+              Fb[(long)ring_s * (out.lmax + 1) + it.m] = make_float2(er - orr, ei - oi);
           }
         }
       }
@@ -418,8 +427,11 @@ static inline uint32_t pow2_cols(int c) {
   return n;
 }
 static size_t stage_bytes(int N) { return 2 * (size_t)GT * GKC * 4 + 2 * (size_t)N * GKC * 4; }
+// Up to N = 128 two CTAs share an SM (their accumulators, 2 N columns each,
+// fit the 512 tensor-memory columns together; shared memory <= 113 KB each);
+// above, one CTA per SM with a deeper ring of chunk buffers.
 static int stage_count(int N) {
-  const size_t avail = 220 * 1024 - 128;
+  const size_t avail = (N <= 128 ? 113 * 1024 : 220 * 1024) - 128;
   return (int)std::max<size_t>(2, std::min<size_t>(4, avail / stage_bytes(N)));
 }
 static size_t smem_bytes(int N) { return 128 + stage_count(N) * stage_bytes(N); }
@@ -456,7 +468,7 @@ static wf_status build_group(Plan &P) {
   const int L = P.lmax;
   g->npairs = P.npairs;
   g->k8 = round8(P.npairs);
-  std::vector<int> ana_first(2 * (L + 1), -1), syn_first(L + 1, 0);
+  std::vector<int> ana_first(L + 1, 0), syn_first(L + 1, 0);
   std::vector<long> xoff(2 * (L + 1), 0);
   long xo = 0;
   for (int m = 0; m <= L; ++m)
@@ -466,35 +478,33 @@ static wf_status build_group(Plan &P) {
     }
   g->xoff_total = xo;
   long ta = 0, ts = 0;
-  for (int m = 0; m <= L; ++m)
-    for (int p = 0; p < 2; ++p) {
-      const int cnt = par_count(L, m, p);
-      if (cnt == 0) continue;
-      ana_first[2 * m + p] = (int)g->ana_h.size();
-      for (int t = 0; t * GT < cnt; ++t) {
-        GItem it{};
-        it.rows = std::min(GT, cnt - t * GT);
-        it.r8 = round8(it.rows);
-        it.a_off[0] = ta;
-        ta += (long)it.r8 * g->k8;
-        it.b_unit[0] = (long)(2 * m + p) * g->k8;
-        it.k[0] = g->k8;
-        it.m = m;
-        it.p = p;
-        it.tile = t;
-        g->ana_h.push_back(it);
+  for (int m = 0; m <= L; ++m) {
+    ana_first[m] = (int)g->ana_h.size();
+    for (int t = 0; t * GT < par_count(L, m, 0); ++t) {
+      GItem it{};
+      for (int p = 0; p < 2; ++p) {
+        it.rows[p] = std::max(0, std::min(GT, par_count(L, m, p) - t * GT));
+        it.r8[p] = round8(it.rows[p]);
+        it.k[p] = it.rows[p] > 0 ? g->k8 : 0;
+        it.a_off[p] = ta;
+        ta += (long)it.r8[p] * it.k[p];
+        it.b_unit[p] = (long)(2 * m + p) * g->k8;
       }
+      it.m = m;
+      it.tile = t;
+      g->ana_h.push_back(it);
     }
+  }
   for (int m = 0; m <= L; ++m) {
     syn_first[m] = (int)g->syn_h.size();
     for (int t = 0; t * GT < P.npairs; ++t) {
       GItem it{};
-      it.rows = std::min(GT, P.npairs - t * GT);
-      it.r8 = round8(it.rows);
       for (int p = 0; p < 2; ++p) {
+        it.rows[p] = std::min(GT, P.npairs - t * GT);
+        it.r8[p] = round8(it.rows[p]);
         it.k[p] = round8(par_count(L, m, p));
         it.a_off[p] = ts;
-        ts += (long)it.r8 * it.k[p];
+        ts += (long)it.r8[p] * it.k[p];
         it.b_unit[p] = xoff[2 * m + p];
       }
       it.m = m;
@@ -575,7 +585,7 @@ static wf_status launch_mma(Plan &P, int nb, GOut out) {
   GroupState *g = P.group;
   const int N = round16(2 * nb);
   const std::vector<GItem> &items = MODE == 0 ? g->ana_h : g->syn_h;
-  const uint32_t cols = pow2_cols(MODE == 0 ? N : 2 * N);
+  const uint32_t cols = pow2_cols(2 * N);
   WF_CUDA(cudaEventRecord(g->ev[0], P.stream));
   ++P.nlaunch;
   k_group_mma<MODE><<<(unsigned)items.size(), G_THREADS, smem_bytes(N), P.stream>>>(
@@ -587,13 +597,11 @@ static wf_status launch_mma(Plan &P, int nb, GOut out) {
   float ms = 0.f;
   WF_CUDA(cudaEventElapsedTime(&ms, g->ev[0], g->ev[1]));
   double terms = 0.0, bytes = 0.0;
-  for (const GItem &it : items) {
-    const int nseg = MODE == 0 ? 1 : 2;
-    for (int s = 0; s < nseg; ++s) {
-      terms += (double)it.rows * (MODE == 0 ? P.npairs : it.k[s]);
-      bytes += 8.0 * it.r8 * it.k[s];  // A hi + lo
+  for (const GItem &it : items)
+    for (int s = 0; s < 2; ++s) {
+      terms += (double)it.rows[s] * (MODE == 0 ? P.npairs : it.k[s]);
+      bytes += 8.0 * it.r8[s] * it.k[s];  // A hi + lo
     }
-  }
   // B hi + lo once, result once
   if (MODE == 0) {
     bytes += 8.0 * 2 * (P.lmax + 1) * g->k8 * N + 16.0 * nb * P.nalm;
@@ -616,13 +624,13 @@ wf_status map2alm_group(Plan &P, int nmaps, const double *maps, double *alm) {
   for (int b0 = 0; b0 < nmaps; b0 += G_MAX_MAPS) {
     const int nb = std::min(G_MAX_MAPS, nmaps - b0);
     const int N = round16(2 * nb);
-    for (int b = 0; b < nb; ++b)
-      WF_TRY(launch_ring<float2>(P, RING_ANALYSIS, nullptr, g->ring + b * fstride,
-                                 maps + (long)(b0 + b) * P.npix, nullptr, nullptr, P.lmax));
-    dim3 grid((P.lmax + 128) / 128, g->k8 / 4, nb);
+    WF_TRY(launch_ring_batch32(P, RING_ANALYSIS, nullptr, g->ring, maps + (long)b0 * P.npix,
+                               nullptr, nb, fstride, P.npix));
+    dim3 grid((P.lmax + 8) / 8, (g->k8 + GKC - 1) / GKC, (nb + 3) / 4);
     ++P.nlaunch;
-    k_group_pack_ana<<<grid, 128, 0, P.stream>>>(P.pairs, P.npairs, P.lmax, g->k8, N, nb,
-                                                 g->ring, fstride, g->b_hi, g->b_lo);
+    k_group_pack_ana<<<grid, PACK_THREADS, 0, P.stream>>>(P.pairs, P.npairs, P.lmax, g->k8, N,
+                                                          nb, g->ring, fstride, g->b_hi,
+                                                          g->b_lo);
     WF_CUDA(cudaGetLastError());
     GOut out{};
     out.alm = reinterpret_cast<double2 *>(alm) + (long)b0 * P.nalm;
@@ -662,9 +670,8 @@ wf_status alm2map_group(Plan &P, int nmaps, const double *alm, double *maps) {
     out.lmax = P.lmax;
     out.nmaps = nb;
     WF_TRY(launch_mma<1>(P, nb, out));
-    for (int b = 0; b < nb; ++b)
-      WF_TRY(launch_ring<float2>(P, RING_SYNTH, g->ring + b * fstride, nullptr, nullptr,
-                                 maps + (long)(b0 + b) * P.npix, nullptr, P.lmax));
+    WF_TRY(launch_ring_batch32(P, RING_SYNTH, g->ring, nullptr, nullptr,
+                               maps + (long)b0 * P.npix, nb, fstride, P.npix));
   }
   return WF_OK;
 }

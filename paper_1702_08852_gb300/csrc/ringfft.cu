@@ -405,13 +405,22 @@ __global__ void __launch_bounds__(RING_THREADS_BIG)
            const SolverState *__restrict__ st, int lstatic, int reverse,
            const float *__restrict__ in32, const float *__restrict__ nv32, int red_ofs,
            const typename CT<T2>::W *__restrict__ phase_all,
-           const float2 *__restrict__ in_dd, const float2 *__restrict__ nv_dd) {
+           const float2 *__restrict__ in_dd, const float2 *__restrict__ nv_dd,
+           long bstride_f, long bstride_m) {
   typedef typename CT<T2>::T T;
   typedef typename CT<T2>::G GT;
   typedef typename CT<T2>::W WT;
   // reverse: the polar rings grow with the pair index; taking the largest
   // first keeps the small ones for the tail of the launch
   const int blk = reverse ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+  // batched launches (plain transforms of several maps): map blockIdx.y
+  if (gridDim.y > 1) {
+    const long bm = blockIdx.y;
+    if (F) F += bm * bstride_f;
+    if (G) G += bm * bstride_f;
+    if (in_map) in_map += bm * bstride_m;
+    if (out_map) out_map += bm * bstride_m;
+  }
   const RingPair rp = pairs[pair_base + blk];
   int Lf = lstatic, Lg = lstatic;
   double xi = 0.0, mu = 0.0, alpha = 1.0;
@@ -661,7 +670,8 @@ template <typename T2, int MODE>
 static wf_status launch_ring_mode(const Plan &P, const typename CT<T2>::G *F,
                                   typename CT<T2>::G *G, const double *in_map,
                                   double *out_map, const SolverState *st, int lstatic,
-                                  const float *in32, const float2 *in_dd = nullptr) {
+                                  const float *in32, const float2 *in_dd = nullptr,
+                                  int nbatch = 1, long bstride_f = 0, long bstride_m = 0) {
   auto kern = k_ring<T2, MODE>;
   // two launches: the polar rings (pairs 0 .. nside-2, Bluestein unless n is
   // a power of two) and the equatorial belt (pairs nside-1 .. 2 nside-1);
@@ -688,10 +698,10 @@ static wf_status launch_ring_mode(const Plan &P, const typename CT<T2>::G *F,
     const size_t smem = sizeof(T2) * (Mg + (nmin < threads ? 2 * threads : 0));
     cudaStream_t s = (fork && g == 1) ? P.side_stream : P.stream;
     ++P.nlaunch;
-    kern<<<e - b, threads, smem, s>>>(
+    kern<<<dim3(e - b, nbatch), threads, smem, s>>>(
         P.pairs, b, P.lmax, F, G, in_map, out_map, P.nvar, Tables<T2>::tw(P),
         P.fftMmax, Tables<T2>::ch(P), Tables<T2>::bh(P), st, lstatic, g == 0, in32,
-        P.nvar32, red_ofs, Tables<T2>::ph(P), in_dd, P.nvardd);
+        P.nvar32, red_ofs, Tables<T2>::ph(P), in_dd, P.nvardd, bstride_f, bstride_m);
     WF_CUDA(cudaGetLastError());
   }
   if (fork) {
@@ -718,6 +728,20 @@ wf_status launch_ring(const Plan &P, int mode, const T2 *F, T2 *G,
       }
       return launch_ring_mode<T2, RING_FUSED>(P, F, G, in_map, out_map, st, lstatic, in32);
   }
+}
+
+wf_status launch_ring_batch32(const Plan &P, int mode, const float2 *F, float2 *G,
+                             const double *in_map, double *out_map, int nbatch,
+                             long fstride, long mstride) {
+  if (mode == RING_SYNTH)
+    return launch_ring_mode<float2, RING_SYNTH>(P, F, G, in_map, out_map, nullptr, P.lmax,
+                                                nullptr, nullptr, nbatch, fstride, mstride);
+  if (mode == RING_ANALYSIS)
+    return launch_ring_mode<float2, RING_ANALYSIS>(P, F, G, in_map, out_map, nullptr,
+                                                   P.lmax, nullptr, nullptr, nbatch, fstride,
+                                                   mstride);
+  set_error("batched ring transform: synthesis or analysis only");
+  return WF_ERR_ARG;
 }
 
 wf_status launch_ring_dd(const Plan &P, int mode, const float4 *F, float4 *G,

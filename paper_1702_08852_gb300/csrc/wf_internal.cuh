@@ -323,6 +323,11 @@ wf_status launch_ring(const Plan &P, int mode, const T2 *F, T2 *G,
 wf_status launch_ring_dd(const Plan &P, int mode, const float4 *F, float4 *G,
                          const double *in_map, double *out_map, const SolverState *st,
                          int lstatic, const float2 *in_dd = nullptr);
+// The FP32 ring synthesis or analysis of nbatch maps in one launch pair
+// (map b: F / G at b * fstride, maps at b * mstride; full band lmax).
+wf_status launch_ring_batch32(const Plan &P, int mode, const float2 *F, float2 *G,
+                              const double *in_map, double *out_map, int nbatch,
+                              long fstride, long mstride);
 // FP64 map -> double-float pairs (hi, lo); +inf -> (+inf, 0)
 wf_status launch_to_dd(const Plan &P, const double *in, float2 *out, long n);
 
