@@ -165,7 +165,7 @@ def test_tuning_report_and_bad_values(torch_cuda):
         # FP64 has no 16-pair, queue or packed candidates
         assert all(ms == -1.0 for ms in t["ana_ms"][0][3:])
         assert all(ms == -1.0 for ms in t["syn_ms"][0][3:])
-        assert t["ana_np"][1] in (2, 4, 8, 16) and t["ana_queue"] in (0, 1)
+        assert t["ana_np"][1] in (2, 4, 6, 8, 16) and t["ana_queue"] in (0, 1)
         for bad in (dict(syn_np=(3, 2)), dict(ana_np=(16, 8)), dict(ana_queue=2),
                     dict(ana_np=(4, 2), ana_queue=1),
                     dict(ana_np=(4, 8), ana_queue=1, ana_packed=1),
