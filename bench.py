@@ -331,7 +331,7 @@ def run_ours(args, rank, world):
     # plain FP64 dual messenger on the same map (rank 0): the comparison the
     # speedup is quoted against, and the mixed result's distance from it;
     # beside it the mixed solver's fast configuration on the same map
-    fp64, fast, cfg2, methods, flat = {}, {}, {}, {}, {}
+    fp64, fast, cfg2, methods, flat, group = {}, {}, {}, {}, {}, {}
     if rank == 0 and not args.no_fp64:
         p64 = wf.Plan(p.nside, p.lmax, p.cl, nv, mk, precision=wf.WF_PREC_FP64,
                       eps_final=args.eps, timing=1, autotune=1)
@@ -357,6 +357,8 @@ def run_ours(args, rank, world):
         cfg2 = config2(wf, args)
         methods = methods_comparison(wf, args)
         flat = flat_sky(wf, args)
+        group = run_group(argparse.Namespace(nside=256, group_maps=64, steps=5, warmup=3),
+                          0, 1)
     plan.close()
     if dist:
         dist.barrier()
@@ -399,6 +401,9 @@ def run_ours(args, rank, world):
         "nside256": cfg2,
         "methods_nside256": methods,
         "flat_sky_512": flat,
+        "group_sht_nside256": {k: group.get(k) for k in (
+            "metric", "value", "unit", "ms_per_step", "per_map_f32", "speedup_vs_per_map_f32",
+            "contraction", "vs_fp64_rel_l2", "table_build_s")} if group else {},
         "peaks": {"hbm_gbs": peaks.get("hbm_gbs"), "source": peak_src, "alu": alu},
     }
     out["gpu_launches"] = int(sum(s["kernel_launches"] for s in stats))
