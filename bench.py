@@ -137,12 +137,13 @@ def measured_peaks():
 # the --kernel-case legendre32 run); scaled to a live launch by its share
 # of the full band's terms.  None once the kernel changes after a capture,
 # and for a plan whose autotuner picked another analysis variant.
-ANALYSIS_DRAM_FULL_BAND = {"nside": 1024, "bytes": None,
+ANALYSIS_DRAM_FULL_BAND = {"nside": 1024, "bytes": 213754624.0,
                            "terms": 3140761977.0,
                            "variant": {"ana_np": 4, "ana_queue": 0, "ana_packed": 1,
                                        "ana_global_acc": 1},
-                           "source": "none: the analysis kernel changed (anchored-stage "
-                                     "denominator) after the last ncu capture"}
+                           "source": "ncu --set full, one full-band launch of the kernel "
+                                     "case (dram__bytes_read.sum 137.4 MB + "
+                                     "dram__bytes_write.sum 76.4 MB)"}
 
 
 def analysis_variant(tuning):
