@@ -963,6 +963,10 @@ def run_profile_solve(args):
 
 def main():
     args = parse()
+    # more hardware work queues than the default 8, so that the batch's
+    # per-map streams do not share queues (read when the CUDA context is
+    # created, i.e. before the first CUDA call of this process)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     if args.kernel_case:
         run_kernel_case(args)
         return

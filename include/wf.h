@@ -198,9 +198,13 @@ wf_status wf_solve(wf_plan_t plan, const double *d_dev, double *alm_dev,
  * be distinct plans with noise; each may have its own nside, lmax, spectrum,
  * noise, mask and options.  d_dev[i] / alm_dev[i] / map_dev[i] as in
  * wf_solve (alm_dev, map_dev and their entries may be NULL).  The maps run
- * concurrently on private streams, each driven by its own host thread with
- * its own captured iteration graphs and device-side stage control; results
- * equal wf_solve's map by map.  stats: NULL or n entries.  elapsed_ms: device
+ * concurrently on private streams, each with its own captured iteration
+ * graphs and device-side stage control, driven by a pool of host threads
+ * (at most one per hardware thread) that take the maps largest first;
+ * results equal wf_solve's map by map.  Concurrency is best when the
+ * process sets CUDA_DEVICE_MAX_CONNECTIONS=32 before its CUDA context is
+ * created (the default 8 hardware queues make streams share queues).
+ * stats: NULL or n entries.  elapsed_ms: device
  * time from the start of the first map to the end of the last.  Returns the
  * first error, else WF_ERR_NOT_CONVERGED if a map hit max_iter, else WF_OK. */
 wf_status wf_solve_batch(wf_plan_t *plans, int n, const double *const *d_dev,

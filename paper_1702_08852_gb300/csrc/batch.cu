@@ -2,11 +2,17 @@
 //
 // Each map keeps its own plan (geometry, noise, mask, spectrum, captured
 // iteration graphs, device-side stage control).  A batch run gives every map
-// a private non-blocking stream and drives its solve from its own host
-// thread, so the small per-map kernels of maps with Nside 64-256 execute
-// concurrently and fill the GPU; maps of different sizes and convergence
-// speeds finish independently.  Results are identical to solving the maps
-// one by one (each map's arithmetic does not depend on the others).
+// a private non-blocking stream; a pool of host threads, one per hardware
+// thread at most, takes maps from a queue (largest first) and drives each
+// one's solve, so the small per-map kernels of maps with Nside 64-256
+// execute concurrently and fill the GPU, while no more threads wait on the
+// GPU than there are cores to run them; maps of different sizes and
+// convergence speeds finish independently.  Results are identical to solving
+// the maps one by one (each map's arithmetic does not depend on the
+// others).
+#include <algorithm>
+#include <atomic>
+#include <numeric>
 #include <string>
 #include <thread>
 #include <vector>
@@ -45,14 +51,25 @@ wf_status solve_batch(Plan **plans, int n, const double *const *d, double *const
   const bool timed = cudaEventCreate(&t0) == cudaSuccess && cudaEventCreate(&t1) == cudaSuccess;
   if (timed) cudaEventRecord(t0, nullptr);
   for (int i = 0; i < n; ++i) cudaStreamWaitEvent(own[i], t0, 0);
+  // largest maps first, so that the longest solves start at once
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return plans[a]->npix > plans[b]->npix; });
+  const int hw = (int)std::thread::hardware_concurrency();
+  const int nthreads = std::max(1, std::min(n, hw > 0 ? hw : n));
+  std::atomic<int> next(0);
   std::vector<std::thread> threads;
-  threads.reserve(n);
-  for (int i = 0; i < n; ++i) {
-    threads.emplace_back([&, i]() {
+  threads.reserve(nthreads);
+  for (int w = 0; w < nthreads; ++w) {
+    threads.emplace_back([&]() {
       cudaSetDevice(dev);
-      status[i] = solve(*plans[i], d[i], alm ? alm[i] : nullptr, map ? map[i] : nullptr,
-                        nullptr, nullptr, stats ? &stats[i] : nullptr);
-      if (status[i] != WF_OK) msg[i] = wf_last_error();
+      for (int q = next.fetch_add(1); q < n; q = next.fetch_add(1)) {
+        const int i = order[q];
+        status[i] = solve(*plans[i], d[i], alm ? alm[i] : nullptr, map ? map[i] : nullptr,
+                          nullptr, nullptr, stats ? &stats[i] : nullptr);
+        if (status[i] != WF_OK) msg[i] = wf_last_error();
+      }
     });
   }
   for (auto &t : threads) t.join();
