@@ -675,7 +675,9 @@ static wf_status fp64_step(Plan &P, const double2 *x, double2 *gx, double *num,
     WF_TRY(launch_ring<double2>(P, RING_FUSED, P.F64, P.G64, P.dmap, nullptr, P.state,
                                 P.lmax));
   if (timed) WF_CUDA(cudaEventRecord(P.dd_ev[2], P.stream));
-  const int La = U ? std::max(L, Lu) : P.lmax;  // band of the analysis launch
+  // band of the analysis launch: the state's lcur (= L) unless it also
+  // computes the unfiltered analysis up to the next stage's band
+  const int La = U ? std::max(L, Lu) : std::max(L, 0);
   if (U) {
     const int Lb = std::max(L, Lu);
     if (dd)
