@@ -336,6 +336,7 @@ def run_ours(args, rank, world):
     if rank == 0 and not args.no_fp64:
         p64 = wf.Plan(p.nside, p.lmax, p.cl, nv, mk, precision=wf.WF_PREC_FP64,
                       eps_final=args.eps, timing=1, autotune=1)
+        flush_l2(flush)
         a64, m64, s64 = p64.solve(d)
         k64 = [p64.kernel_stats(k) for k in (0, 1)]
         fp64 = {"solve_s": s64["elapsed_ms"] / 1e3, "iterations": s64["iterations"],

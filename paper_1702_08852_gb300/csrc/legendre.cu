@@ -1228,10 +1228,10 @@ __global__ void __launch_bounds__(SYN_THREADS)
   }
   lmin = warp_min(lmin);
   linj = warp_max(linj);
-  for (int l = lmin; l <= L; ++l) {
+  // one l at a time: seeds may enter (inj), parity of l - m picks the sums
+  auto step = [&](int l, bool inj) {
     const dd c = sc[l - m], xr = sxr[l - m], xi = sxi[l - m];
     const bool even = ((l - m) & 1) == 0;
-    const bool inj = l <= linj;
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
       dd u = dd_rec(c, z[j], u1[j], u2[j]);
@@ -1249,7 +1249,29 @@ __global__ void __launch_bounds__(SYN_THREADS)
         dd_acc(oi[j], u, xi);
       }
     }
+  };
+  int l = lmin;
+  for (; l <= L && l <= linj; ++l) step(l, true);
+  if (l <= L && ((l - m) & 1)) step(l++, false);
+  // plain recurrence two l at a time (l - m even, then odd): the same
+  // operations in the same order, without the parity branch and with the
+  // u_{l-1}, u_{l-2} rotation left to register renaming
+  for (; l + 1 <= L; l += 2) {
+    const dd c0 = sc[l - m], xr0 = sxr[l - m], xi0 = sxi[l - m];
+    const dd c1 = sc[l + 1 - m], xr1 = sxr[l + 1 - m], xi1 = sxi[l + 1 - m];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const dd w = dd_rec(c0, z[j], u1[j], u2[j]);
+      dd_acc(er[j], w, xr0);
+      dd_acc(ei[j], w, xi0);
+      const dd v = dd_rec(c1, z[j], w, u1[j]);
+      dd_acc(orr[j], v, xr1);
+      dd_acc(oi[j], v, xi1);
+      u2[j] = w;
+      u1[j] = v;
+    }
   }
+  if (l <= L) step(l, false);
   const long stride = lmax + 1;
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
