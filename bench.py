@@ -57,6 +57,12 @@ def parse():
     ap.add_argument("--train-maps", type=int, default=64)
     ap.add_argument("--eval-maps", type=int, default=8)
     ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--net-channels", type=int, default=16,
+                    help="learned: channels of the per-ring convolutions (<= 32)")
+    ap.add_argument("--net-kernel", type=int, default=9,
+                    help="learned: odd convolution width (<= 15)")
+    ap.add_argument("--net-hidden", type=int, default=32,
+                    help="learned: width of the l-feature MLP (<= 64)")
     ap.add_argument("--profile-solve", action="store_true",
                     help="one warm-up solve, then one solve inside the NVTX range "
                          "'solve' (for a bounded profiler launch list) and exit")
@@ -711,7 +717,7 @@ def run_learned(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     ns = 256
-    H, K, Hm = 16, 9, 32
+    H, K, Hm = args.net_channels, args.net_kernel, args.net_hidden
     t_start = time.perf_counter()
 
     def make(seed):
