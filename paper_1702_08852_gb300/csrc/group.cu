@@ -615,9 +615,17 @@ static wf_status launch_mma(Plan &P, int nb, GOut out) {
   return check_group_err(P);
 }
 
+// build_group, leaving no half-built state behind on failure
+static wf_status ensure_group(Plan &P) {
+  if (P.group) return WF_OK;
+  const wf_status s = build_group(P);
+  if (s != WF_OK) free_group(P);
+  return s;
+}
+
 wf_status map2alm_group(Plan &P, int nmaps, const double *maps, double *alm) {
   if (nmaps == 0) return WF_OK;
-  if (!P.group) WF_TRY(build_group(P));
+  WF_TRY(ensure_group(P));
   GroupState *g = P.group;
   WF_TRY(reserve_group(P, std::min(nmaps, G_MAX_MAPS)));
   const long fstride = (long)P.nring * (P.lmax + 1);
@@ -647,7 +655,7 @@ wf_status map2alm_group(Plan &P, int nmaps, const double *maps, double *alm) {
 
 wf_status alm2map_group(Plan &P, int nmaps, const double *alm, double *maps) {
   if (nmaps == 0) return WF_OK;
-  if (!P.group) WF_TRY(build_group(P));
+  WF_TRY(ensure_group(P));
   GroupState *g = P.group;
   WF_TRY(reserve_group(P, std::min(nmaps, G_MAX_MAPS)));
   const long fstride = (long)P.nring * (P.lmax + 1);
