@@ -54,6 +54,33 @@ def test_batch_equals_one_by_one(torch_cuda, osht, precision):
         plan.close()
 
 
+def test_batch_with_more_maps_than_host_threads(torch_cuda, osht):
+    """More maps than the pool has threads (one per core): the queue hands
+    each thread several maps, largest first; every result equals its
+    one-by-one solve."""
+    import os
+    torch = torch_cuda
+    from paper_1702_08852_gb300 import wf
+    n = (os.cpu_count() or 16) + 5
+    specs = [("lognormal" if i % 2 else "scan", 8, 100 + i) for i in range(n)]
+    probs = make_problems(osht, specs)
+    plans, ds, single = [], [], []
+    for p, d in probs:
+        nv = torch.from_numpy(p.noise_var).cuda()
+        mk = torch.from_numpy(p.mask.astype(np.uint8)).cuda()
+        plan = wf.Plan(p.nside, p.lmax, p.cl, nv, mk, precision=1)
+        dd = torch.from_numpy(d).cuda()
+        a, _, _ = plan.solve(dd, want_map=False)
+        single.append(a.cpu().numpy())
+        plans.append(plan)
+        ds.append(dd)
+    alms, _, stats, _ = wf.wf_solve_batch(plans, ds)
+    for a1, a2, st in zip(single, alms, stats):
+        assert np.array_equal(a1, a2.cpu().numpy()) and st["converged"] == 1
+    for plan in plans:
+        plan.close()
+
+
 def test_batch_rejects_duplicates_and_missing_noise(torch_cuda):
     torch = torch_cuda
     from paper_1702_08852_gb300 import wf
