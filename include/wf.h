@@ -309,9 +309,10 @@ wf_status wf_map2alm_df64(wf_plan_t plan, const double *map_dev, double *alm_dev
  *            b * 2 * Nalm doubles, layout as for wf_solve.
  *  nmaps     >= 0; up to 128 maps go into one product, and more are done
  *            in groups of 128.  0 does nothing.
- * The first call builds the table on the device: about 16 bytes per
- * (l, m, ring pair), twice (one copy laid out for each direction; ~1.1 GB
- * at Nside 256, lmax 512).  Its operand buffers are sized for the largest
+ * The first call builds the table on the device: two copies, one laid out
+ * for each direction, each 8 bytes (TF32 hi and lo) per (l, m, ring pair),
+ * about 16 bytes per term in all (~1.1 GB at Nside 256, lmax 512).  Its
+ * operand buffers are sized for the largest
  * group seen.  Both stay until wf_destroy.  Host-synchronous.  Errors:
  * WF_ERR_ARG for nmaps < 0 or a NULL buffer with nmaps > 0; WF_ERR_CUDA
  * (e.g. out of device memory); WF_ERR_TIMEOUT if a device barrier wait gave
